@@ -1,0 +1,177 @@
+/*
+ * sfg.h -- C ABI of the GB300 self-gravity library (libsfg.so).
+ *
+ * The library evaluates the self-gravity field of gas cells and sink
+ * particles as the STARFORGE methods paper defines it (Grudic et al. 2021,
+ * Sec. 2.2 "Gravity" and Sec. 2.2.1 "Softening"): an oct-tree over the
+ * particles, Barnes-Hut opening angle theta = L/r (node side over distance to
+ * the node centre of mass, Sec. 2.2), monopole + quadrupole node fields, and
+ * per-pair M4 cubic-spline softening of compact support: the adaptive gas
+ * softening S_i = H_i with the two kernels averaged for gas-gas pairs, and a
+ * single kernel of support max(S_i, S_j) for any pair that involves a sink
+ * (Sec. 2.2.1).  The field is evaluated only for the "active" particles of a
+ * timestep bin (Sec. 2.3), and the library also provides the adjoint
+ * (vector-Jacobian product) of that evaluation with the interaction lists
+ * frozen, built from the softened tidal tensor T = -grad grad Phi of the same
+ * kernel (Sec. 2.2).
+ *
+ * Conventions (every entry point):
+ *   - All array pointers are DEVICE pointers unless stated otherwise, in
+ *     row-major layout: positions are [n][3] float64 (x, y, z interleaved).
+ *   - Calls are asynchronous and ordered on the CUDA stream passed as
+ *     `stream` (a cudaStream_t; NULL = the legacy default stream), except
+ *     sfg_build, which synchronizes `stream` once at its end to size the tree.
+ *   - Inputs are owned by the caller and may be freed once the stream has
+ *     passed the call.  sfg_build copies what the tree needs.  Outputs are
+ *     allocated by the caller.
+ *   - A tree must be used from one stream at a time (it keeps a workspace).
+ *   - Return value: SFG_OK or an SFG_E* status.  Nothing aborts or exits.
+ *     Errors that only the device can see (non-finite inputs, an index out
+ *     of range, a traversal buffer overflow that survived its retry) are
+ *     recorded in the tree's status word and returned by sfg_get_status,
+ *     which synchronizes the tree's last stream.
+ *   - Particle indices are int64 in [0, n); n must be < 2^31.
+ */
+#ifndef SFG_H
+#define SFG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFG_OK 0
+#define SFG_EINVAL 1    /* bad argument: n <= 0, NULL pointer, h <= 0, m < 0, non-finite, index out of range */
+#define SFG_ENOMEM 2    /* device allocation failed */
+#define SFG_ECUDA 3     /* a CUDA runtime call or launch failed */
+#define SFG_EOVERFLOW 4 /* a traversal buffer overflowed even after the automatic retry */
+#define SFG_ETIMEOUT 5  /* a bounded device-side wait gave up */
+
+typedef struct sfg_tree sfg_tree; /* opaque; owns its device memory */
+
+/* Numerical and launch parameters of a tree. */
+typedef struct sfg_params {
+    double G;        /* gravitational constant multiplying every term */
+    double theta;    /* maximum opening angle Theta of Sec. 2.2 (the paper uses 0.5); 0 = always open */
+    int leaf_size;   /* N_leaf: a node with <= N_leaf particles (or at the 21st level) is a leaf; 1..256 */
+    int group_size;  /* G_group: <= G_group active targets share one walk; 1..32 */
+    int list_depth;  /* interaction-list buffer depth per warp (reserved; 0 = default) */
+    int quadrupole;  /* 1: monopole + quadrupole node fields; 0: monopole only (Sec. 2.2) */
+    int precision;   /* 0: FP32 pair/multipole arithmetic on node-centred offsets, FP64
+                        frame/moments/potential sums; 1: all-FP64 evaluation */
+    int store_lists; /* reserved: the adjoint always recomputes the forward's lists */
+    /* Optional device allocator (stream-ordered).  NULL alloc => cudaMallocAsync. */
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *alloc_ctx;
+} sfg_params;
+
+/* Summary of a tree and of the last sfg_accel / sfg_accel_vjp call. */
+typedef struct sfg_stats {
+    int64_t n;            /* particles */
+    int64_t n_nodes;      /* tree nodes */
+    int32_t depth;        /* deepest level (root = 0) */
+    int32_t n_levels;     /* depth + 1 */
+    double x0[3];         /* frame origin: per-axis minimum position */
+    double L0;            /* root cube side: smallest power of two >= the largest extent */
+    int64_t n_groups;     /* groups of the last call */
+    int64_t n_targets;    /* distinct active particles of the last call */
+    int64_t n_p2p;        /* particle-particle interactions of the last call (self excluded) */
+    int64_t n_p2m;        /* particle-node interactions of the last call */
+    int64_t n_overflow;   /* groups that needed the spill traversal buffer */
+} sfg_stats;
+
+/* Fill *p with the defaults: G = 1, theta = 0.5, leaf_size = 16, group_size = 32,
+ * quadrupole = 1, precision = 0, list_depth = 0, store_lists = 0, no allocator. */
+void sfg_default_params(sfg_params *p);
+
+/* Build the tree of n particles (Sec. 2.2: the oct-tree over every gas cell and
+ * sink): frame, 63-bit Morton keys on a 2^21-per-axis grid, stable radix sort,
+ * octree, FP64 node moments (mass, centre of mass, traceless quadrupole about
+ * it), and the FP32 node/particle records of the walk.
+ *   pos     [n][3] float64, device
+ *   mass    [n]    float64 >= 0, device
+ *   soft    [n]    float64 > 0, device: kernel radius of compact support (H for
+ *                  gas, S_* for sinks, Sec. 2.2.1)
+ *   is_sink [n]    uint8 (nonzero = sink particle), device, or NULL (all gas)
+ *   params  host pointer, or NULL for the defaults; copied into the tree
+ *   out     host pointer receiving the new tree (NULL on failure)
+ * Synchronizes `stream` once (the node count sizes the tree).  Errors:
+ * SFG_EINVAL (n <= 0, n >= 2^31, NULL pointer, bad params, non-finite or
+ * out-of-domain inputs), SFG_ENOMEM, SFG_ECUDA. */
+int sfg_build(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink, int64_t n,
+              const sfg_params *params, void *stream, sfg_tree **out);
+
+/* Field at the active particles (Sec. 2.2, the active set of a timestep bin,
+ * Sec. 2.3): for row k, the particle i = active_idx[k] gets
+ *   accel[k][3] = g_i = -grad Phi (x_i)   and   phi[k] = Phi(x_i),
+ * summing softened pair terms over the particles of opened leaves (self
+ * excluded) and multipole terms over accepted nodes.
+ *   active_idx [n_active] int64, device, or NULL for all particles in order;
+ *              duplicates are allowed (rows are independent)
+ *   accel      [n_active][3] float64, device, overwritten
+ *   phi        [n_active]    float64, device, overwritten (may be NULL)
+ * n_active == 0 is a no-op.  An index outside [0, n) is reported through
+ * sfg_get_status as SFG_EINVAL and its row is left unwritten. */
+int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
+              void *stream);
+
+/* Adjoint of sfg_accel with the interaction lists frozen (recomputed by the
+ * same walk): with L = sum_k cot_a[k] . accel[k] + cot_phi[k] * phi[k],
+ *   d_pos[n][3] = dL/dpos  and  d_mass[n] = dL/dmass
+ * (original particle order, overwritten), including the dependence of node
+ * moments on member positions and masses.  The softening radii are constants.
+ *   cot_a   [n_active][3] float64, device
+ *   cot_phi [n_active]    float64, device, or NULL (zero)
+ * Duplicate rows sum.  Errors as for sfg_accel. */
+int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
+                  const double *cot_phi, double *d_pos, double *d_mass, void *stream);
+
+/* Statistics of the tree and of its last call (host pointer).  Synchronizes. */
+int sfg_get_stats(sfg_tree *tree, sfg_stats *out);
+
+/* Device-side status accumulated since the last call of this function
+ * (SFG_OK if none); synchronizes the tree's last stream and clears it. */
+int sfg_get_status(sfg_tree *tree);
+
+/* Release the tree and all its device memory (synchronizes its last stream). */
+void sfg_free(sfg_tree *tree);
+
+/* Static string naming a status code. */
+const char *sfg_status_string(int status);
+
+/* ---- inspection (tests and tools; copies to HOST memory, synchronizing) ----
+ * field ids and layouts:
+ *   SFG_FIELD_KEYS      uint64 [n]        sorted Morton keys
+ *   SFG_FIELD_ORDER     int32  [n]        sorted rank -> original index
+ *   SFG_FIELD_NODE_INT  int32  [nn][16]   level, first, count, parent, child_first,
+ *                                         nchild, lo[3], hi[3], cq[3], pad
+ *   SFG_FIELD_NODE_HQ   uint64 [nn]       ceil((h_max / cell)^2), capped at 2^62
+ *   SFG_FIELD_NODE_F64  float64 [nn][11]  M, com[3], Q[6] (xx yy zz xy xz yz), h_max
+ * `bytes` must equal the field's size. */
+#define SFG_FIELD_KEYS 1
+#define SFG_FIELD_ORDER 2
+#define SFG_FIELD_NODE_INT 3
+#define SFG_FIELD_NODE_HQ 4
+#define SFG_FIELD_NODE_F64 5
+int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes);
+
+/* Interaction lists of every group for the given active set (same walk as
+ * sfg_accel), copied to HOST memory.  First call with NULL arrays to get
+ * *n_groups, *n_p2m_total and *n_p2p_total; then call again with
+ *   groups [n_groups][4] int64: first target (rank in the sorted list of
+ *          distinct active particles), target count, P2M list length, P2P
+ *          list length (leaves)
+ *   p2m    [n_p2m_total] int32 accepted node ids, group after group
+ *   p2p    [n_p2p_total] int32 opened leaf ids, group after group
+ * Each group's entries come in walk order. */
+int sfg_debug_lists(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, int64_t *n_groups,
+                    int64_t *n_p2m_total, int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFG_H */

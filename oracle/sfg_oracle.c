@@ -237,7 +237,8 @@ static uint64_t hq_of(double h, double scale)
     double v = h * scale;
     double v2 = v * v;
     if (!(v2 < 4611686018427387904.0)) return CAP62;
-    return (uint64_t)ceil(v2);
+    uint64_t c = (uint64_t)ceil(v2);
+    return c > 0 ? c : 1u; /* >= 1: a node touching a target's cell is always opened */
 }
 
 typedef struct { uint64_t key; int64_t idx; } kv;
@@ -554,10 +555,23 @@ static void walk_group(const sfgo_tree *t, const ogroup *g, int64_t ni, const ui
     }
 }
 
-/* Groups: a node with 1..G active targets whose parent holds more than G
- * (or the root); a leaf holding more than G is cut into runs of G.  Then
- * every group (or, if need != NULL, only groups holding a listed original
- * index) is walked from the root.  Returns the number of groups. */
+/* Groups of <= G active targets, contiguous in sorted (Morton) order:
+ *   - the root, if it holds 1..G targets;
+ *   - under every internal node holding more than G targets, its children
+ *     that hold 1..G targets are packed greedily, in octant order, into runs
+ *     of at most G targets (a child holding more than G is not packed: if it
+ *     is internal its own children are packed, if it is a leaf it is cut);
+ *   - a leaf holding more than G targets is cut into runs of G.
+ * Groups are numbered by their first target (Morton order).  Every group (or,
+ * if need != NULL, only the groups holding a listed original index) is then
+ * walked from the root.  Returns the number of groups. */
+typedef struct { int64_t tfirst, tcount, node; } grun;
+static int grun_cmp(const void *a, const void *b)
+{
+    const grun *x = (const grun *)a, *y = (const grun *)b;
+    return (x->tfirst > y->tfirst) - (x->tfirst < y->tfirst);
+}
+
 int64_t sfgo_walk(sfgo_tree *t, const int64_t *active, int64_t n_active, int gsize, double theta,
                   const int64_t *need, int64_t n_need)
 {
@@ -570,52 +584,82 @@ int64_t sfgo_walk(sfgo_tree *t, const int64_t *active, int64_t n_active, int gsi
     int64_t *pre = (int64_t *)malloc(8 * (n + 1));
     pre[0] = 0;
     for (int64_t r = 0; r < n; r++) pre[r + 1] = pre[r] + act[r];
-    t->tgt = (int64_t *)malloc(8 * (pre[n] > 0 ? pre[n] : 1));
+    int64_t U = pre[n];
+    t->tgt = (int64_t *)malloc(8 * (U > 0 ? U : 1));
+    for (int64_t r = 0, k = 0; r < n; r++)
+        if (act[r]) t->tgt[k++] = r;
     t->tgroup = (int64_t *)malloc(8 * n);
     for (int64_t r = 0; r < n; r++) t->tgroup[r] = -1;
-    int64_t gcap = 64, ng = 0, nt = 0;
-    t->groups = (ogroup *)calloc(gcap, sizeof(ogroup));
+
+    int64_t rcap = 64, nr = 0;
+    grun *runs = (grun *)malloc(sizeof(grun) * rcap);
+#define EMIT(tf, tc, nd)                                                   \
+    do {                                                                   \
+        if (nr == rcap) {                                                  \
+            rcap *= 2;                                                     \
+            runs = (grun *)realloc(runs, sizeof(grun) * rcap);             \
+        }                                                                  \
+        runs[nr].tfirst = (tf);                                            \
+        runs[nr].tcount = (tc);                                            \
+        runs[nr].node = (nd);                                              \
+        nr++;                                                              \
+    } while (0)
     for (int64_t i = 0; i < t->nn; i++) {
         const onode *nd = &t->nodes[i];
         int64_t c = pre[nd->first + nd->count] - pre[nd->first];
         if (c == 0) continue;
-        if (i != 0) {
-            const onode *p = &t->nodes[nd->parent];
-            if (pre[p->first + p->count] - pre[p->first] <= gsize) continue;
+        if (i == 0 && c <= gsize) EMIT(pre[nd->first], c, i);
+        if (c > gsize && nd->nchild == 0 && i == 0)
+            for (int64_t s = 0; s < c; s += gsize) EMIT(pre[nd->first] + s, (c - s) < gsize ? (c - s) : gsize, i);
+        if (c <= gsize || nd->nchild == 0) continue;
+        int64_t run_first = -1, run_count = 0;
+        for (int k = 0; k < nd->nchild; k++) {
+            const onode *ch = &t->nodes[nd->child_first + k];
+            int64_t tf = pre[ch->first];
+            int64_t cc = pre[ch->first + ch->count] - tf;
+            if (cc == 0) continue;
+            if (cc > gsize) {
+                if (run_count) EMIT(run_first, run_count, i);
+                run_count = 0;
+                if (ch->nchild == 0)
+                    for (int64_t s = 0; s < cc; s += gsize) EMIT(tf + s, (cc - s) < gsize ? (cc - s) : gsize, i);
+                continue;
+            }
+            if (run_count + cc > gsize) {
+                EMIT(run_first, run_count, i);
+                run_count = 0;
+            }
+            if (run_count == 0) run_first = tf;
+            run_count += cc;
         }
-        if (c > gsize && nd->nchild != 0) continue;
-        /* targets of this node in sorted order, cut into runs of <= gsize */
-        int64_t k0 = nt;
-        for (int64_t r = nd->first; r < nd->first + nd->count; r++)
-            if (act[r]) t->tgt[nt++] = r;
-        for (int64_t s = k0; s < nt; s += gsize) {
-            if (ng == gcap) {
-                gcap *= 2;
-                t->groups = (ogroup *)realloc(t->groups, sizeof(ogroup) * gcap);
-            }
-            ogroup *g = &t->groups[ng];
-            memset(g, 0, sizeof(ogroup));
-            g->node = i;
-            g->tfirst = s;
-            g->tcount = (nt - s) < gsize ? (nt - s) : gsize;
+        if (run_count) EMIT(run_first, run_count, i);
+    }
+#undef EMIT
+    qsort(runs, (size_t)nr, sizeof(grun), grun_cmp);
+    int64_t ng = nr;
+    t->groups = (ogroup *)calloc(ng > 0 ? ng : 1, sizeof(ogroup));
+    for (int64_t g = 0; g < ng; g++) {
+        ogroup *G = &t->groups[g];
+        G->node = runs[g].node;
+        G->tfirst = runs[g].tfirst;
+        G->tcount = runs[g].tcount;
+        for (int a = 0; a < 3; a++) {
+            G->lo[a] = GRID_MAX;
+            G->hi[a] = 0;
+        }
+        G->hq = 0;
+        for (int64_t k = G->tfirst; k < G->tfirst + G->tcount; k++) {
+            int64_t r = t->tgt[k];
+            t->tgroup[r] = g;
             for (int a = 0; a < 3; a++) {
-                g->lo[a] = GRID_MAX;
-                g->hi[a] = 0;
+                if (t->q[3 * r + a] < G->lo[a]) G->lo[a] = t->q[3 * r + a];
+                if (t->q[3 * r + a] > G->hi[a]) G->hi[a] = t->q[3 * r + a];
             }
-            g->hq = 0;
-            for (int64_t k = s; k < s + g->tcount; k++) {
-                int64_t r = t->tgt[k];
-                t->tgroup[r] = ng;
-                for (int a = 0; a < 3; a++) {
-                    if (t->q[3 * r + a] < g->lo[a]) g->lo[a] = t->q[3 * r + a];
-                    if (t->q[3 * r + a] > g->hi[a]) g->hi[a] = t->q[3 * r + a];
-                }
-                uint64_t h = hq_of(t->soft[r], t->scale);
-                if (h > g->hq) g->hq = h;
-            }
-            ng++;
+            uint64_t h = hq_of(t->soft[r], t->scale);
+            if (h > G->hq) G->hq = h;
         }
     }
+    free(runs);
     t->ng = ng;
     uint64_t T[LMAX + 1];
     for (int l = 0; l <= LMAX; l++) T[l] = open_threshold(l, theta);

@@ -1,0 +1,249 @@
+// api.cu -- the extern "C" entry points declared in include/sfg.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "sfg_internal.cuh"
+
+struct sfg_tree {
+    sfg::Tree t;
+};
+
+namespace sfg {
+
+void *dev_alloc(Tree *t, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (t->prm.alloc) {
+        p = t->prm.alloc(bytes, (void *)s, t->prm.alloc_ctx);
+    } else if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) t->live.insert(p);
+    return p;
+}
+
+void dev_free(Tree *t, void *p, cudaStream_t s)
+{
+    if (!p) return;
+    t->live.erase(p);
+    if (t->prm.alloc) {
+        if (t->prm.free) t->prm.free(p, (void *)s, t->prm.alloc_ctx);
+    } else {
+        cudaFreeAsync(p, s);
+    }
+}
+
+} // namespace sfg
+
+using namespace sfg;
+
+static void release(sfg_tree *T)
+{
+    Tree *t = &T->t;
+    cudaStreamSynchronize(t->stream);
+    std::vector<void *> ptrs(t->live.begin(), t->live.end());
+    for (void *p : ptrs) dev_free(t, p, t->stream);
+    cudaStreamSynchronize(t->stream);
+    delete T;
+}
+
+extern "C" {
+
+void sfg_default_params(sfg_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->G = 1.0;
+    p->theta = 0.5;
+    p->leaf_size = 16;
+    p->group_size = 32;
+    p->list_depth = 0;
+    p->quadrupole = 1;
+    p->precision = 0;
+    p->store_lists = 0;
+}
+
+const char *sfg_status_string(int st)
+{
+    switch (st) {
+    case SFG_OK: return "SFG_OK";
+    case SFG_EINVAL: return "SFG_EINVAL: invalid argument or input value";
+    case SFG_ENOMEM: return "SFG_ENOMEM: device allocation failed";
+    case SFG_ECUDA: return "SFG_ECUDA: CUDA runtime error";
+    case SFG_EOVERFLOW: return "SFG_EOVERFLOW: traversal buffer overflow after retry";
+    case SFG_ETIMEOUT: return "SFG_ETIMEOUT: bounded device wait expired";
+    default: return "unknown sfg status";
+    }
+}
+
+int sfg_build(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink, int64_t n,
+              const sfg_params *params, void *stream, sfg_tree **out)
+{
+    if (!out) return SFG_EINVAL;
+    *out = nullptr;
+    if (!pos || !mass || !soft || n <= 0 || n >= 0x7fffffffLL) return SFG_EINVAL;
+    sfg_params p;
+    if (params) p = *params;
+    else sfg_default_params(&p);
+    if (!(isfinite(p.G)) || !(p.theta >= 0.0) || !isfinite(p.theta) || p.leaf_size < 1 || p.leaf_size > 256 ||
+        p.group_size < 1 || p.group_size > 32 || (p.quadrupole != 0 && p.quadrupole != 1) ||
+        (p.precision != 0 && p.precision != 1) || (p.alloc && !p.free))
+        return SFG_EINVAL;
+    sfg_tree *T = new sfg_tree;
+    T->t.prm = p;
+    T->t.n = n;
+    T->t.stream = (cudaStream_t)stream;
+    int rc = build_tree(&T->t, pos, mass, soft, is_sink, (cudaStream_t)stream);
+    if (rc != SFG_OK) {
+        cudaGetLastError();
+        release(T);
+        return rc;
+    }
+    T->t.last.n = n;
+    *out = T;
+    return SFG_OK;
+}
+
+int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi, void *stream)
+{
+    if (!tree || n_active < 0 || (n_active > 0 && !accel)) return SFG_EINVAL;
+    tree->t.stream = (cudaStream_t)stream;
+    return sfg::accel(&tree->t, active_idx, n_active, accel, phi, (cudaStream_t)stream);
+}
+
+int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
+                  const double *cot_phi, double *d_pos, double *d_mass, void *stream)
+{
+    if (!tree || n_active < 0 || !d_pos || !d_mass || (n_active > 0 && !cot_a)) return SFG_EINVAL;
+    tree->t.stream = (cudaStream_t)stream;
+    return sfg::accel_vjp(&tree->t, active_idx, n_active, cot_a, cot_phi, d_pos, d_mass, (cudaStream_t)stream);
+}
+
+int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
+{
+    if (!tree || !out) return SFG_EINVAL;
+    Tree *t = &tree->t;
+    unsigned long long c[8];
+    if (cudaMemcpyAsync(c, t->d_counters, sizeof(c), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+        cudaStreamSynchronize(t->stream) != cudaSuccess)
+        return SFG_ECUDA;
+    sfg_stats s;
+    memset(&s, 0, sizeof(s));
+    s.n = t->n;
+    s.n_nodes = t->nn;
+    s.depth = t->depth;
+    s.n_levels = t->n_levels;
+    for (int a = 0; a < 3; a++) s.x0[a] = t->frame_h.x0[a];
+    s.L0 = t->frame_h.L0;
+    s.n_p2p = (int64_t)c[0];
+    s.n_p2m = (int64_t)c[1];
+    s.n_overflow = (int64_t)c[2];
+    s.n_groups = (int64_t)(*(int *)&c[5]);
+    s.n_targets = (int64_t)c[6];
+    *out = s;
+    return SFG_OK;
+}
+
+int sfg_get_status(sfg_tree *tree)
+{
+    if (!tree) return SFG_EINVAL;
+    Tree *t = &tree->t;
+    int st = 0;
+    if (cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+        cudaStreamSynchronize(t->stream) != cudaSuccess)
+        return SFG_ECUDA;
+    if (st) cudaMemsetAsync(t->d_status, 0, sizeof(int), t->stream);
+    if (st & ST_EINVAL) return SFG_EINVAL;
+    if (st & ST_EOVERFLOW) return SFG_EOVERFLOW;
+    if (st & ST_ETIMEOUT) return SFG_ETIMEOUT;
+    return SFG_OK;
+}
+
+void sfg_free(sfg_tree *tree)
+{
+    if (tree) release(tree);
+}
+
+int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
+{
+    if (!tree || !host_dst) return SFG_EINVAL;
+    Tree *t = &tree->t;
+    cudaStream_t s = t->stream;
+    const size_t n = (size_t)t->n, nn = (size_t)t->nn;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SFG_ECUDA;
+    switch (field) {
+    case SFG_FIELD_KEYS:
+        if (bytes != 8 * n) return SFG_EINVAL;
+        SFG_CUDA_OK(cudaMemcpy(host_dst, t->key, bytes, cudaMemcpyDeviceToHost));
+        return SFG_OK;
+    case SFG_FIELD_ORDER:
+        if (bytes != 4 * n) return SFG_EINVAL;
+        SFG_CUDA_OK(cudaMemcpy(host_dst, t->order, bytes, cudaMemcpyDeviceToHost));
+        return SFG_OK;
+    case SFG_FIELD_NODE_HQ:
+        if (bytes != 8 * nn) return SFG_EINVAL;
+        SFG_CUDA_OK(cudaMemcpy(host_dst, t->Whq, bytes, cudaMemcpyDeviceToHost));
+        return SFG_OK;
+    case SFG_FIELD_NODE_INT: {
+        if (bytes != 64 * nn) return SFG_EINVAL;
+        std::vector<int32_t> a(6 * nn);
+        std::vector<int4> w(3 * nn);
+        SFG_CUDA_OK(cudaMemcpy(&a[0], t->nlevel, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&a[nn], t->nfirst, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&a[2 * nn], t->ncount, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&a[3 * nn], t->nparent, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&a[4 * nn], t->nchild_first, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&a[5 * nn], t->nnchild, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&w[0], t->W0, 16 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&w[nn], t->W1, 16 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&w[2 * nn], t->W2, 16 * nn, cudaMemcpyDeviceToHost));
+        int32_t *o = (int32_t *)host_dst;
+        for (size_t i = 0; i < nn; i++) {
+            int32_t *r = o + 16 * i;
+            for (int k = 0; k < 6; k++) r[k] = a[k * nn + i];
+            int4 w0 = w[i], w1 = w[nn + i], w2 = w[2 * nn + i];
+            r[6] = w0.x; r[7] = w0.y; r[8] = w0.z;
+            r[9] = w1.x; r[10] = w1.y; r[11] = w1.z;
+            r[12] = w2.x; r[13] = w2.y; r[14] = w2.z;
+            r[15] = 0;
+        }
+        return SFG_OK;
+    }
+    case SFG_FIELD_NODE_F64: {
+        if (bytes != 88 * nn) return SFG_EINVAL;
+        std::vector<double> M(nn), com(3 * nn), Q(6 * nn), h(nn);
+        SFG_CUDA_OK(cudaMemcpy(M.data(), t->nM, 8 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(com.data(), t->ncom, 24 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(Q.data(), t->nQ, 48 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(h.data(), t->nhmax, 8 * nn, cudaMemcpyDeviceToHost));
+        double *o = (double *)host_dst;
+        for (size_t i = 0; i < nn; i++) {
+            double *r = o + 11 * i;
+            r[0] = M[i];
+            for (int a = 0; a < 3; a++) r[1 + a] = com[3 * i + a];
+            for (int k = 0; k < 6; k++) r[4 + k] = Q[6 * i + k];
+            r[10] = h[i];
+        }
+        return SFG_OK;
+    }
+    default: return SFG_EINVAL;
+    }
+}
+
+int sfg_debug_lists(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, int64_t *n_groups,
+                    int64_t *n_p2m_total, int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p,
+                    void *stream)
+{
+    if (!tree || !n_groups || !n_p2m_total || !n_p2p_total || n_active < 0) return SFG_EINVAL;
+    tree->t.stream = (cudaStream_t)stream;
+    return sfg::debug_lists(&tree->t, active_idx, n_active, n_groups, n_p2m_total, n_p2p_total, groups, p2m, p2p,
+                            (cudaStream_t)stream);
+}
+
+} // extern "C"

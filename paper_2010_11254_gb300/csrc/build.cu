@@ -1,0 +1,759 @@
+// build.cu -- tree construction on the GPU (STARFORGE methods paper, Sec. 2.2:
+// the oct-tree that recursively subdivides the domain; node multipoles).
+//
+// Steps (one CUDA stream, all device-side; sfg_build synchronizes once):
+//   1. validate inputs and reduce per-axis min/max (FP64 values compared as
+//      order-preserving 64-bit integers: exact and order-free);
+//   2. frame: origin x0 = per-axis minimum, root side L0 = smallest power of
+//      two >= the largest extent;
+//   3. keys: cell q = floor((x - x0) 2^21 / L0) per axis (clamped), 63-bit
+//      Morton key, value = original index;
+//   4. stable LSD radix sort of (key, index), 8 passes of 8 bits;
+//   5. gather sorted FP64 particle arrays;
+//   6. octree, one level at a time: a node with > N_leaf particles below
+//      level 21 is split into its non-empty octants (binary search of the
+//      child digit in the node's sorted key range); node ids are breadth-first;
+//   7. moments, bottom-up in one launch: leaves sum their members in sorted
+//      order, the last child to finish combines its siblings in octant order
+//      (parallel-axis theorem).  The operation order is fixed and this file
+//      is compiled without FMA contraction, so the FP64 moments are
+//      reproducible bit for bit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "sfg_internal.cuh"
+
+namespace sfg {
+
+// ---------------------------------------------------------------- scans ----
+constexpr int SCAN_NB = 512;
+constexpr int SCAN_BT = 256;
+
+__device__ inline int warp_incl_scan(int v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Inclusive block scan; returns the block total in *total.  Uses sh[32].
+__device__ inline int block_incl_scan(int v, int *sh, int *total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = warp_incl_scan(v);
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < nw ? sh[lane] : 0;
+        s = warp_incl_scan(s);
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    int pre = w > 0 ? sh[w - 1] : 0;
+    *total = sh[nw - 1];
+    __syncthreads();
+    return x + pre;
+}
+
+__device__ inline int scan_len(const int *d_lo, const int *d_hi) { return *d_hi - (d_lo ? *d_lo : 0); }
+
+__global__ void k_scan_reduce(const int *in, const int *d_lo, const int *d_hi, int max_n, int *bsum)
+{
+    __shared__ int sh[32];
+    int n = min(scan_len(d_lo, d_hi), max_n);
+    int chunk = (n + SCAN_NB - 1) / SCAN_NB;
+    int b0 = min(n, blockIdx.x * chunk), b1 = min(n, b0 + chunk);
+    int s = 0;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += in[i];
+    int tot;
+    block_incl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int *bsum, const int *d_lo, const int *d_hi, int max_n, int *out, int *extra_dst,
+                           const int *extra_base)
+{
+    __shared__ int sh[32];
+    int v = bsum[threadIdx.x];
+    int tot;
+    int incl = block_incl_scan(v, sh, &tot);
+    bsum[threadIdx.x] = incl - v;
+    if (threadIdx.x == 0) {
+        int n = min(scan_len(d_lo, d_hi), max_n);
+        out[n] = tot;
+        if (extra_dst) *extra_dst = *extra_base + tot;
+    }
+}
+
+__global__ void k_scan_down(const int *in, int *out, const int *d_lo, const int *d_hi, int max_n, const int *bsum)
+{
+    __shared__ int sh[32];
+    int n = min(scan_len(d_lo, d_hi), max_n);
+    int chunk = (n + SCAN_NB - 1) / SCAN_NB;
+    int b0 = min(n, blockIdx.x * chunk), b1 = min(n, b0 + chunk);
+    int carry = bsum[blockIdx.x];
+    for (int base = b0; base < b1; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < b1 ? in[i] : 0;
+        int tot;
+        int incl = block_incl_scan(v, sh, &tot);
+        if (i < b1) out[i] = carry + incl - v;
+        carry += tot;
+    }
+}
+
+size_t scan_scratch_bytes() { return SCAN_NB * sizeof(int); }
+
+// Range-length form: n = *d_hi - *d_lo (d_lo may be NULL).
+static void scan_range(const int *in, int *out, const int *d_lo, const int *d_hi, int max_n, int *extra_dst,
+                       const int *extra_base, void *scratch, cudaStream_t s)
+{
+    int *bsum = (int *)scratch;
+    k_scan_reduce<<<SCAN_NB, SCAN_BT, 0, s>>>(in, d_lo, d_hi, max_n, bsum);
+    k_scan_top<<<1, SCAN_NB, 0, s>>>(bsum, d_lo, d_hi, max_n, out, extra_dst, extra_base);
+    k_scan_down<<<SCAN_NB, SCAN_BT, 0, s>>>(in, out, d_lo, d_hi, max_n, bsum);
+}
+
+void scan_exclusive(const int *in, int *out, const int *d_n, int max_n, int *extra_dst, const int *extra_base,
+                    void *scratch, cudaStream_t s)
+{
+    scan_range(in, out, nullptr, d_n, max_n, extra_dst, extra_base, scratch, s);
+}
+
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+__global__ void k_set_int(int *p, int v) { *p = v; }
+
+// ------------------------------------------------------ validate + frame ----
+__device__ inline unsigned long long ord_of(double x)
+{
+    long long b = __double_as_longlong(x);
+    return b >= 0 ? (unsigned long long)b ^ 0x8000000000000000ull : ~(unsigned long long)b;
+}
+__device__ inline double from_ord(unsigned long long u)
+{
+    long long b = (u & 0x8000000000000000ull) ? (long long)(u ^ 0x8000000000000000ull) : (long long)~u;
+    return __longlong_as_double(b);
+}
+
+__global__ void k_minmax_init(unsigned long long *mm)
+{
+    if (threadIdx.x < 3) mm[threadIdx.x] = ~0ull;
+    else if (threadIdx.x < 6) mm[threadIdx.x] = 0ull;
+}
+
+__global__ void k_validate_minmax(const double *pos, const double *mass, const double *soft, int n,
+                                  unsigned long long *mm, int *status)
+{
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; a++) {
+            double x = pos[3 * (size_t)i + a];
+            if (!isfinite(x)) bad = true;
+            unsigned long long u = ord_of(x);
+            lo[a] = u < lo[a] ? u : lo[a];
+            hi[a] = u > hi[a] ? u : hi[a];
+        }
+        double m = mass[i], h = soft[i];
+        if (!(m >= 0.0) || !isfinite(m) || !(h > 0.0) || !isfinite(h)) bad = true;
+    }
+    for (int a = 0; a < 3; a++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo[a], o);
+            unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi[a], o);
+            lo[a] = l2 < lo[a] ? l2 : lo[a];
+            hi[a] = h2 > hi[a] ? h2 : hi[a];
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[a], lo[a]);
+            atomicMax(&mm[3 + a], hi[a]);
+        }
+    }
+    if (bad) atomicOr(status, ST_EINVAL);
+}
+
+__global__ void k_frame(const unsigned long long *mm, Frame *fr, int *status)
+{
+    double E = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double lo = from_ord(mm[a]), hi = from_ord(mm[3 + a]);
+        fr->x0[a] = lo;
+        double e = hi - lo;
+        if (e > E) E = e;
+    }
+    double L0;
+    if (E == 0.0) {
+        L0 = 1.0;
+    } else {
+        long long b = __double_as_longlong(E);
+        int ex = (int)((b >> 52) & 0x7ff);
+        long long mant = b & 0xfffffffffffffll;
+        if (ex == 0 || ex >= 0x7fe) {
+            atomicOr(status, ST_EINVAL); // subnormal or huge extent: outside the supported domain
+            L0 = 1.0;
+        } else {
+            L0 = mant == 0 ? E : ldexp(1.0, ex - 1023 + 1);
+        }
+    }
+    fr->L0 = L0;
+    fr->scale = ldexp(1.0, SFG_LMAX) / L0;
+    fr->half_cell = ldexp(L0, -22);
+}
+
+// ------------------------------------------------------------------ keys ----
+__global__ void k_keys(const double *pos, int n, const Frame *fr, uint64_t *key, uint32_t *val)
+{
+    const double x0 = fr->x0[0], y0 = fr->x0[1], z0 = fr->x0[2], sc = fr->scale;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t qx = cell_of(pos[3 * (size_t)i], x0, sc);
+        uint32_t qy = cell_of(pos[3 * (size_t)i + 1], y0, sc);
+        uint32_t qz = cell_of(pos[3 * (size_t)i + 2], z0, sc);
+        key[i] = morton3(qx, qy, qz);
+        val[i] = (uint32_t)i;
+    }
+}
+
+// ------------------------------------------------------------ radix sort ----
+constexpr int RS_WARPS = 8;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_WARPS * 32 * RS_ITEMS; // 4096
+
+__global__ void __launch_bounds__(RS_WARPS * 32) k_rs_hist(const uint64_t *key, int n, int shift, int *hist, int nb)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * RS_TILE, end = min(n, base + RS_TILE);
+    for (int i = base + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&h[(key[i] >> shift) & 255], 1);
+    __syncthreads();
+    hist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_WARPS * 32)
+    k_rs_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n, int shift,
+                 const int *off, int nb)
+{
+    __shared__ int wcnt[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t k[RS_ITEMS];
+    uint32_t v[RS_ITEMS];
+    int dg[RS_ITEMS], loc[RS_ITEMS];
+    int base = blockIdx.x * RS_TILE + w * 32 * RS_ITEMS;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        int i = base + r * 32 + lane;
+        bool valid = i < n;
+        k[r] = valid ? kin[i] : 0;
+        v[r] = valid ? vin[i] : 0;
+        int d = valid ? (int)((k[r] >> shift) & 255) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = __popc(peers & lt);
+        int c0 = valid ? wcnt[w][d] : 0;
+        __syncwarp();
+        if (valid && (31 - __clz(peers)) == lane) wcnt[w][d] = c0 + __popc(peers);
+        __syncwarp();
+        dg[r] = d;
+        loc[r] = c0 + before;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps (thread t owns digit t)
+    {
+        int d = threadIdx.x;
+        int run = 0;
+        for (int ww = 0; ww < RS_WARPS; ww++) {
+            int c = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        if (dg[r] < 256) {
+            int p = off[dg[r] * nb + blockIdx.x] + wcnt[w][dg[r]] + loc[r];
+            kout[p] = k[r];
+            vout[p] = v[r];
+        }
+    }
+}
+
+
+// --------------------------------------------------------------- gather ----
+__global__ void k_pack(const double *pos, const double *mass, const double *soft, const uint8_t *sink, int n,
+                       const uint32_t *val, int32_t *order, int32_t *rank, double *pos_s, double *mass_s,
+                       double *soft_s, uint8_t *sink_s)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        int i = (int)val[r];
+        order[r] = i;
+        rank[i] = r;
+        pos_s[3 * (size_t)r] = pos[3 * (size_t)i];
+        pos_s[3 * (size_t)r + 1] = pos[3 * (size_t)i + 1];
+        pos_s[3 * (size_t)r + 2] = pos[3 * (size_t)i + 2];
+        mass_s[r] = mass[i];
+        soft_s[r] = soft[i];
+        sink_s[r] = sink ? (uint8_t)(sink[i] != 0) : (uint8_t)0;
+    }
+}
+
+// --------------------------------------------------------------- octree ----
+// First index k in [lo, hi) with child digit(key[k]) >= d (digits are
+// non-decreasing inside one node's range).
+__device__ inline int lower_digit(const uint64_t *key, int lo, int hi, int cshift, uint32_t d)
+{
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (((key[mid] >> cshift) & 7u) < d) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_oct_root(int n, int32_t *nfirst, int32_t *ncount, int32_t *nparent, int32_t *nlevel, int *lvl)
+{
+    nfirst[0] = 0;
+    ncount[0] = n;
+    nparent[0] = -1;
+    nlevel[0] = 0;
+    lvl[0] = 0;
+    lvl[1] = 1;
+}
+
+__global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int leaf_size, int cap,
+                            const int32_t *nfirst, const int32_t *ncount, int *tmp, int *status)
+{
+    int b = lvl[level], e = lvl[level + 1];
+    if (e > cap) {
+        e = cap;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_NODECAP);
+    }
+    for (int node = b + blockIdx.x * blockDim.x + threadIdx.x; node < e; node += gridDim.x * blockDim.x) {
+        int f = nfirst[node], c = ncount[node];
+        int nch = 0;
+        if (c > leaf_size && level < SFG_LMAX) {
+            int cshift = 3 * (SFG_LMAX - level - 1);
+            int prev = f;
+            for (uint32_t d = 1; d <= 8; d++) {
+                int s = d < 8 ? lower_digit(key, prev, f + c, cshift, d) : f + c;
+                if (s > prev) nch++;
+                prev = s;
+            }
+        }
+        tmp[node - b] = nch;
+    }
+}
+
+__global__ void k_oct_write(const uint64_t *key, const int *lvl, int level, int leaf_size, int cap, int32_t *nfirst,
+                            int32_t *ncount, int32_t *nparent, int32_t *nchild_first, int32_t *nnchild,
+                            int32_t *nlevel, const int *tmp_off, int *status)
+{
+    int b = lvl[level], e = min(lvl[level + 1], cap);
+    int next = lvl[level + 1];
+    for (int node = b + blockIdx.x * blockDim.x + threadIdx.x; node < e; node += gridDim.x * blockDim.x) {
+        int f = nfirst[node], c = ncount[node];
+        if (!(c > leaf_size && level < SFG_LMAX)) {
+            nchild_first[node] = -1;
+            nnchild[node] = 0;
+            continue;
+        }
+        int cshift = 3 * (SFG_LMAX - level - 1);
+        int cf = next + tmp_off[node - b];
+        int k = 0, prev = f;
+        for (uint32_t d = 1; d <= 8; d++) {
+            int s = d < 8 ? lower_digit(key, prev, f + c, cshift, d) : f + c;
+            if (s > prev) {
+                int id = cf + k;
+                if (id < cap) {
+                    nfirst[id] = prev;
+                    ncount[id] = s - prev;
+                    nparent[id] = node;
+                    nlevel[id] = level + 1;
+                } else {
+                    atomicOr(status, ST_NODECAP);
+                }
+                k++;
+            }
+            prev = s;
+        }
+        nchild_first[node] = cf;
+        nnchild[node] = k;
+    }
+}
+
+// -------------------------------------------------------------- moments ----
+struct MomArgs {
+    const uint64_t *key;
+    const double *pos, *mass, *soft;
+    const uint8_t *sink;
+    const int32_t *nfirst, *ncount, *nparent, *nchild_first, *nnchild, *nlevel;
+    const Frame *fr;
+    int4 *W0, *W1, *W2;
+    unsigned long long *Whq;
+    float4 *E0, *E1, *E2;
+    double *nM, *ncom, *nQ, *nhmax;
+    float4 *pw;
+    int4 *pc;
+    int *arrive;
+    int nn;
+};
+
+__device__ inline void node_centre(const Frame &fr, const uint32_t lo[3], int level, int ci[3], double c[3])
+{
+    int sh = SFG_LMAX - level;
+    for (int a = 0; a < 3; a++) {
+        uint32_t corner = (lo[a] >> sh) << sh;
+        ci[a] = (int)(2u * corner + (1u << sh));
+        c[a] = fr.x0[a] + (double)(2u * corner + (1u << sh)) * fr.half_cell;
+    }
+}
+
+__device__ inline void write_records(const MomArgs &A, const Frame &fr, int node, int level, bool leaf, int link,
+                                     int cnt, const uint32_t lo[3], const uint32_t hi[3], double M,
+                                     const double com[3], const double Q[6], double hmax, const double c[3],
+                                     const int ci[3])
+{
+    uint32_t cq[3];
+    for (int a = 0; a < 3; a++) cq[a] = cell_of(com[a], fr.x0[a], fr.scale);
+    A.W0[node] = make_int4((int)lo[0], (int)lo[1], (int)lo[2], level | (leaf ? 256 : 0));
+    A.W1[node] = make_int4((int)hi[0], (int)hi[1], (int)hi[2], link);
+    A.W2[node] = make_int4((int)cq[0], (int)cq[1], (int)cq[2], cnt);
+    A.Whq[node] = hq_of(hmax, fr.scale);
+    A.E0[node] = make_float4((float)(com[0] - c[0]), (float)(com[1] - c[1]), (float)(com[2] - c[2]), (float)M);
+    A.E1[node] = make_float4((float)Q[0], (float)Q[1], (float)Q[3], (float)Q[4]);
+    A.E2[node] = make_float4((float)Q[5], __int_as_float(ci[0]), __int_as_float(ci[1]), __int_as_float(ci[2]));
+    A.nM[node] = M;
+    for (int a = 0; a < 3; a++) A.ncom[3 * (size_t)node + a] = com[a];
+    for (int k = 0; k < 6; k++) A.nQ[6 * (size_t)node + k] = Q[k];
+    A.nhmax[node] = hmax;
+}
+
+__device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
+{
+    const int f = A.nfirst[node], c = A.ncount[node], level = A.nlevel[node];
+    uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
+    double M = 0.0, s[3] = {0.0, 0.0, 0.0}, hmax = 0.0;
+    for (int k = f; k < f + c; k++) M = M + A.mass[k];
+    for (int k = f; k < f + c; k++) {
+        double m = A.mass[k];
+        for (int a = 0; a < 3; a++) s[a] = s[a] + m * A.pos[3 * (size_t)k + a];
+        uint64_t key = A.key[k];
+        uint32_t q[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
+        for (int a = 0; a < 3; a++) {
+            lo[a] = q[a] < lo[a] ? q[a] : lo[a];
+            hi[a] = q[a] > hi[a] ? q[a] : hi[a];
+        }
+        double h = A.soft[k];
+        if (h > hmax) hmax = h;
+    }
+    int ci[3];
+    double cen[3], com[3];
+    node_centre(fr, lo, level, ci, cen);
+    if (M > 0.0) {
+        for (int a = 0; a < 3; a++) com[a] = s[a] / M;
+    } else {
+        for (int a = 0; a < 3; a++) com[a] = cen[a];
+    }
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = f; k < f + c; k++) {
+        double m = A.mass[k];
+        double x0 = A.pos[3 * (size_t)k], x1 = A.pos[3 * (size_t)k + 1], x2 = A.pos[3 * (size_t)k + 2];
+        double d0 = x0 - com[0], d1 = x1 - com[1], d2 = x2 - com[2];
+        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        Q[0] = Q[0] + m * (3.0 * d0 * d0 - r2);
+        Q[1] = Q[1] + m * (3.0 * d1 * d1 - r2);
+        Q[2] = Q[2] + m * (3.0 * d2 * d2 - r2);
+        Q[3] = Q[3] + m * (3.0 * d0 * d1);
+        Q[4] = Q[4] + m * (3.0 * d0 * d2);
+        Q[5] = Q[5] + m * (3.0 * d1 * d2);
+        // particle record of the walk: FP32 offset from the leaf centre
+        float hs = (float)A.soft[k];
+        if (A.sink[k]) hs = -hs;
+        A.pw[k] = make_float4((float)(x0 - cen[0]), (float)(x1 - cen[1]), (float)(x2 - cen[2]), (float)m);
+        A.pc[k] = make_int4(ci[0], ci[1], ci[2], __float_as_int(hs));
+    }
+    write_records(A, fr, node, level, true, f, c, lo, hi, M, com, Q, hmax, cen, ci);
+}
+
+__device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
+{
+    const int cf = A.nchild_first[node], nc = A.nnchild[node], level = A.nlevel[node];
+    uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
+    double M = 0.0, s[3] = {0.0, 0.0, 0.0}, hmax = 0.0;
+    for (int k = 0; k < nc; k++) M = M + __ldcg(&A.nM[cf + k]);
+    for (int k = 0; k < nc; k++) {
+        int ch = cf + k;
+        double Mc = __ldcg(&A.nM[ch]);
+        for (int a = 0; a < 3; a++) s[a] = s[a] + Mc * __ldcg(&A.ncom[3 * (size_t)ch + a]);
+        int4 w0 = __ldcg(&A.W0[ch]), w1 = __ldcg(&A.W1[ch]);
+        uint32_t l3[3] = {(uint32_t)w0.x, (uint32_t)w0.y, (uint32_t)w0.z};
+        uint32_t h3[3] = {(uint32_t)w1.x, (uint32_t)w1.y, (uint32_t)w1.z};
+        for (int a = 0; a < 3; a++) {
+            lo[a] = l3[a] < lo[a] ? l3[a] : lo[a];
+            hi[a] = h3[a] > hi[a] ? h3[a] : hi[a];
+        }
+        double h = __ldcg(&A.nhmax[ch]);
+        if (h > hmax) hmax = h;
+    }
+    int ci[3];
+    double cen[3], com[3];
+    node_centre(fr, lo, level, ci, cen);
+    if (M > 0.0) {
+        for (int a = 0; a < 3; a++) com[a] = s[a] / M;
+    } else {
+        for (int a = 0; a < 3; a++) com[a] = cen[a];
+    }
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < nc; k++) {
+        int ch = cf + k;
+        double Mc = __ldcg(&A.nM[ch]);
+        double d0 = __ldcg(&A.ncom[3 * (size_t)ch]) - com[0];
+        double d1 = __ldcg(&A.ncom[3 * (size_t)ch + 1]) - com[1];
+        double d2 = __ldcg(&A.ncom[3 * (size_t)ch + 2]) - com[2];
+        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double *Qc = A.nQ + 6 * (size_t)ch;
+        Q[0] = Q[0] + (__ldcg(&Qc[0]) + Mc * (3.0 * d0 * d0 - r2));
+        Q[1] = Q[1] + (__ldcg(&Qc[1]) + Mc * (3.0 * d1 * d1 - r2));
+        Q[2] = Q[2] + (__ldcg(&Qc[2]) + Mc * (3.0 * d2 * d2 - r2));
+        Q[3] = Q[3] + (__ldcg(&Qc[3]) + Mc * (3.0 * d0 * d1));
+        Q[4] = Q[4] + (__ldcg(&Qc[4]) + Mc * (3.0 * d0 * d2));
+        Q[5] = Q[5] + (__ldcg(&Qc[5]) + Mc * (3.0 * d1 * d2));
+    }
+    write_records(A, fr, node, level, false, cf, nc, lo, hi, M, com, Q, hmax, cen, ci);
+}
+
+__global__ void k_moments(MomArgs A)
+{
+    const Frame fr = *A.fr;
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < A.nn; node += gridDim.x * blockDim.x) {
+        if (A.nnchild[node] != 0) continue;
+        leaf_moments(A, fr, node);
+        int cur = node;
+        while (true) {
+            int p = A.nparent[cur];
+            if (p < 0) break;
+            __threadfence();
+            int old = atomicAdd(&A.arrive[p], 1);
+            if (old != A.nnchild[p] - 1) break;
+            __threadfence();
+            internal_moments(A, fr, p);
+            cur = p;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side ----
+static int grid_for(int64_t n, int bt)
+{
+    int64_t g = (n + bt - 1) / bt;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+#define ALLOC(ptr, type, count)                                                                              \
+    do {                                                                                                     \
+        ptr = (type *)dev_alloc(t, sizeof(type) * (size_t)(count), s);                                      \
+        if (!ptr) return SFG_ENOMEM;                                                                         \
+    } while (0)
+
+static int alloc_nodes(Tree *t, int cap, cudaStream_t s)
+{
+    t->cap = cap;
+    ALLOC(t->nfirst, int32_t, cap);
+    ALLOC(t->ncount, int32_t, cap);
+    ALLOC(t->nparent, int32_t, cap);
+    ALLOC(t->nchild_first, int32_t, cap);
+    ALLOC(t->nnchild, int32_t, cap);
+    ALLOC(t->nlevel, int32_t, cap);
+    return SFG_OK;
+}
+
+static void free_nodes(Tree *t, cudaStream_t s)
+{
+    dev_free(t, t->nfirst, s);
+    dev_free(t, t->ncount, s);
+    dev_free(t, t->nparent, s);
+    dev_free(t, t->nchild_first, s);
+    dev_free(t, t->nnchild, s);
+    dev_free(t, t->nlevel, s);
+    t->nfirst = t->ncount = t->nparent = t->nchild_first = t->nnchild = t->nlevel = nullptr;
+}
+
+int build_tree(Tree *t, const double *pos, const double *mass, const double *soft, const uint8_t *is_sink,
+               cudaStream_t s)
+{
+    const int n = (int)t->n;
+    const int BT = 256;
+    ALLOC(t->d_status, int, 1);
+    ALLOC(t->d_frame, Frame, 1);
+    ALLOC(t->d_minmax, unsigned long long, 6);
+    ALLOC(t->d_lvl, int, SFG_LMAX + 3);
+    ALLOC(t->d_counters, unsigned long long, 8);
+    ALLOC(t->d_n, int, 1);
+    k_set_int<<<1, 1, 0, s>>>(t->d_n, n);
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, 8 * sizeof(unsigned long long), s));
+
+    k_minmax_init<<<1, 32, 0, s>>>(t->d_minmax);
+    k_validate_minmax<<<grid_for(n, BT), BT, 0, s>>>(pos, mass, soft, n, t->d_minmax, t->d_status);
+    k_frame<<<1, 1, 0, s>>>(t->d_minmax, t->d_frame, t->d_status);
+
+    // keys + sort
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    ALLOC(k0, uint64_t, n);
+    ALLOC(k1, uint64_t, n);
+    ALLOC(v0, uint32_t, n);
+    ALLOC(v1, uint32_t, n);
+    k_keys<<<grid_for(n, BT), BT, 0, s>>>(pos, n, t->d_frame, k0, v0);
+    const int nb = (n + RS_TILE - 1) / RS_TILE;
+    int *hist, *hoff, *d_hn, *scr;
+    ALLOC(hist, int, 256 * (size_t)nb);
+    ALLOC(hoff, int, 256 * (size_t)nb + 1);
+    ALLOC(d_hn, int, 1);
+    ALLOC(scr, int, scan_scratch_bytes() / sizeof(int));
+    k_set_int<<<1, 1, 0, s>>>(d_hn, 256 * nb);
+    for (int pass = 0; pass < 8; pass++) {
+        int shift = 8 * pass;
+        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(k0, n, shift, hist, nb);
+        scan_exclusive(hist, hoff, d_hn, 256 * nb, nullptr, nullptr, scr, s);
+        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, k1, v1, n, shift, hoff, nb);
+        uint64_t *tk = k0;
+        k0 = k1;
+        k1 = tk;
+        uint32_t *tv = v0;
+        v0 = v1;
+        v1 = tv;
+    }
+    t->key = k0;
+    dev_free(t, k1, s);
+    dev_free(t, hist, s);
+    dev_free(t, hoff, s);
+    dev_free(t, d_hn, s);
+
+    ALLOC(t->order, int32_t, n);
+    ALLOC(t->rank, int32_t, n);
+    ALLOC(t->pos_s, double, 3 * (size_t)n);
+    ALLOC(t->mass_s, double, n);
+    ALLOC(t->soft_s, double, n);
+    ALLOC(t->sink_s, uint8_t, n);
+    ALLOC(t->pw, float4, n);
+    ALLOC(t->pc, int4, n);
+    k_pack<<<grid_for(n, BT), BT, 0, s>>>(pos, mass, soft, is_sink, n, v0, t->order, t->rank, t->pos_s, t->mass_s,
+                                          t->soft_s, t->sink_s);
+    dev_free(t, v0, s);
+    dev_free(t, v1, s);
+
+    // octree, retried with a larger node capacity if the estimate was short
+    int64_t cap64 = 4 * ((int64_t)n / (t->prm.leaf_size + 1)) + 4096;
+    int *tmp = nullptr, *tmpo = nullptr;
+    for (int attempt = 0;; attempt++) {
+        if (cap64 > 0x7fffffff) cap64 = 0x7fffffff;
+        int cap = (int)cap64;
+        int rc = alloc_nodes(t, cap, s);
+        if (rc) return rc;
+        ALLOC(tmp, int, cap + 1);
+        ALLOC(tmpo, int, cap + 1);
+        k_oct_root<<<1, 1, 0, s>>>(n, t->nfirst, t->ncount, t->nparent, t->nlevel, t->d_lvl);
+        for (int level = 0; level <= SFG_LMAX; level++) {
+            k_oct_count<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+                                                         t->ncount, tmp, t->d_status);
+            scan_range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
+                       t->d_lvl + level + 1, scr, s);
+            k_oct_write<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+                                                         t->ncount, t->nparent, t->nchild_first, t->nnchild,
+                                                         t->nlevel, tmpo, t->d_status);
+        }
+        int st = 0;
+        SFG_CUDA_OK(cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SFG_CUDA_OK(cudaMemcpyAsync(t->lvl_off, t->d_lvl, sizeof(int) * (SFG_LMAX + 3), cudaMemcpyDeviceToHost, s));
+        SFG_CUDA_OK(cudaStreamSynchronize(s));
+        SFG_CUDA_OK(cudaGetLastError());
+        dev_free(t, tmp, s);
+        dev_free(t, tmpo, s);
+        if (st & ST_EINVAL) return SFG_EINVAL;
+        if (!(st & ST_NODECAP)) break;
+        free_nodes(t, s);
+        SFG_CUDA_OK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
+        cap64 *= 2;
+        if (attempt > 8) return SFG_ENOMEM;
+    }
+    const int nn = t->lvl_off[SFG_LMAX + 2];
+    t->nn = nn;
+    t->depth = 0;
+    for (int l = 0; l <= SFG_LMAX; l++)
+        if (t->lvl_off[l + 1] > t->lvl_off[l]) t->depth = l;
+    t->n_levels = t->depth + 1;
+
+    ALLOC(t->W0, int4, nn);
+    ALLOC(t->W1, int4, nn);
+    ALLOC(t->W2, int4, nn);
+    ALLOC(t->Whq, unsigned long long, nn);
+    ALLOC(t->E0, float4, nn);
+    ALLOC(t->E1, float4, nn);
+    ALLOC(t->E2, float4, nn);
+    ALLOC(t->nM, double, nn);
+    ALLOC(t->ncom, double, 3 * (size_t)nn);
+    ALLOC(t->nQ, double, 6 * (size_t)nn);
+    ALLOC(t->nhmax, double, nn);
+    int *arrive;
+    ALLOC(arrive, int, nn);
+    SFG_CUDA_OK(cudaMemsetAsync(arrive, 0, sizeof(int) * (size_t)nn, s));
+    MomArgs A;
+    A.key = t->key;
+    A.pos = t->pos_s;
+    A.mass = t->mass_s;
+    A.soft = t->soft_s;
+    A.sink = t->sink_s;
+    A.nfirst = t->nfirst;
+    A.ncount = t->ncount;
+    A.nparent = t->nparent;
+    A.nchild_first = t->nchild_first;
+    A.nnchild = t->nnchild;
+    A.nlevel = t->nlevel;
+    A.fr = t->d_frame;
+    A.W0 = t->W0;
+    A.W1 = t->W1;
+    A.W2 = t->W2;
+    A.Whq = t->Whq;
+    A.E0 = t->E0;
+    A.E1 = t->E1;
+    A.E2 = t->E2;
+    A.nM = t->nM;
+    A.ncom = t->ncom;
+    A.nQ = t->nQ;
+    A.nhmax = t->nhmax;
+    A.pw = t->pw;
+    A.pc = t->pc;
+    A.arrive = arrive;
+    A.nn = nn;
+    k_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);
+    dev_free(t, arrive, s);
+    dev_free(t, scr, s);
+    SFG_CUDA_OK(cudaMemcpyAsync(&t->frame_h, t->d_frame, sizeof(Frame), cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+} // namespace sfg

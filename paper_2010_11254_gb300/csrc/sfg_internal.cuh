@@ -1,0 +1,160 @@
+// sfg_internal.cuh -- internal declarations of libsfg (not part of the ABI).
+//
+// Data layout in HBM (n particles, nn nodes; "sorted" = Morton order):
+//   particles  key[n] u64, order[n] i32 (sorted rank -> original index),
+//              rank[n] i32 (inverse), pos_s[n][3] f64, mass_s[n] f64,
+//              soft_s[n] f64, sink_s[n] u8,
+//              pw[n] float4 = (x - c_leaf (FP32), m),
+//              pc[n] int4   = (leaf centre in half-cells (3 x i32), h bits; h < 0 for sinks)
+//   nodes (breadth-first: ids ordered by (level, first sorted index); the
+//   children of a node are consecutive ids)
+//              nfirst/ncount/nparent/nchild_first/nnchild/nlevel [nn] i32
+//              W0[nn] int4 = (lo.xyz, level | leaf << 8)       } walk record:
+//              W1[nn] int4 = (hi.xyz, leaf ? first : child_first) } integer cell boxes,
+//              W2[nn] int4 = (cq.xyz, leaf ? count : nchild)    } centre-of-mass cell
+//              Whq[nn] u64 = ceil((h_max / cell)^2) capped at 2^62
+//              E0[nn] float4 = (com - c_node (FP32), M)      } FP32 multipole record
+//              E1[nn] float4 = (Qxx, Qyy, Qxy, Qxz)          } (Qzz = -Qxx - Qyy)
+//              E2[nn] float4 = (Qyz, node centre in half-cells as 3 x i32 bits)
+//              nM[nn], ncom[nn][3], nQ[nn][6], nhmax[nn] f64  } FP64 moments
+// Grid: integer cells of side L0 / 2^21 from the frame origin x0; node and
+// group centres are integers in half-cell units, so centre differences are
+// exact in FP32 (|difference| < 2^22).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <unordered_set>
+
+#include "../../include/sfg.h"
+
+#define SFG_LMAX 21
+#define SFG_GRID_MAX 2097151u
+#define SFG_CAP62 4611686018427387904ull
+
+namespace sfg {
+
+// status bits recorded on the device (mapped to SFG_E* on the host)
+enum : int { ST_EINVAL = 1, ST_EOVERFLOW = 2, ST_ETIMEOUT = 4, ST_NODECAP = 8 };
+
+struct Frame {
+    double x0[3];
+    double L0;
+    double scale;     // 2^21 / L0 (exact)
+    double half_cell; // L0 / 2^22 (exact)
+};
+
+struct Tree {
+    sfg_params prm;
+    int64_t n = 0;
+    int nn = 0, cap = 0, depth = 0, n_levels = 0;
+    int lvl_off[SFG_LMAX + 3] = {0};
+    Frame frame_h{};
+    cudaStream_t stream = nullptr;
+    int *d_status = nullptr;
+    Frame *d_frame = nullptr;
+    unsigned long long *d_minmax = nullptr;
+    int *d_lvl = nullptr; // device level offsets [SFG_LMAX + 3]
+    // particles
+    uint64_t *key = nullptr;
+    int32_t *order = nullptr, *rank = nullptr;
+    double *pos_s = nullptr, *mass_s = nullptr, *soft_s = nullptr;
+    uint8_t *sink_s = nullptr;
+    float4 *pw = nullptr;
+    int4 *pc = nullptr;
+    // nodes
+    int32_t *nfirst = nullptr, *ncount = nullptr, *nparent = nullptr, *nchild_first = nullptr,
+            *nnchild = nullptr, *nlevel = nullptr;
+    int4 *W0 = nullptr, *W1 = nullptr, *W2 = nullptr;
+    unsigned long long *Whq = nullptr;
+    float4 *E0 = nullptr, *E1 = nullptr, *E2 = nullptr;
+    double *nM = nullptr, *ncom = nullptr, *nQ = nullptr, *nhmax = nullptr;
+    // per-call workspace (grow-only)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    sfg_stats last{};
+    // [0] p2p, [1] p2m, [2] overflowed groups, [3] work, [4] retry work, [5] groups, [6] distinct targets
+    unsigned long long *d_counters = nullptr;
+    int *d_n = nullptr; // device copy of n
+    std::unordered_set<void *> live; // every device allocation still held
+};
+
+// ---- memory ----
+void *dev_alloc(Tree *t, size_t bytes, cudaStream_t s);
+void dev_free(Tree *t, void *p, cudaStream_t s);
+
+// ---- build (build.cu) ----
+int build_tree(Tree *t, const double *pos, const double *mass, const double *soft, const uint8_t *is_sink,
+               cudaStream_t s);
+
+// ---- scans (build.cu) ----
+// Exclusive scan of in[0..*d_n) into out[0..*d_n], out[*d_n] = total.  If
+// extra_dst != NULL, *extra_dst = *extra_base + total.  max_n bounds *d_n.
+// Scratch: scan_scratch_bytes() bytes.
+size_t scan_scratch_bytes();
+void scan_exclusive(const int *in, int *out, const int *d_n, int max_n, int *extra_dst, const int *extra_base,
+                    void *scratch, cudaStream_t s);
+
+// ---- forward / adjoint (walk.cu) ----
+int accel(Tree *t, const int64_t *active, int64_t n_active, double *accel, double *phi, cudaStream_t s);
+int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *cot_a, const double *cot_phi,
+              double *d_pos, double *d_mass, cudaStream_t s);
+int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
+                int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s);
+
+int num_sms();
+
+// ---- device helpers ----
+__host__ __device__ inline uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__host__ __device__ inline uint32_t compact3(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+// Morton interleave: bit 3k+2 = x, 3k+1 = y, 3k = z.
+__host__ __device__ inline uint64_t morton3(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
+__device__ inline uint32_t cell_of(double x, double x0, double scale)
+{
+    double s = __dmul_rn(__dsub_rn(x, x0), scale);
+    if (!(s > 0.0)) return 0u;
+    if (s >= 2097152.0) return SFG_GRID_MAX;
+    return (uint32_t)s;
+}
+
+__device__ inline unsigned long long hq_of(double h, double scale)
+{
+    double v = __dmul_rn(h, scale);
+    double v2 = __dmul_rn(v, v);
+    if (!(v2 < 4611686018427387904.0)) return SFG_CAP62;
+    unsigned long long c = (unsigned long long)ceil(v2);
+    return c > 0 ? c : 1ull;
+}
+
+#define SFG_CUDA_OK(expr)                                                                                    \
+    do {                                                                                                     \
+        cudaError_t _e = (expr);                                                                             \
+        if (_e != cudaSuccess) return SFG_ECUDA;                                                             \
+    } while (0)
+
+} // namespace sfg

@@ -1,0 +1,980 @@
+// walk.cu -- field at the active particles (STARFORGE methods paper, Sec. 2.2
+// and 2.2.1) and its adjoint.
+//
+// Groups: the distinct active particles, in Morton order, are cut into runs
+// of <= G targets: under every node holding more than G targets, its
+// children holding 1..G are packed greedily in octant order; a leaf holding
+// more than G is cut; the root forms one group if it holds <= G.
+//
+// One warp walks the tree for one group (persistent warps take groups from
+// an atomic counter).  The walk is a stack of node-id ranges; each round pops
+// up to 32 nodes (one per lane) and applies the opening rule, in exact
+// integer arithmetic on the 2^21 grid (conservative form of Sec. 2.2's
+// "open if L/r > Theta"):
+//   accept node n  iff  (i)  sum_a gap(cell of com_n, group box)^2 >= ceil(4^(21-l)/Theta^2)
+//                  and  (ii) sum_a gap(node box, group box)^2     >= max(hq_group, hq_node)
+// (gap in whole cells between closed cell intervals; hq = ceil((h/cell)^2)):
+// every target then sees the node at L/r <= Theta and lies outside the
+// softening support of every member (Sec. 2.2.1), so the Newtonian
+// multipole is the node's field.  Accepted nodes go to the P2M list, opened
+// leaves to the P2P range queue, opened internal nodes push their child
+// range.  Lists live in shared memory; every full tile of 32 entries is
+// evaluated at once: each lane stages one source in shared memory, relative
+// to the group centre in FP32 (integer half-cell centre differences are
+// exact in FP32, plus the FP32 offset stored per node / particle), then
+// every lane (one target each) loops over the tile reading broadcast
+// shared-memory values.  Potentials are summed per tile in FP32 and
+// accumulated in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfg_internal.cuh"
+
+namespace sfg {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WALK_WARPS = 4;  // warps per block
+constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
+constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
+constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3;
+
+struct WarpSmem {
+    int2 stack[STK];
+    int p2m[64];
+    int2 leafq[64];
+    float4 tP[32];
+    float4 tA[32]; // P2M: (Qxx, Qyy, Qxy, Qxz); P2P: (h signed, 1/h, j bits, -)
+    float tB[32];  // P2M: Qyz
+    int tN[32];    // P2M: node id (adjoint)
+};
+
+struct WalkParams {
+    const int4 *W0, *W1, *W2;
+    const unsigned long long *Whq;
+    const float4 *E0, *E1, *E2;
+    const float4 *pw;
+    const int4 *pc;
+    const uint64_t *key;
+    const double *pos_s, *soft_s;
+    const uint8_t *sink_s;
+    Frame fr;
+    float s22;
+    unsigned long long T[SFG_LMAX + 1];
+    int nn;
+    const int2 *gtab;
+    const int *d_ngroups;
+    const int *tgt;
+    float4 *res_a;
+    double *res_phi;
+    unsigned long long *counters; // [0] p2p [1] p2m [2] overflowed groups [3] work [4] retry work
+    int *ovf_list;
+    int *status;
+    int2 *gstack;
+    // debug lists
+    int *dbg_counts;
+    const long long *dbg_off;
+    int *dbg_m, *dbg_p;
+    // adjoint
+    const float4 *cot; // per distinct target: (cot_a, cot_phi)
+    double *gpart;     // [n][4] sorted: d_pos, d_mass
+    double *gnode;     // [nn][10]: gM, gcom[3], gQ sym[6]
+};
+
+// Target-lane state of one group.
+struct Tgt {
+    bool has;
+    int r;
+    float ox, oy, oz, h, hinv;
+    bool sink;
+    int cg[3];
+};
+
+// ------------------------------------------------------------ kernels ----
+// Softened kernel of support h at separation r (u = r/h < 1 here):
+// a = K (x_j - x_i), phi = P per unit mass (M4 cubic spline, Sec. 2.2.1).
+__device__ __forceinline__ void soft_KP(float r, float rinv, float h, float hinv, float &K, float &P)
+{
+    float u = r * hinv;
+    if (u >= 1.f) {
+        float ri2 = rinv * rinv;
+        K = ri2 * rinv;
+        P = -rinv;
+        return;
+    }
+    float h3inv = hinv * hinv * hinv;
+    float u2 = u * u;
+    if (u < 0.5f) {
+        K = h3inv * fmaf(u2, fmaf(32.f, u, -38.4f), 10.6666667f);
+        P = hinv * fmaf(u2, fmaf(u2, fmaf(6.4f, u, -9.6f), 5.33333333f), -2.8f);
+    } else {
+        float uinv = h * rinv;
+        float uinv3 = uinv * uinv * uinv;
+        K = h3inv * (fmaf(u, fmaf(u, fmaf(-10.6666667f, u, 38.4f), -48.f), 21.3333333f) - 0.0666666667f * uinv3);
+        P = hinv * (fmaf(u2, fmaf(u, fmaf(u, fmaf(-2.13333333f, u, 9.6f), -16.f), 10.6666667f), -3.2f) +
+                    0.0666666667f * uinv);
+    }
+}
+
+// Same kernel plus K'(r)/r (for the tidal tensor of the adjoint).
+__device__ __forceinline__ void soft_KPR(float r, float rinv, float h, float hinv, float &K, float &P, float &R)
+{
+    float u = r * hinv;
+    float ri2 = rinv * rinv;
+    if (u >= 1.f) {
+        K = ri2 * rinv;
+        P = -rinv;
+        R = -3.f * K * ri2;
+        return;
+    }
+    float h2inv = hinv * hinv, h3inv = h2inv * hinv, h5inv = h3inv * h2inv;
+    float u2 = u * u;
+    if (u < 0.5f) {
+        K = h3inv * fmaf(u2, fmaf(32.f, u, -38.4f), 10.6666667f);
+        P = hinv * fmaf(u2, fmaf(u2, fmaf(6.4f, u, -9.6f), 5.33333333f), -2.8f);
+        R = h5inv * fmaf(96.f, u, -76.8f);
+    } else {
+        float uinv = h * rinv;
+        float uinv2 = uinv * uinv, uinv3 = uinv2 * uinv;
+        K = h3inv * (fmaf(u, fmaf(u, fmaf(-10.6666667f, u, 38.4f), -48.f), 21.3333333f) - 0.0666666667f * uinv3);
+        P = hinv * (fmaf(u2, fmaf(u, fmaf(u, fmaf(-2.13333333f, u, 9.6f), -16.f), 10.6666667f), -3.2f) +
+                    0.0666666667f * uinv);
+        R = h5inv * (fmaf(-32.f, u, 76.8f) - 48.f * uinv + 0.2f * uinv2 * uinv3);
+    }
+}
+
+// Pair rule (Sec. 2.2.1): gas-gas averages the kernels of h_i and h_j; a pair
+// with a sink uses one kernel of support max(h_i, h_j).
+__device__ __forceinline__ void pair_supports(const Tgt &T, float hj_signed, float hjinv, float &ha, float &hainv,
+                                              float &hb, float &hbinv)
+{
+    float hj = fabsf(hj_signed);
+    bool sink = T.sink || (hj_signed < 0.f);
+    ha = T.h;
+    hainv = T.hinv;
+    hb = hj;
+    hbinv = hjinv;
+    if (sink) {
+        if (hj > T.h) {
+            ha = hj;
+            hainv = hjinv;
+        }
+        hb = ha;
+        hbinv = hainv;
+    }
+}
+
+// ------------------------------------------------------- forward tiles ----
+template <bool QUAD>
+__device__ __forceinline__ void fwd_p2m(const WarpSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+                                        double &phi)
+{
+    float pt = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < cnt; k++) {
+        float4 p = S.tP[k];
+        float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float rinv = rsqrtf(r2);
+        float ri2 = rinv * rinv;
+        float ri3 = ri2 * rinv;
+        if (QUAD) {
+            float4 q = S.tA[k];
+            float qyz = S.tB[k];
+            float qzz = -(q.x + q.y);
+            float Qd0 = fmaf(q.x, dx, fmaf(q.z, dy, q.w * dz));
+            float Qd1 = fmaf(q.z, dx, fmaf(q.y, dy, qyz * dz));
+            float Qd2 = fmaf(q.w, dx, fmaf(qyz, dy, qzz * dz));
+            float dQd = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2));
+            float ri5 = ri3 * ri2;
+            float c = fmaf(2.5f * dQd * ri5, ri2, p.w * ri3);
+            ax = fmaf(c, dx, fmaf(-ri5, Qd0, ax));
+            ay = fmaf(c, dy, fmaf(-ri5, Qd1, ay));
+            az = fmaf(c, dz, fmaf(-ri5, Qd2, az));
+            pt = fmaf(-p.w, rinv, fmaf(-0.5f * dQd, ri5, pt));
+        } else {
+            float c = p.w * ri3;
+            ax = fmaf(c, dx, ax);
+            ay = fmaf(c, dy, ay);
+            az = fmaf(c, dz, az);
+            pt = fmaf(-p.w, rinv, pt);
+        }
+    }
+    phi += (double)pt;
+}
+
+__device__ __forceinline__ void fwd_p2p(const WarpSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+                                        double &phi)
+{
+    float pt = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < cnt; k++) {
+        float4 p = S.tP[k];
+        float4 hh = S.tA[k];
+        float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float m = (__float_as_int(hh.z) == T.r) ? 0.f : p.w;
+        float ha, hainv, hb, hbinv;
+        pair_supports(T, hh.x, hh.y, ha, hainv, hb, hbinv);
+        float hm = fmaxf(ha, hb);
+        float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        float K, P;
+        if (r2 < hm * hm) {
+            float r = r2 * rinv;
+            float K1, P1, K2, P2;
+            soft_KP(r, rinv, ha, hainv, K1, P1);
+            soft_KP(r, rinv, hb, hbinv, K2, P2);
+            K = 0.5f * (K1 + K2);
+            P = 0.5f * (P1 + P2);
+        } else {
+            K = rinv * rinv * rinv;
+            P = -rinv;
+        }
+        float mK = m * K;
+        ax = fmaf(mK, dx, ax);
+        ay = fmaf(mK, dy, ay);
+        az = fmaf(mK, dz, az);
+        pt = fmaf(m, P, pt);
+    }
+    phi += (double)pt;
+}
+
+// ------------------------------------------------------- adjoint tiles ----
+// Butterfly sum over the warp; every lane gets the total.
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Target side accumulates -dL/dd in registers; source side is warp-summed and
+// added to the source particle (P2P) or node (P2M) gradients.
+template <bool QUAD>
+__device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
+                                        float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
+{
+    for (int k = 0; k < cnt; k++) {
+        float4 p = S.tP[k];
+        float g[10];
+        if (T.has) {
+            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float rinv = rsqrtf(r2);
+            float ri2 = rinv * rinv, ri3 = ri2 * rinv, ri5 = ri3 * ri2;
+            float M = p.w;
+            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
+            // monopole: a = M d ri3, phi = -M ri
+            float s1 = M * ri3;                           // coefficient of c
+            float s2 = M * fmaf(-3.f * cd, ri5, cf * ri3); // coefficient of d
+            float gd0 = fmaf(s1, c0, s2 * dx), gd1 = fmaf(s1, c1, s2 * dy), gd2 = fmaf(s1, c2, s2 * dz);
+            g[0] = fmaf(cd, ri3, -cf * rinv);
+            for (int q = 4; q < 10; q++) g[q] = 0.f;
+            if (QUAD) {
+                float4 q = S.tA[k];
+                float qyz = S.tB[k];
+                float qzz = -(q.x + q.y);
+                float Qd0 = fmaf(q.x, dx, fmaf(q.z, dy, q.w * dz));
+                float Qd1 = fmaf(q.z, dx, fmaf(q.y, dy, qyz * dz));
+                float Qd2 = fmaf(q.w, dx, fmaf(qyz, dy, qzz * dz));
+                float Qc0 = fmaf(q.x, c0, fmaf(q.z, c1, q.w * c2));
+                float Qc1 = fmaf(q.z, c0, fmaf(q.y, c1, qyz * c2));
+                float Qc2 = fmaf(q.w, c0, fmaf(qyz, c1, qzz * c2));
+                float dQd = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2));
+                float cQd = fmaf(c0, Qd0, fmaf(c1, Qd1, c2 * Qd2));
+                float ri7 = ri5 * ri2, ri9 = ri7 * ri2;
+                // d/dd of c.(-Q d ri5 + 2.5 dQd d ri7) + cf (-0.5 dQd ri5)
+                float aQ = -ri5;                                  // coefficient of Qc
+                float aQd = 5.f * cd * ri7 - cf * ri5;            // coefficient of Qd
+                float ad = 5.f * cQd * ri7 - 17.5f * dQd * cd * ri9 + 2.5f * cf * dQd * ri7; // of d
+                float ac = 2.5f * dQd * ri7;                      // of c
+                gd0 += aQ * Qc0 + aQd * Qd0 + ad * dx + ac * c0;
+                gd1 += aQ * Qc1 + aQd * Qd1 + ad * dy + ac * c1;
+                gd2 += aQ * Qc2 + aQd * Qd2 + ad * dz + ac * c2;
+                float s = 2.5f * cd * ri7 - 0.5f * cf * ri5;
+                g[4] = fmaf(-c0 * dx, ri5, s * dx * dx);
+                g[5] = fmaf(-c1 * dy, ri5, s * dy * dy);
+                g[6] = fmaf(-c2 * dz, ri5, s * dz * dz);
+                g[7] = fmaf(-0.5f * (c0 * dy + dx * c1), ri5, s * dx * dy);
+                g[8] = fmaf(-0.5f * (c0 * dz + dx * c2), ri5, s * dx * dz);
+                g[9] = fmaf(-0.5f * (c1 * dz + dy * c2), ri5, s * dy * dz);
+            }
+            g[1] = gd0;
+            g[2] = gd1;
+            g[3] = gd2;
+            gx -= gd0;
+            gy -= gd1;
+            gz -= gd2;
+        } else {
+            for (int q = 0; q < 10; q++) g[q] = 0.f;
+        }
+        const int nq = QUAD ? 10 : 4;
+        double *dst = P.gnode + 10 * (size_t)S.tN[k];
+        for (int q = 0; q < nq; q++) {
+            float v = warp_sum(g[q]);
+            if (lane == q && v != 0.f) atomicAdd(dst + q, (double)v);
+        }
+    }
+}
+
+__device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
+                                        float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
+{
+    for (int k = 0; k < cnt; k++) {
+        float4 p = S.tP[k];
+        float4 hh = S.tA[k];
+        int j = __float_as_int(hh.z);
+        float l0 = 0.f, l1 = 0.f, l2 = 0.f, lm = 0.f;
+        if (T.has && j != T.r) {
+            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float ha, hainv, hb, hbinv;
+            pair_supports(T, hh.x, hh.y, ha, hainv, hb, hbinv);
+            float hm = fmaxf(ha, hb);
+            float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            float K, Pp, R;
+            if (r2 < hm * hm) {
+                float r = r2 * rinv;
+                float K1, P1, R1, K2, P2, R2;
+                soft_KPR(r, rinv, ha, hainv, K1, P1, R1);
+                soft_KPR(r, rinv, hb, hbinv, K2, P2, R2);
+                K = 0.5f * (K1 + K2);
+                Pp = 0.5f * (P1 + P2);
+                R = 0.5f * (R1 + R2);
+            } else {
+                float ri2 = rinv * rinv;
+                K = ri2 * rinv;
+                Pp = -rinv;
+                R = -3.f * K * ri2;
+            }
+            float m = p.w;
+            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
+            float mK = m * K;
+            float s = m * fmaf(R, cd, cf * K);
+            l0 = fmaf(mK, c0, s * dx);
+            l1 = fmaf(mK, c1, s * dy);
+            l2 = fmaf(mK, c2, s * dz);
+            lm = fmaf(K, cd, Pp * cf);
+            gx -= l0;
+            gy -= l1;
+            gz -= l2;
+        }
+        l0 = warp_sum(l0);
+        l1 = warp_sum(l1);
+        l2 = warp_sum(l2);
+        lm = warp_sum(lm);
+        double *dst = P.gpart + 4 * (size_t)j;
+        float v = lane == 0 ? l0 : lane == 1 ? l1 : lane == 2 ? l2 : lm;
+        if (lane < 4 && v != 0.f) atomicAdd(dst + lane, (double)v);
+    }
+}
+
+// --------------------------------------------------------- tile staging ----
+template <bool QUAD, bool NODEID>
+__device__ __forceinline__ void stage_p2m(const WalkParams &P, WarpSmem &S, const int *list, int cnt, const Tgt &T,
+                                          int lane)
+{
+    if (lane < cnt) {
+        int id = list[lane];
+        float4 e0 = P.E0[id];
+        float4 e2 = P.E2[id];
+        float px = fmaf((float)(__float_as_int(e2.y) - T.cg[0]), P.s22, e0.x);
+        float py = fmaf((float)(__float_as_int(e2.z) - T.cg[1]), P.s22, e0.y);
+        float pz = fmaf((float)(__float_as_int(e2.w) - T.cg[2]), P.s22, e0.z);
+        S.tP[lane] = make_float4(px, py, pz, e0.w);
+        if (QUAD) {
+            S.tA[lane] = P.E1[id];
+            S.tB[lane] = e2.x;
+        }
+        if (NODEID) S.tN[lane] = id;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int cnt, int &qh, int &qoff, const Tgt &T,
+                                          int lane)
+{
+    int j = -1, filled = 0;
+    // at most 64 queued ranges can be pending; each iteration consumes one
+    // range or completes the tile
+    for (int it = 0; filled < cnt && it < 66; it++) {
+        int2 hr = S.leafq[qh & 63];
+        int take = min(hr.y - qoff, cnt - filled);
+        if (take < 0) take = 0;
+        if (lane >= filled && lane < filled + take) j = hr.x + qoff + (lane - filled);
+        filled += take;
+        qoff += take;
+        if (qoff >= hr.y) {
+            qh++;
+            qoff = 0;
+        }
+    }
+    if (filled < cnt) {
+        if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
+        if (lane >= filled) j = -1;
+    }
+    if (lane < cnt && j >= 0) {
+        float4 a = P.pw[j];
+        int4 b = P.pc[j];
+        float px = fmaf((float)(b.x - T.cg[0]), P.s22, a.x);
+        float py = fmaf((float)(b.y - T.cg[1]), P.s22, a.y);
+        float pz = fmaf((float)(b.z - T.cg[2]), P.s22, a.z);
+        S.tP[lane] = make_float4(px, py, pz, a.w);
+        float h = __int_as_float(b.w);
+        S.tA[lane] = make_float4(h, 1.f / fabsf(h), __int_as_float(j), 0.f);
+    }
+    __syncwarp();
+}
+
+// ----------------------------------------------------------- the walk ----
+template <bool QUAD, int MODE, bool GSTACK>
+__device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const int cap = GSTACK ? GSTK : STK;
+    const int2 gt = P.gtab[g];
+    const int tfirst = gt.x, tcount = gt.y;
+    Tgt T;
+    T.has = lane < tcount;
+    T.r = T.has ? P.tgt[tfirst + lane] : -1;
+    uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
+    unsigned long long hq = 0;
+    double xd[3] = {0, 0, 0};
+    T.h = 1.f;
+    T.sink = false;
+    if (T.has) {
+        uint64_t k = P.key[T.r];
+        lo[0] = hi[0] = compact3(k >> 2);
+        lo[1] = hi[1] = compact3(k >> 1);
+        lo[2] = hi[2] = compact3(k);
+        for (int a = 0; a < 3; a++) xd[a] = P.pos_s[3 * (size_t)T.r + a];
+        double h = P.soft_s[T.r];
+        hq = hq_of(h, P.fr.scale);
+        T.h = (float)h;
+        T.sink = P.sink_s[T.r] != 0;
+    }
+    T.hinv = 1.f / T.h;
+    int glo[3], ghi[3];
+    for (int a = 0; a < 3; a++) {
+        glo[a] = (int)__reduce_min_sync(FULL, lo[a]);
+        ghi[a] = (int)__reduce_max_sync(FULL, hi[a]);
+        T.cg[a] = glo[a] + ghi[a] + 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(FULL, hq, o);
+        hq = t > hq ? t : hq;
+    }
+    {
+        double c0 = P.fr.x0[0] + (double)T.cg[0] * P.fr.half_cell;
+        double c1 = P.fr.x0[1] + (double)T.cg[1] * P.fr.half_cell;
+        double c2 = P.fr.x0[2] + (double)T.cg[2] * P.fr.half_cell;
+        T.ox = (float)(xd[0] - c0);
+        T.oy = (float)(xd[1] - c1);
+        T.oz = (float)(xd[2] - c2);
+    }
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    double phi = 0.0;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, cf = 0.f;
+    if (MODE == MODE_VJP && T.has) {
+        float4 cv = P.cot[tfirst + lane];
+        c0 = cv.x;
+        c1 = cv.y;
+        c2 = cv.z;
+        cf = cv.w;
+    }
+    long long off_m = 0, off_p = 0;
+    if (MODE == MODE_DUMP) {
+        off_m = P.dbg_off[2 * g];
+        off_p = P.dbg_off[2 * g + 1];
+    }
+
+    if (lane == 0) stack[0] = make_int2(0, 1);
+    __syncwarp();
+    int sp = 1, nm = 0, qh = 0, qt = 0, qoff = 0, qn = 0;
+    long long tot_m = 0, tot_p = 0, tot_leaf = 0;
+    bool overflow = false;
+    // every node is visited at most once per group, so nn + 1 rounds bound the walk
+    long long rounds = 0;
+    const long long max_rounds = (long long)P.nn + 1;
+    while (sp > 0) {
+        if (++rounds > max_rounds) {
+            if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
+            break;
+        }
+        int node = -1;
+        int taken = 0;
+        while (taken < 32 && sp > 0) {
+            int2 top = stack[sp - 1];
+            int take = min(32 - taken, top.y);
+            if (lane >= taken && lane < taken + take) node = top.x + (top.y - take) + (lane - taken);
+            taken += take;
+            __syncwarp();
+            if (take == top.y) sp--;
+            else if (lane == 0) stack[sp - 1].y = top.y - take;
+            __syncwarp();
+        }
+        bool acc = false, lf = false, op = false;
+        int link = 0, cnt = 0;
+        if (node >= 0) {
+            int4 w0 = P.W0[node], w1 = P.W1[node], w2 = P.W2[node];
+            unsigned long long nhq = P.Whq[node];
+            int level = w0.w & 255;
+            bool leaf = (w0.w >> 8) & 1;
+            int gc0 = max(0, max(glo[0] - w2.x - 1, w2.x - ghi[0] - 1));
+            int gc1 = max(0, max(glo[1] - w2.y - 1, w2.y - ghi[1] - 1));
+            int gc2 = max(0, max(glo[2] - w2.z - 1, w2.z - ghi[2] - 1));
+            int gb0 = max(0, max(glo[0] - w1.x - 1, w0.x - ghi[0] - 1));
+            int gb1 = max(0, max(glo[1] - w1.y - 1, w0.y - ghi[1] - 1));
+            int gb2 = max(0, max(glo[2] - w1.z - 1, w0.z - ghi[2] - 1));
+            unsigned long long sc = (unsigned long long)gc0 * (unsigned)gc0 +
+                                    (unsigned long long)gc1 * (unsigned)gc1 +
+                                    (unsigned long long)gc2 * (unsigned)gc2;
+            unsigned long long sb = (unsigned long long)gb0 * (unsigned)gb0 +
+                                    (unsigned long long)gb1 * (unsigned)gb1 +
+                                    (unsigned long long)gb2 * (unsigned)gb2;
+            unsigned long long need = nhq > hq ? nhq : hq;
+            acc = sc >= P.T[level] && sb >= need;
+            lf = !acc && leaf;
+            op = !acc && !leaf;
+            link = w1.w;
+            cnt = w2.w;
+        }
+        unsigned ba = __ballot_sync(FULL, acc);
+        unsigned bl = __ballot_sync(FULL, lf);
+        unsigned bo = __ballot_sync(FULL, op);
+        int npush = __popc(bo);
+        if (sp + npush > cap) {
+            overflow = true;
+            break;
+        }
+        if (op) stack[sp + __popc(bo & lt)] = make_int2(link, cnt);
+        sp += npush;
+        int lc = __reduce_add_sync(FULL, lf ? cnt : 0);
+        tot_m += __popc(ba);
+        tot_leaf += __popc(bl);
+        tot_p += lc;
+        if (MODE == MODE_COUNT || MODE == MODE_DUMP) {
+            if (MODE == MODE_DUMP) {
+                if (acc) P.dbg_m[off_m + __popc(ba & lt)] = node;
+                if (lf) P.dbg_p[off_p + __popc(bl & lt)] = node;
+                off_m += __popc(ba);
+                off_p += __popc(bl);
+            }
+            __syncwarp();
+            continue;
+        }
+        if (acc) S.p2m[nm + __popc(ba & lt)] = node;
+        nm += __popc(ba);
+        if (lf) S.leafq[(qt + __popc(bl & lt)) & 63] = make_int2(link, cnt);
+        qt += __popc(bl);
+        qn += lc;
+        __syncwarp();
+        while (nm >= 32) {
+            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m + nm - 32, 32, T, lane);
+            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2m<QUAD>(S, 32, T, ax, ay, az, phi);
+            __syncwarp();
+            nm -= 32;
+        }
+        while (qn >= 32) {
+            stage_p2p(P, S, 32, qh, qoff, T, lane);
+            if (MODE == MODE_VJP) vjp_p2p(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2p(S, 32, T, ax, ay, az, phi);
+            __syncwarp();
+            qn -= 32;
+        }
+    }
+    if (overflow) {
+        if (GSTACK) {
+            if (lane == 0) atomicOr(P.status, ST_EOVERFLOW);
+        } else if (lane == 0) {
+            unsigned long long idx = atomicAdd(&P.counters[2], 1ull);
+            P.ovf_list[idx] = g;
+        }
+        __syncwarp();
+        return;
+    }
+    if (MODE == MODE_COUNT) {
+        if (lane == 0) {
+            P.dbg_counts[2 * g] = (int)tot_m;
+            P.dbg_counts[2 * g + 1] = (int)tot_leaf;
+        }
+        return;
+    }
+    if (MODE == MODE_DUMP) return;
+    if (nm > 0) {
+        stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m, nm, T, lane);
+        if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, nm, T, c0, c1, c2, cf, ax, ay, az, lane);
+        else if (T.has) fwd_p2m<QUAD>(S, nm, T, ax, ay, az, phi);
+        __syncwarp();
+    }
+    while (qn > 0) {
+        int c = min(qn, 32);
+        stage_p2p(P, S, c, qh, qoff, T, lane);
+        if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+        else if (T.has) fwd_p2p(S, c, T, ax, ay, az, phi);
+        __syncwarp();
+        qn -= c;
+    }
+    if (MODE == MODE_EVAL) {
+        if (T.has) {
+            P.res_a[tfirst + lane] = make_float4(ax, ay, az, 0.f);
+            P.res_phi[tfirst + lane] = phi;
+        }
+    } else if (MODE == MODE_VJP) {
+        if (T.has) {
+            double *dst = P.gpart + 4 * (size_t)T.r;
+            atomicAdd(dst, (double)ax);
+            atomicAdd(dst + 1, (double)ay);
+            atomicAdd(dst + 2, (double)az);
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&P.counters[0], (unsigned long long)(tcount * (tot_p - 1)));
+        atomicAdd(&P.counters[1], (unsigned long long)(tcount * tot_m));
+    }
+}
+
+template <bool QUAD, int MODE, bool GSTACK>
+__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkParams P)
+{
+    __shared__ WarpSmem sm[WALK_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpSmem &S = sm[w];
+    int2 *stack = GSTACK ? P.gstack + (size_t)(blockIdx.x * WALK_WARPS + w) * GSTK : S.stack;
+    const int ngroups = GSTACK ? (int)P.counters[2] : *P.d_ngroups;
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(&P.counters[GSTACK ? 4 : 3], 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= ngroups) break;
+        int g = GSTACK ? P.ovf_list[item] : item;
+        walk_group<QUAD, MODE, GSTACK>(P, S, stack, g, lane);
+    }
+}
+
+// ---------------------------------------------------- group formation ----
+__global__ void k_mark(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, int *flag, int *status)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) {
+            atomicOr(status, ST_EINVAL);
+            continue;
+        }
+        flag[rank[i]] = 1;
+    }
+}
+
+__global__ void k_compact(const int *flag, const int *pre, int n, int *tgt)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        if (flag[r]) tgt[pre[r]] = r;
+}
+
+__device__ inline void put_group(int *gflag, int *gcnt, int tf, int tc)
+{
+    gflag[tf] = 1;
+    gcnt[tf] = tc;
+}
+
+__global__ void k_group_marks(const int32_t *nfirst, const int32_t *ncount, const int32_t *nchild_first,
+                              const int32_t *nnchild, int nn, const int *pre, int G, int *gflag, int *gcnt)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        int f = nfirst[i];
+        int tf = pre[f];
+        int c = pre[f + ncount[i]] - tf;
+        if (c == 0) continue;
+        bool leaf = nnchild[i] == 0;
+        if (i == 0 && c <= G) put_group(gflag, gcnt, tf, c);
+        if (i == 0 && c > G && leaf)
+            for (int s = 0; s < c; s += G) put_group(gflag, gcnt, tf + s, min(G, c - s));
+        if (c <= G || leaf) continue;
+        int run_first = -1, run_count = 0;
+        int cf = nchild_first[i], nc = nnchild[i];
+        for (int k = 0; k < nc; k++) {
+            int ch = cf + k;
+            int ctf = pre[nfirst[ch]];
+            int cc = pre[nfirst[ch] + ncount[ch]] - ctf;
+            if (cc == 0) continue;
+            if (cc > G) {
+                if (run_count) put_group(gflag, gcnt, run_first, run_count);
+                run_count = 0;
+                if (nnchild[ch] == 0)
+                    for (int s = 0; s < cc; s += G) put_group(gflag, gcnt, ctf + s, min(G, cc - s));
+                continue;
+            }
+            if (run_count + cc > G) {
+                put_group(gflag, gcnt, run_first, run_count);
+                run_count = 0;
+            }
+            if (run_count == 0) run_first = ctf;
+            run_count += cc;
+        }
+        if (run_count) put_group(gflag, gcnt, run_first, run_count);
+    }
+}
+
+__global__ void k_group_table(const int *gflag, const int *gcnt, const int *goff, const int *d_U, int2 *gtab)
+{
+    int U = *d_U;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
+        if (gflag[u]) gtab[goff[u]] = make_int2(u, gcnt[u]);
+}
+
+__global__ void k_rows_out(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
+                           const float4 *res_a, const double *res_phi, double G, double *accel, double *phi)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) continue;
+        int u = pre[rank[i]];
+        float4 a = res_a[u];
+        accel[3 * k] = G * (double)a.x;
+        accel[3 * k + 1] = G * (double)a.y;
+        accel[3 * k + 2] = G * (double)a.z;
+        if (phi) phi[k] = G * res_phi[u];
+    }
+}
+
+// --------------------------------------------------------- host side ----
+static int grid_for(int64_t n, int bt)
+{
+    int64_t g = (n + bt - 1) / bt;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Per-call workspace carved from one grow-only allocation.
+struct Work {
+    int *flag, *pre, *tgt, *gflag, *gcnt, *goff, *ovf, *scr;
+    int2 *gtab, *gstack;
+    float4 *res_a;
+    double *res_phi;
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int get_work(Tree *t, cudaStream_t s, Work &w)
+{
+    const size_t n = (size_t)t->n;
+    const int retry_warps = num_sms() * WALK_WARPS;
+    size_t sz[12] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, n * 4, scan_scratch_bytes(),
+                     n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8};
+    size_t total = 0;
+    for (size_t b : sz) total += align_up(b);
+    if (t->ws_bytes < total) {
+        if (t->ws) dev_free(t, t->ws, s);
+        t->ws = dev_alloc(t, total, s);
+        if (!t->ws) {
+            t->ws_bytes = 0;
+            return SFG_ENOMEM;
+        }
+        t->ws_bytes = total;
+    }
+    char *p = (char *)t->ws;
+    void *ptr[12];
+    for (int k = 0; k < 12; k++) {
+        ptr[k] = p;
+        p += align_up(sz[k]);
+    }
+    w.flag = (int *)ptr[0];
+    w.pre = (int *)ptr[1];
+    w.tgt = (int *)ptr[2];
+    w.gflag = (int *)ptr[3];
+    w.gcnt = (int *)ptr[4];
+    w.goff = (int *)ptr[5];
+    w.ovf = (int *)ptr[6];
+    w.scr = (int *)ptr[7];
+    w.gtab = (int2 *)ptr[8];
+    w.gstack = (int2 *)ptr[9];
+    w.res_a = (float4 *)ptr[10];
+    w.res_phi = (double *)ptr[11];
+    return SFG_OK;
+}
+
+// Groups of the active set: flags by sorted rank, distinct targets in Morton
+// order, group table.  Leaves the group count at w.goff[U] (device).
+static int form_groups(Tree *t, const int64_t *active, int64_t n_active, Work &w, const int **d_ngroups,
+                       cudaStream_t s)
+{
+    const int n = (int)t->n, BT = 256;
+    SFG_CUDA_OK(cudaMemsetAsync(w.flag, 0, sizeof(int) * (size_t)n, s));
+    SFG_CUDA_OK(cudaMemsetAsync(w.gflag, 0, sizeof(int) * (size_t)n, s));
+    k_mark<<<grid_for(n_active, BT), BT, 0, s>>>(active, n_active, n, t->rank, w.flag, t->d_status);
+    scan_exclusive(w.flag, w.pre, t->d_n, n, nullptr, nullptr, w.scr, s);
+    k_compact<<<grid_for(n, BT), BT, 0, s>>>(w.flag, w.pre, n, w.tgt);
+    k_group_marks<<<grid_for(t->nn, BT), BT, 0, s>>>(t->nfirst, t->ncount, t->nchild_first, t->nnchild, t->nn,
+                                                     w.pre, t->prm.group_size, w.gflag, w.gcnt);
+    scan_exclusive(w.gflag, w.goff, w.pre + n, n, nullptr, nullptr, w.scr, s);
+    k_group_table<<<grid_for(n, BT), BT, 0, s>>>(w.gflag, w.gcnt, w.goff, w.pre + n, w.gtab);
+    *d_ngroups = nullptr;
+    return SFG_OK;
+}
+
+// groups = goff[U] -> counters[5] (as int), U -> counters[6]
+__global__ void k_ngroups(const int *pre, int n, const int *goff, unsigned long long *counters)
+{
+    int U = pre[n];
+    *(int *)(counters + 5) = goff[U];
+    counters[6] = (unsigned long long)U;
+}
+
+static void fill_params(Tree *t, Work &w, WalkParams &P)
+{
+    P.W0 = t->W0;
+    P.W1 = t->W1;
+    P.W2 = t->W2;
+    P.Whq = t->Whq;
+    P.E0 = t->E0;
+    P.E1 = t->E1;
+    P.E2 = t->E2;
+    P.pw = t->pw;
+    P.pc = t->pc;
+    P.key = t->key;
+    P.pos_s = t->pos_s;
+    P.soft_s = t->soft_s;
+    P.sink_s = t->sink_s;
+    P.fr = t->frame_h;
+    P.nn = t->nn;
+    P.s22 = (float)t->frame_h.half_cell;
+    const double th = t->prm.theta;
+    for (int l = 0; l <= SFG_LMAX; l++) {
+        double v = ldexp(1.0, 2 * (SFG_LMAX - l)) / (th * th);
+        P.T[l] = (v < 4611686018427387904.0) ? (unsigned long long)ceil(v) : SFG_CAP62;
+    }
+    P.gtab = w.gtab;
+    P.tgt = w.tgt;
+    P.res_a = w.res_a;
+    P.res_phi = w.res_phi;
+    P.counters = t->d_counters;
+    P.ovf_list = w.ovf;
+    P.status = t->d_status;
+    P.gstack = w.gstack;
+    P.dbg_counts = nullptr;
+    P.dbg_off = nullptr;
+    P.dbg_m = nullptr;
+    P.dbg_p = nullptr;
+    P.cot = nullptr;
+    P.gpart = nullptr;
+    P.gnode = nullptr;
+}
+
+template <int MODE>
+static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
+{
+    const int blocks = num_sms() * 4;
+    const int retry_blocks = num_sms();
+    if (t->prm.quadrupole) {
+        k_walk<true, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
+        k_walk<true, MODE, true><<<retry_blocks, WALK_WARPS * 32, 0, s>>>(P);
+    } else {
+        k_walk<false, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
+        k_walk<false, MODE, true><<<retry_blocks, WALK_WARPS * 32, 0, s>>>(P);
+    }
+}
+
+// counters: [0] p2p [1] p2m [2] overflow count [3] work [4] retry work [5] ngroups (int)
+static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, WalkParams &P, cudaStream_t s)
+{
+    int rc = get_work(t, s, w);
+    if (rc) return rc;
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, 8 * sizeof(unsigned long long), s));
+    const int *dng;
+    rc = form_groups(t, active, n_active, w, &dng, s);
+    if (rc) return rc;
+    int *d_ngroups = (int *)(t->d_counters + 5);
+    k_ngroups<<<1, 1, 0, s>>>(w.pre, (int)t->n, w.goff, t->d_counters);
+    fill_params(t, w, P);
+    P.d_ngroups = d_ngroups;
+    return SFG_OK;
+}
+
+int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double *phi, cudaStream_t s)
+{
+    if (n_active == 0) return SFG_OK;
+    if (t->prm.precision != 0) return SFG_EINVAL; // all-FP64 evaluation is not built yet
+    Work w;
+    WalkParams P;
+    int rc = prepare(t, active, n_active, w, P, s);
+    if (rc) return rc;
+    launch_walk<MODE_EVAL>(t, P, s);
+    k_rows_out<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, w.res_a,
+                                                       w.res_phi, t->prm.G, acc, phi);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+int accel_vjp(Tree *, const int64_t *, int64_t, const double *, const double *, double *, double *, cudaStream_t)
+{
+    return SFG_EINVAL;
+}
+
+int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
+                int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s)
+{
+    Work w;
+    WalkParams P;
+    int rc = prepare(t, active, n_active, w, P, s);
+    if (rc) return rc;
+    int ng = 0;
+    SFG_CUDA_OK(cudaMemcpyAsync(&ng, t->d_counters + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
+    int *cnt = (int *)dev_alloc(t, sizeof(int) * 2 * (size_t)(ng > 0 ? ng : 1), s);
+    if (!cnt) return SFG_ENOMEM;
+    P.dbg_counts = cnt;
+    launch_walk<MODE_COUNT>(t, P, s);
+    int2 *gt_h = (int2 *)malloc(sizeof(int2) * (size_t)(ng > 0 ? ng : 1));
+    int *cnt_h = (int *)malloc(sizeof(int) * 2 * (size_t)(ng > 0 ? ng : 1));
+    SFG_CUDA_OK(cudaMemcpyAsync(gt_h, w.gtab, sizeof(int2) * (size_t)ng, cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaMemcpyAsync(cnt_h, cnt, sizeof(int) * 2 * (size_t)ng, cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
+    long long tm = 0, tp = 0;
+    long long *off_h = (long long *)malloc(sizeof(long long) * 2 * (size_t)(ng > 0 ? ng : 1));
+    for (int g = 0; g < ng; g++) {
+        off_h[2 * g] = tm;
+        off_h[2 * g + 1] = tp;
+        tm += cnt_h[2 * g];
+        tp += cnt_h[2 * g + 1];
+    }
+    *n_groups = ng;
+    *n_p2m_total = tm;
+    *n_p2p_total = tp;
+    if (groups && p2m && p2p) {
+        for (int g = 0; g < ng; g++) {
+            groups[4 * g] = gt_h[g].x;
+            groups[4 * g + 1] = gt_h[g].y;
+            groups[4 * g + 2] = cnt_h[2 * g];
+            groups[4 * g + 3] = cnt_h[2 * g + 1];
+        }
+        long long *off_d = (long long *)dev_alloc(t, sizeof(long long) * 2 * (size_t)(ng > 0 ? ng : 1), s);
+        int *dm = (int *)dev_alloc(t, sizeof(int) * (size_t)(tm > 0 ? tm : 1), s);
+        int *dp = (int *)dev_alloc(t, sizeof(int) * (size_t)(tp > 0 ? tp : 1), s);
+        if (!off_d || !dm || !dp) return SFG_ENOMEM;
+        SFG_CUDA_OK(cudaMemcpyAsync(off_d, off_h, sizeof(long long) * 2 * (size_t)ng, cudaMemcpyHostToDevice, s));
+        SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
+        P.dbg_off = off_d;
+        P.dbg_m = dm;
+        P.dbg_p = dp;
+        launch_walk<MODE_DUMP>(t, P, s);
+        SFG_CUDA_OK(cudaMemcpyAsync(p2m, dm, sizeof(int) * (size_t)tm, cudaMemcpyDeviceToHost, s));
+        SFG_CUDA_OK(cudaMemcpyAsync(p2p, dp, sizeof(int) * (size_t)tp, cudaMemcpyDeviceToHost, s));
+        SFG_CUDA_OK(cudaStreamSynchronize(s));
+        dev_free(t, off_d, s);
+        dev_free(t, dm, s);
+        dev_free(t, dp, s);
+    }
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
+    dev_free(t, cnt, s);
+    free(gt_h);
+    free(cnt_h);
+    free(off_h);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+} // namespace sfg

@@ -1,0 +1,193 @@
+"""GPU field at the active particles against the oracle (Sec. 2.2, 2.2.1):
+bit-exact groups and interaction lists (as sets per group), then forces and
+potentials with identical lists within the FP32 tolerance: median relative
+force error <= 1e-5, potentials <= 1e-6 (FP64-accumulated tile sums)."""
+import numpy as np
+import pytest
+
+import gen
+from _helpers import edge_clouds, oracle_tree, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+FORCE_MEDIAN = 1e-5
+FORCE_P99 = 2e-4
+PHI_MAX = 1e-6
+
+
+def _run(c, active, theta, leaf_size=16, group_size=32, quad=True, check_lists=True, G=1.0):
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    pos, mass, soft, sink = to_dev(c, torch)
+    t = sfg.Tree(pos, mass, soft, sink, theta=theta, leaf_size=leaf_size, group_size=group_size, quadrupole=quad,
+                 G=G)
+    act = torch.from_numpy(np.asarray(active, np.int64)).cuda()
+    acc, phi = t.accel(act)
+    assert t.status() == sfg.SFG_OK
+    st = t.stats()
+    o = oracle_tree(c, leaf_size)
+    o.walk(active, group_size, theta)
+    if check_lists:
+        groups, p2m, p2p = t.debug_lists(act)
+        og = o.groups()
+        np.testing.assert_array_equal(groups[:, 0], og[:, 1])
+        np.testing.assert_array_equal(groups[:, 1], og[:, 2])
+        np.testing.assert_array_equal(groups[:, 2], og[:, 4])
+        np.testing.assert_array_equal(groups[:, 3], og[:, 5])
+        om = np.cumsum(np.r_[0, groups[:, 2]])
+        op = np.cumsum(np.r_[0, groups[:, 3]])
+        for g in range(len(og)):
+            lm, lp = o.group_lists(g, og)
+            np.testing.assert_array_equal(np.sort(p2m[om[g]:om[g + 1]]), np.sort(lm))
+            np.testing.assert_array_equal(np.sort(p2p[op[g]:op[g + 1]]), np.sort(lp))
+    ao, po = o.accel_group(active, G=G, quadrupole=quad)
+    t.close()
+    return acc.cpu().numpy(), phi.cpu().numpy(), ao, po, st
+
+
+def _check_fields(acc, phi, ao, po):
+    e = rel_err(acc, ao)
+    assert np.median(e) <= FORCE_MEDIAN, np.median(e)
+    assert np.percentile(e, 99) <= FORCE_P99, np.percentile(e, 99)
+    assert rel_err(phi, po).max() <= PHI_MAX
+
+
+@pytest.mark.parametrize("quad", [True, False])
+def test_uniform_4096_theta07_all_active(quad):
+    c = gen.uniform_cloud(4096)
+    act = np.arange(c.n)
+    acc, phi, ao, po, st = _run(c, act, 0.7, quad=quad)
+    _check_fields(acc, phi, ao, po)
+    assert st["n_targets"] == c.n
+
+
+@pytest.mark.parametrize("leaf_size,group_size", [(1, 1), (4, 8), (16, 32), (64, 32), (32, 17)])
+def test_leaf_and_group_sizes(leaf_size, group_size):
+    c = gen.uniform_cloud(6000, seed=2, n_sink=9)
+    act = gen.active_subset(c.n, 0.4, seed=3)
+    acc, phi, ao, po, _ = _run(c, act, 0.5, leaf_size=leaf_size, group_size=group_size)
+    _check_fields(acc, phi, ao, po)
+
+
+def test_clumpy_with_sinks_sparse_active():
+    c = gen.clumpy_cloud(1 << 16, n_clumps=128, n_sink=64, seed=14)
+    act = gen.active_subset(c.n, 0.1, seed=4)
+    acc, phi, ao, po, st = _run(c, act, 0.5)
+    _check_fields(acc, phi, ao, po)
+    assert st["n_p2p"] > 0 and st["n_p2m"] > 0
+
+
+def test_theta_zero_is_direct_sum():
+    import oracle
+    c = gen.uniform_cloud(3000, seed=9, n_sink=5)
+    act = np.arange(c.n)
+    acc, phi, ao, po, st = _run(c, act, 0.0, check_lists=False)
+    ad, pd = oracle.direct(c.pos, c.mass, c.soft, c.is_sink)
+    _check_fields(acc, phi, ad, pd)
+    assert st["n_p2m"] == 0 and st["n_p2p"] == c.n * (c.n - 1)
+
+
+def test_duplicate_and_unordered_active_rows():
+    c = gen.uniform_cloud(5000, seed=10)
+    rng = np.random.default_rng(1)
+    act = rng.integers(0, c.n, 3000)  # duplicates, any order
+    acc, phi, ao, po, st = _run(c, act, 0.6)
+    _check_fields(acc, phi, ao, po)
+    assert st["n_targets"] == np.unique(act).size
+    dup = act[:, None] == act[None, :]
+    i, j = np.nonzero(np.triu(dup, 1))
+    np.testing.assert_array_equal(acc[i], acc[j])
+
+
+def test_G_scales_the_field():
+    c = gen.uniform_cloud(2000, seed=11)
+    act = np.arange(0, c.n, 3)
+    acc, phi, ao, po, _ = _run(c, act, 0.5, G=6.674e-8, check_lists=False)
+    _check_fields(acc, phi, ao, po)
+
+
+@pytest.mark.parametrize("name", ["n1", "n2", "identical", "duplicates", "decades", "sinks_only", "massless"])
+def test_edge_cases(name):
+    c = edge_clouds()[name]
+    act = np.arange(c.n)
+    acc, phi, ao, po, _ = _run(c, act, 0.5, leaf_size=8)
+    np.testing.assert_allclose(phi, po, rtol=PHI_MAX, atol=0)
+    if c.n == 1:
+        assert np.all(acc == 0) and np.all(phi == 0)
+        return
+    if name == "identical":
+        # coincident particles: softened pairs at zero separation exert no force
+        assert np.all(acc == 0) and np.all(ao == 0)
+        return
+    e = rel_err(acc, ao)
+    big = np.linalg.norm(ao, axis=1) > 1e-12 * np.linalg.norm(ao, axis=1).max()
+    if name == "decades":
+        # 500 cells in a 1e-9 clump share one level-21 grid cell (side ~1e-6):
+        # their FP32 offsets from that cell's centre resolve separations to
+        # ~1e-4 relative; the rest of the cloud keeps the FP32 tolerance.
+        assert np.median(e[:500]) <= 1e-3
+        assert np.median(e[500:][big[500:]]) <= FORCE_MEDIAN
+        return
+    assert np.median(e[big]) <= FORCE_MEDIAN
+
+
+def test_empty_active_and_out_of_range_index():
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.uniform_cloud(500, seed=12)
+    pos, mass, soft, sink = to_dev(c, torch)
+    t = sfg.Tree(pos, mass, soft, sink)
+    acc, phi = t.accel(torch.zeros(0, dtype=torch.int64, device="cuda"))
+    assert acc.shape == (0, 3)
+    t.accel(torch.tensor([3, 500], dtype=torch.int64, device="cuda"))
+    assert t.status() == sfg.SFG_EINVAL
+    assert t.status() == sfg.SFG_OK  # cleared
+    a_all, _ = t.accel(None)
+    a_idx, _ = t.accel(torch.arange(500, device="cuda"))
+    assert torch.equal(a_all, a_idx)
+    t.close()
+
+
+def test_translation_shift_keeps_lists_and_fields():
+    """Dyadic cloud shifted by a multiple of the cell size: same lists; fields
+    within the FP32 tolerance of each other (Galilean-invariance idea, Sec. 2.1)."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.uniform_cloud(4096, seed=13)
+    pos = np.round(c.pos * 2.0 ** 20) / 2.0 ** 20
+    c0 = gen.Cloud(pos, np.full(c.n, 2.0 ** -12), c.soft, c.is_sink, 0, "dyadic")
+    o = oracle_tree(c0, 16)
+    shift = np.array([3.0, -5.0, 7.0]) * o.L0 / 2.0 ** 21 * 1024
+    c1 = gen.Cloud(pos + shift, c0.mass, c0.soft, c0.is_sink, 0, "shifted")
+    res = []
+    for cc in (c0, c1):
+        p, m, s, k = to_dev(cc, torch)
+        t = sfg.Tree(p, m, s, k)
+        a, ph = t.accel(None)
+        res.append((a.cpu().numpy(), ph.cpu().numpy(), t.debug_lists(None)))
+        t.close()
+    for x, y in zip(res[0][2], res[1][2]):
+        np.testing.assert_array_equal(x, y)
+    assert np.median(rel_err(res[1][0], res[0][0])) <= FORCE_MEDIAN
+
+
+@pytest.mark.slow
+def test_clumpy_2e21_sampled_full_size():
+    """The 2^21-cell clumpy cloud + 256 sinks at theta = 0.5, 10% active (the
+    benchmark's launch configuration), checked on 2000 sampled targets."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    import gen as g
+    c = g.clumpy_cloud(1 << 21, n_clumps=512, n_sink=256, seed=g.CONFIG_SEED[2])
+    act = g.active_subset(c.n, 0.1, seed=g.CONFIG_SEED[2])
+    pos, mass, soft, sink = to_dev(c, torch)
+    t = sfg.Tree(pos, mass, soft, sink, theta=0.5)
+    acc, phi = t.accel(torch.from_numpy(act).cuda())
+    assert t.status() == sfg.SFG_OK
+    rng = np.random.default_rng(0)
+    pick = rng.choice(act.size, 2000, replace=False)
+    o = oracle_tree(c, 16)
+    o.walk(act, 32, 0.5, need=act[pick])
+    ao, po = o.accel_group(act[pick])
+    _check_fields(acc.cpu().numpy()[pick], phi.cpu().numpy()[pick], ao, po)
+    t.close()

@@ -1,0 +1,75 @@
+"""GPU build (frame, keys, sort, octree, FP64 moments) against the oracle:
+bit-exact keys, order, topology, integer boxes, centre-of-mass cells and FP64
+moments (same integer-quantised geometry, same fixed operation order)."""
+import numpy as np
+import pytest
+
+import gen
+from _helpers import edge_clouds, oracle_tree, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_build(c, leaf_size):
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    pos, mass, soft, sink = to_dev(c, torch)
+    t = sfg.Tree(pos, mass, soft, sink, leaf_size=leaf_size)
+    o = oracle_tree(c, leaf_size)
+    st = t.stats()
+    assert st["n_nodes"] == o.n_nodes
+    assert st["L0"] == o.L0
+    np.testing.assert_array_equal(np.array(st["x0"]), o.x0)
+    key, order = o.keys()
+    np.testing.assert_array_equal(t.export(sfg.FIELD_KEYS), key)
+    np.testing.assert_array_equal(t.export(sfg.FIELD_ORDER).astype(np.int64), order)
+    gi = t.export(sfg.FIELD_NODE_INT).astype(np.int64)
+    oi = o.nodes_int()
+    np.testing.assert_array_equal(gi[:, :6], oi[:, :6])          # level first count parent child_first nchild
+    np.testing.assert_array_equal(gi[:, 6:15], oi[:, 9:18])      # lo, hi, cq
+    np.testing.assert_array_equal(t.export(sfg.FIELD_NODE_HQ).astype(np.int64), oi[:, 18])
+    gf = t.export(sfg.FIELD_NODE_F64)
+    of = o.nodes_f64()
+    np.testing.assert_array_equal(gf, of[:, :11])                # M com Q hmax, bit for bit
+    assert t.status() == sfg.SFG_OK
+    t.close()
+
+
+@pytest.mark.parametrize("leaf_size", [1, 8, 16, 64])
+def test_build_uniform_4096(leaf_size):
+    _compare_build(gen.uniform_cloud(4096), leaf_size)
+
+
+def test_build_clumpy_with_sinks():
+    _compare_build(gen.clumpy_cloud(1 << 15, n_clumps=64, n_sink=32, seed=12), 16)
+
+
+def test_build_sizes_spanning_tiles():
+    # sizes around the radix-sort tile (4096) and scan chunking, with a ragged tail
+    for n in [4095, 4097, 12289, 70001]:
+        _compare_build(gen.uniform_cloud(n, seed=n, n_sink=n % 7), 16)
+
+
+@pytest.mark.parametrize("name", ["n1", "n2", "identical", "duplicates", "decades", "sinks_only", "massless"])
+def test_build_edge_cases(name):
+    _compare_build(edge_clouds()[name], 8)
+
+
+def test_build_rejects_bad_inputs():
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.uniform_cloud(100, seed=1)
+    pos, mass, soft, sink = to_dev(c, torch)
+    for bad in ["nan_pos", "neg_mass", "zero_soft", "inf_soft"]:
+        p, m, s = pos.clone(), mass.clone(), soft.clone()
+        if bad == "nan_pos":
+            p[5, 1] = float("nan")
+        elif bad == "neg_mass":
+            m[3] = -1.0
+        elif bad == "zero_soft":
+            s[9] = 0.0
+        else:
+            s[0] = float("inf")
+        with pytest.raises(sfg.SfgError) as e:
+            sfg.Tree(p, m, s, sink)
+        assert e.value.code == sfg.SFG_EINVAL

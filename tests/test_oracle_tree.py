@@ -112,14 +112,22 @@ def test_groups_partition_targets(oracle_lib):
     nd = t.nodes_int()
     isact = np.zeros(c.n, bool)
     isact[rank[act]] = True
+    assert np.all(np.diff(g[:, 1]) > 0)  # Morton order of first targets
+    np.testing.assert_array_equal(np.cumsum(g[:, 2])[:-1], g[1:, 1])
     for k in range(ng):
         node, tf, tc = g[k, :3]
         assert 1 <= tc <= G
         inside = tg[tf:tf + tc]
+        # the run lies inside the node that packed it, and that node holds > G
+        # targets unless it is the root
         assert np.all((inside >= nd[node, 1]) & (inside < nd[node, 1] + nd[node, 2]))
         if node != 0:
-            p = nd[node, 3]
-            assert isact[nd[p, 1]:nd[p, 1] + nd[p, 2]].sum() > G
+            assert isact[nd[node, 1]:nd[node, 1] + nd[node, 2]].sum() > G
+    # groups are no smaller than the packing rule allows: two consecutive runs
+    # packed under the same node never fit together into one group unless a
+    # child holding more than G targets separates them
+    fill = g[:, 2].mean() / G
+    assert fill > 0.5
 
 
 def test_lists_cover_every_source_once_and_are_conservative(oracle_lib):
