@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the self-gravity hot path (STARFORGE methods paper, Sec. 2.2).
+
+One step = the whole path over one synthetic cloud: sfg_build (frame, keys,
+sort, octree, FP64 moments) + sfg_accel (groups, walk, FP32 evaluation) at the
+active particles + sfg_accel_vjp (adjoint with frozen lists) for random
+cotangents.  Metric: active-particle gravity evaluations per second
+(= active particles / step time), with the walk kernel's FP32 throughput
+against the GB300 FP32 ALU peak.
+
+Default workload: the clumpy GMC-like cloud -- 2^21 equal-mass cells in 512
+Plummer clumps (70 % of the mass) + 30 % uniform in the unit sphere, 32nd-
+neighbour softening, 256 sinks (log-normal masses, softening 1e-3), theta =
+0.5, quadrupoles, a random 10 % active subset.  Inputs are resident in HBM
+when the timed region starts; L2 (129 MB) is flushed before every timed step
+by writing a 512 MB buffer.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload clumpy-2M|paper-20M] [--active-frac F]
+
+Multi-GPU (torchrun): every rank solves its own independent cloud (seed +
+rank); no collective touches the data path; timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# FP32 operations per interaction, counted from the evaluation source
+# (walk.cu: fwd_p2p Newtonian branch, fwd_p2m with quadrupole / monopole);
+# FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The softened branch's extra work is not
+# counted.
+FLOP_P2P = 21
+FLOP_P2M_QUAD = 55
+FLOP_P2M_MONO = 20
+# Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
+# passes x 32, gather 94, moments + walk records 150).
+BUILD_BYTES_PER_PARTICLE = 576
+
+WORKLOADS = {
+    "clumpy-2M": dict(n_gas=1 << 21, n_clumps=512, n_sink=256, theta=0.5, active=0.1, seed_id=2),
+    "paper-20M": dict(n_gas=20_000_000, n_clumps=2048, n_sink=1024, theta=0.5, active=0.1, seed_id=5),
+    "clumpy-256K": dict(n_gas=1 << 18, n_clumps=128, n_sink=64, theta=0.5, active=0.1, seed_id=2),
+}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_inputs(wl: dict, rank: int, frac: float | None):
+    import gen
+    seed = gen.CONFIG_SEED[wl["seed_id"]] + 1000 * rank
+    c = gen.clumpy_cloud(wl["n_gas"], n_clumps=wl["n_clumps"], n_sink=wl["n_sink"], seed=seed)
+    f = wl["active"] if frac is None else frac
+    act = gen.active_subset(c.n, f, seed=seed)
+    ca, cp = gen.cotangents(act.size, seed=seed + 7)
+    return c, act, ca, cp, f
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl: dict, c, act, ca, cp, sample: int = 4096, seed: int = 0) -> dict:
+    """The oracle as it stands (FP64, OpenMP) on a bounded sample: the full
+    tree build, plus walk + field + adjoint for `sample` random active rows,
+    extrapolated per active row to the whole active set."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(act.size, min(sample, act.size), replace=False))
+    rows = act[pick]
+    t0 = time.perf_counter()
+    tr = oracle.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=16)
+    t1 = time.perf_counter()
+    tr.walk(act, 32, wl["theta"], need=rows)
+    tr.accel_group(rows)
+    t2 = time.perf_counter()
+    tr.vjp(rows[:1], ca[pick[:1]], cp[pick[:1]])
+    t3 = time.perf_counter()
+    tr.vjp(rows, ca[pick], cp[pick])
+    t4 = time.perf_counter()
+    t_build = t1 - t0
+    per_row = ((t2 - t1) + max(0.0, (t4 - t3) - (t3 - t2))) / rows.size
+    t_fixed_vjp = t3 - t2
+    t_step = t_build + t_fixed_vjp + per_row * act.size
+    return {"value": act.size / t_step, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle tree build over all {c.n} particles + group walk, field and adjoint for "
+                      f"{rows.size} of {act.size} active rows; per-row cost extrapolated to all rows",
+            "cpu_seconds_measured": round(t4 - t0, 3), "est_step_s": round(t_step, 4)}
+
+
+def run_reference(args, wl, rank, world):
+    """--impl reference: the CPU oracle on this workload (rank 0 only)."""
+    if rank != 0:
+        return
+    c, act, ca, cp, frac = make_inputs(wl, 0, args.active_frac)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, c, act, ca, cp, sample=1024, seed=1)
+    vals, wall = [], []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        r = cpu_baseline(wl, c, act, ca, cp, sample=2048, seed=10 + k)
+        wall.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "active-particle gravity evaluations per second (build + field + adjoint)",
+            "value": v, "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * act.size / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_particles": int(c.n), "n_active": int(act.size),
+                       "active_frac": frac, "theta": wl["theta"]},
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": v},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS))
+    ap.add_argument("--active-frac", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    import paper_2010_11254_gb300 as sfg
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    os.environ.setdefault("SFG_TIMING", "1")
+
+    c, act, ca, cp, frac = make_inputs(wl, rank, args.active_frac)
+    d_pos = torch.from_numpy(c.pos).to(dev)
+    d_mass = torch.from_numpy(c.mass).to(dev)
+    d_soft = torch.from_numpy(c.soft).to(dev)
+    d_sink = torch.from_numpy(c.is_sink).to(dev)
+    d_act = torch.from_numpy(act).to(dev)
+    d_ca = torch.from_numpy(ca).to(dev)
+    d_cp = torch.from_numpy(cp).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(theta=wl["theta"], leaf_size=16, group_size=32, quadrupole=True)
+
+    def one_step():
+        tree = sfg.Tree(d_pos, d_mass, d_soft, d_sink, **kw)
+        tree.set_timing(True)
+        acc, phi = tree.accel(d_act)
+        g_pos, g_mass = tree.accel_vjp(d_act, d_ca, d_cp)
+        return tree, (acc, phi, g_pos, g_mass)
+
+    for _ in range(args.warmup):
+        tree, out = one_step()
+        tree.check()
+        tree.close()
+
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    times, walk_ms, vjp_walk_ms, fwd_ms, vjp_ms, build_ms = [], [], [], [], [], []
+    p2p = p2m = launches = n_ovf = 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree, out = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = tree.stats()
+        walk_ms.append(st["fwd_walk_ms"])
+        vjp_walk_ms.append(st["vjp_walk_ms"])
+        fwd_ms.append(st["fwd_ms"])
+        vjp_ms.append(st["vjp_ms"])
+        build_ms.append(st["build_ms"])
+        p2p, p2m = st["n_p2p"], st["n_p2m"]
+        n_ovf = st["n_overflow"]
+        launches += st["n_launches"]
+        tree.check()
+        tree.close()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * act.size / (ms_per_step * 1e-3)
+
+    # end to end: pinned host inputs -> device, the three calls, results -> pinned host
+    h_in = [torch.from_numpy(x).pin_memory() for x in (c.pos, c.mass, c.soft, c.is_sink, act, ca, cp)]
+    h_out = [torch.empty((act.size, 3), dtype=torch.float64).pin_memory(),
+             torch.empty(act.size, dtype=torch.float64).pin_memory(),
+             torch.empty((c.n, 3), dtype=torch.float64).pin_memory(),
+             torch.empty(c.n, dtype=torch.float64).pin_memory()]
+    bi = sum(x.numel() * x.element_size() for x in h_in)
+    bo = sum(x.numel() * x.element_size() for x in h_out)
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dv = [x.to(dev, non_blocking=True) for x in h_in]
+        tree = sfg.Tree(dv[0], dv[1], dv[2], dv[3], **kw)
+        acc, phi = tree.accel(dv[4])
+        g_pos, g_mass = tree.accel_vjp(dv[4], dv[5], dv[6])
+        for h, d in zip(h_out, (acc, phi, g_pos, g_mass)):
+            h.copy_(d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        tree.close()
+        if k >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    peaks, peak_src = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    flops = p2p * FLOP_P2P + p2m * FLOP_P2M_QUAD
+    wk = statistics.mean(walk_ms)
+    achieved = flops / (wk * 1e-3) / 1e12
+    line = {
+        "metric": "active-particle gravity evaluations per second (build + field + adjoint)",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
+                   "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"], "leaf_size": 16,
+                   "group_size": 32, "quadrupole": True, "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"independent clouds x{world}"},
+        "roofline": {"bound": "alu", "kernel": "k_walk (forward walk + FP32 evaluation)",
+                     "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
+                     "flops_per_launch": flops, "launch_ms": round(wk, 4),
+                     "flop_model": f"P2P {FLOP_P2P}, P2M quadrupole {FLOP_P2M_QUAD} per interaction"},
+        "phases_ms": {"build": round(statistics.mean(build_ms), 4), "fwd": round(statistics.mean(fwd_ms), 4),
+                      "fwd_walk": round(wk, 4), "vjp": round(statistics.mean(vjp_ms), 4),
+                      "vjp_walk": round(statistics.mean(vjp_walk_ms), 4)},
+        "adjoint_over_forward": round(statistics.mean(vjp_ms) / statistics.mean(fwd_ms), 3),
+        "interactions": {"p2p": int(p2p), "p2m": int(p2m),
+                         "per_active": round((p2p + p2m) / act.size, 1), "overflowed_groups": int(n_ovf),
+                         "fwd_per_s": round((p2p + p2m) / (statistics.mean(fwd_ms) * 1e-3), 1)},
+        "build_hbm": {"algorithmic_GBps": round(BUILD_BYTES_PER_PARTICLE * c.n / (statistics.mean(build_ms) * 1e-3)
+                                                / 1e9, 1), "peak_GBps": peaks.get("hbm_gbs")},
+        "particles_per_s": c.n * world / (ms_per_step * 1e-3),
+        "e2e": {"value": world * act.size / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo, "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, c, act, ca, cp)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,14 @@ typedef struct sfg_stats {
     int64_t n_p2p;        /* particle-particle interactions of the last call (self excluded) */
     int64_t n_p2m;        /* particle-node interactions of the last call */
     int64_t n_overflow;   /* groups that needed the spill traversal buffer */
+    int64_t n_launches;   /* kernels this tree has launched since it was built (build included) */
+    /* with timing on (sfg_set_timing), milliseconds of the last call of each kind,
+     * from CUDA events on the call's stream (0 when off) */
+    float build_ms;       /* whole sfg_build */
+    float fwd_ms;         /* whole sfg_accel */
+    float fwd_walk_ms;    /* its walk + evaluation kernels */
+    float vjp_ms;         /* whole sfg_accel_vjp */
+    float vjp_walk_ms;    /* its walk + adjoint kernels */
 } sfg_stats;
 
 /* Fill *p with the defaults: G = 1, theta = 0.5, leaf_size = 16, group_size = 32,
@@ -128,6 +136,10 @@ int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, doubl
  * Duplicate rows sum.  Errors as for sfg_accel. */
 int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
                   const double *cot_phi, double *d_pos, double *d_mass, void *stream);
+
+/* Turn per-phase CUDA-event timing of later calls on (1) or off (0).  Timing
+ * records a few events per call on the call's stream; it does not synchronize. */
+int sfg_set_timing(sfg_tree *tree, int on);
 
 /* Statistics of the tree and of its last call (host pointer).  Synchronizes. */
 int sfg_get_stats(sfg_tree *tree, sfg_stats *out);

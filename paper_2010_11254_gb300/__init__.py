@@ -49,7 +49,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("depth", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("x0", ctypes.c_double * 3), ("L0", ctypes.c_double),
                 ("n_groups", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("n_p2p", ctypes.c_int64),
-                ("n_p2m", ctypes.c_int64), ("n_overflow", ctypes.c_int64)]
+                ("n_p2m", ctypes.c_int64), ("n_overflow", ctypes.c_int64), ("n_launches", ctypes.c_int64),
+                ("build_ms", ctypes.c_float), ("fwd_ms", ctypes.c_float), ("fwd_walk_ms", ctypes.c_float),
+                ("vjp_ms", ctypes.c_float), ("vjp_walk_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +84,8 @@ def _load():
         lib.sfg_accel_vjp.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.sfg_get_stats.restype = i32
+        lib.sfg_set_timing.argtypes = [vp, i32]
+        lib.sfg_set_timing.restype = i32
         lib.sfg_get_status.argtypes = [vp]
         lib.sfg_get_status.restype = i32
         lib.sfg_free.argtypes = [vp]
@@ -187,6 +191,9 @@ class Tree:
         s = Stats()
         _check(_load().sfg_get_stats(self._h, ctypes.byref(s)), "sfg_get_stats")
         return s.as_dict()
+
+    def set_timing(self, on: bool = True):
+        _check(_load().sfg_set_timing(self._h, int(bool(on))), "sfg_set_timing")
 
     def status(self) -> int:
         return int(_load().sfg_get_status(self._h))

@@ -43,10 +43,28 @@ void dev_free(Tree *t, void *p, cudaStream_t s)
 
 using namespace sfg;
 
+// Keep memory freed to the device's default pool mapped for reuse by later
+// calls (the default release threshold returns it at every synchronization).
+static void keep_pool_memory()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
 static void release(sfg_tree *T)
 {
     Tree *t = &T->t;
     cudaStreamSynchronize(t->stream);
+    for (int k = 0; k < 10; k++)
+        if (t->ev[k]) cudaEventDestroy(t->ev[k]);
     std::vector<void *> ptrs(t->live.begin(), t->live.end());
     for (void *p : ptrs) dev_free(t, p, t->stream);
     cudaStreamSynchronize(t->stream);
@@ -95,11 +113,16 @@ int sfg_build(const double *pos, const double *mass, const double *soft, const u
         p.group_size < 1 || p.group_size > 32 || (p.quadrupole != 0 && p.quadrupole != 1) ||
         (p.precision != 0 && p.precision != 1) || (p.alloc && !p.free))
         return SFG_EINVAL;
+    keep_pool_memory();
     sfg_tree *T = new sfg_tree;
     T->t.prm = p;
     T->t.n = n;
     T->t.stream = (cudaStream_t)stream;
+    const char *env = getenv("SFG_TIMING");
+    T->t.timing = env && env[0] == '1';
+    ph_begin(&T->t, PH_BUILD, (cudaStream_t)stream);
     int rc = build_tree(&T->t, pos, mass, soft, is_sink, (cudaStream_t)stream);
+    ph_end(&T->t, PH_BUILD, (cudaStream_t)stream);
     if (rc != SFG_OK) {
         cudaGetLastError();
         release(T);
@@ -146,7 +169,20 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
     s.n_overflow = (int64_t)c[2];
     s.n_groups = (int64_t)(*(int *)&c[5]);
     s.n_targets = (int64_t)c[6];
+    s.n_launches = t->n_launch;
+    float *ms[5] = {&s.build_ms, &s.fwd_ms, &s.fwd_walk_ms, &s.vjp_ms, &s.vjp_walk_ms};
+    for (int ph = 0; ph < 5; ph++) {
+        *ms[ph] = 0.f;
+        if (t->ev_used[ph]) cudaEventElapsedTime(ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);
+    }
     *out = s;
+    return SFG_OK;
+}
+
+int sfg_set_timing(sfg_tree *tree, int on)
+{
+    if (!tree) return SFG_EINVAL;
+    tree->t.timing = on != 0;
     return SFG_OK;
 }
 

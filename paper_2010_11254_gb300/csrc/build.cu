@@ -113,6 +113,7 @@ size_t scan_scratch_bytes() { return SCAN_NB * sizeof(int); }
 static void scan_range(const int *in, int *out, const int *d_lo, const int *d_hi, int max_n, int *extra_dst,
                        const int *extra_base, void *scratch, cudaStream_t s)
 {
+    // three launches
     int *bsum = (int *)scratch;
     k_scan_reduce<<<SCAN_NB, SCAN_BT, 0, s>>>(in, d_lo, d_hi, max_n, bsum);
     k_scan_top<<<1, SCAN_NB, 0, s>>>(bsum, d_lo, d_hi, max_n, out, extra_dst, extra_base);
@@ -614,6 +615,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     SFG_CUDA_OK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
     SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, 8 * sizeof(unsigned long long), s));
 
+    t->n_launch += 2 + 3; // k_set_int, k_minmax_init, k_validate_minmax, k_frame, k_keys
     k_minmax_init<<<1, 32, 0, s>>>(t->d_minmax);
     k_validate_minmax<<<grid_for(n, BT), BT, 0, s>>>(pos, mass, soft, n, t->d_minmax, t->d_status);
     k_frame<<<1, 1, 0, s>>>(t->d_minmax, t->d_frame, t->d_status);
@@ -633,6 +635,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(d_hn, int, 1);
     ALLOC(scr, int, scan_scratch_bytes() / sizeof(int));
     k_set_int<<<1, 1, 0, s>>>(d_hn, 256 * nb);
+    t->n_launch += 1 + 8 * 5 + 1; // set, 8 x (hist, 3 scan, scatter), pack
     for (int pass = 0; pass < 8; pass++) {
         int shift = 8 * pass;
         k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(k0, n, shift, hist, nb);
@@ -675,6 +678,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         ALLOC(tmp, int, cap + 1);
         ALLOC(tmpo, int, cap + 1);
         k_oct_root<<<1, 1, 0, s>>>(n, t->nfirst, t->ncount, t->nparent, t->nlevel, t->d_lvl);
+        t->n_launch += 1 + (SFG_LMAX + 1) * 5;
         for (int level = 0; level <= SFG_LMAX; level++) {
             k_oct_count<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, tmp, t->d_status);
@@ -748,6 +752,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.arrive = arrive;
     A.nn = nn;
     k_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);
+    t->n_launch += 1;
     dev_free(t, arrive, s);
     dev_free(t, scr, s);
     SFG_CUDA_OK(cudaMemcpyAsync(&t->frame_h, t->d_frame, sizeof(Frame), cudaMemcpyDeviceToHost, s));

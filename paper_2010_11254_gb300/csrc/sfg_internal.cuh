@@ -71,12 +71,16 @@ struct Tree {
     float4 *E0 = nullptr, *E1 = nullptr, *E2 = nullptr;
     double *nM = nullptr, *ncom = nullptr, *nQ = nullptr, *nhmax = nullptr;
     // per-call workspace (grow-only)
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
+    void *ws = nullptr, *ws2 = nullptr;
+    size_t ws_bytes = 0, ws2_bytes = 0;
     sfg_stats last{};
     // [0] p2p, [1] p2m, [2] overflowed groups, [3] work, [4] retry work, [5] groups, [6] distinct targets
     unsigned long long *d_counters = nullptr;
     int *d_n = nullptr; // device copy of n
+    long long n_launch = 0;
+    bool timing = false;
+    cudaEvent_t ev[10] = {};  // pairs: build, fwd, fwd walk, vjp, vjp walk
+    bool ev_used[5] = {false, false, false, false, false};
     std::unordered_set<void *> live; // every device allocation still held
 };
 
@@ -104,6 +108,24 @@ int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_gro
                 int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s);
 
 int num_sms();
+
+// timing helpers (no-ops unless t->timing)
+enum { PH_BUILD = 0, PH_FWD = 1, PH_FWD_WALK = 2, PH_VJP = 3, PH_VJP_WALK = 4 };
+inline void ph_begin(Tree *t, int ph, cudaStream_t s)
+{
+    if (!t->timing) return;
+    if (!t->ev[2 * ph]) {
+        cudaEventCreate(&t->ev[2 * ph]);
+        cudaEventCreate(&t->ev[2 * ph + 1]);
+    }
+    cudaEventRecord(t->ev[2 * ph], s);
+}
+inline void ph_end(Tree *t, int ph, cudaStream_t s)
+{
+    if (!t->timing || !t->ev[2 * ph]) return;
+    cudaEventRecord(t->ev[2 * ph + 1], s);
+    t->ev_used[ph] = true;
+}
 
 // ---- device helpers ----
 __host__ __device__ inline uint64_t spread3(uint32_t v)

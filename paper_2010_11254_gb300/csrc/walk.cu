@@ -70,7 +70,16 @@ struct WalkParams {
     int *ovf_list;
     int *status;
     int2 *gstack;
-    // debug lists
+    // work items: group g is split into K_g items; item i -> g by binary
+    // search of ioff (exclusive prefix of K_g); item k of K evaluates the
+    // tiles t = k (mod K) of the group's walk
+    const int *ioff;
+    const int *kcnt;     // K_g
+    const int *soff;     // first partial slot of a split group
+    int *gdone;          // items finished per split group
+    float4 *part_a;      // [slots][32]
+    double *part_phi;    // [slots][32]
+    // debug lists and costs: 3 ints per group (P2M nodes, P2P leaves, P2P particles)
     int *dbg_counts;
     const long long *dbg_off;
     int *dbg_m, *dbg_p;
@@ -81,12 +90,17 @@ struct WalkParams {
 };
 
 // Target-lane state of one group.
+// Lane layout: the group's T targets are padded to T' = 2^lb >= T; lane l
+// serves target l mod T' and source slice l / T' of every tile (R = 32 / T'
+// slices), so a small group still uses every lane; partial sums are reduced
+// over the slices once per group.
 struct Tgt {
     bool has;
     int r;
     float ox, oy, oz, h, hinv;
     bool sink;
     int cg[3];
+    int tp, R, tl, slice;
 };
 
 // ------------------------------------------------------------ kernels ----
@@ -170,7 +184,7 @@ __device__ __forceinline__ void fwd_p2m(const WarpSmem &S, int cnt, const Tgt &T
 {
     float pt = 0.f;
 #pragma unroll 2
-    for (int k = 0; k < cnt; k++) {
+    for (int k = T.slice; k < cnt; k += T.R) {
         float4 p = S.tP[k];
         float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
         float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -207,7 +221,7 @@ __device__ __forceinline__ void fwd_p2p(const WarpSmem &S, int cnt, const Tgt &T
 {
     float pt = 0.f;
 #pragma unroll 2
-    for (int k = 0; k < cnt; k++) {
+    for (int k = T.slice; k < cnt; k += T.R) {
         float4 p = S.tP[k];
         float4 hh = S.tA[k];
         float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
@@ -239,11 +253,11 @@ __device__ __forceinline__ void fwd_p2p(const WarpSmem &S, int cnt, const Tgt &T
 }
 
 // ------------------------------------------------------- adjoint tiles ----
-// Butterfly sum over the warp; every lane gets the total.
-__device__ __forceinline__ float warp_sum(float v)
+// Sum over the T' lanes of one slice (lanes l..l+T'-1); every lane of the
+// slice gets its slice's total.
+__device__ __forceinline__ float seg_sum(float v, int tp)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    for (int o = 1; o < tp; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
 
@@ -253,10 +267,13 @@ template <bool QUAD>
 __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
-    for (int k = 0; k < cnt; k++) {
-        float4 p = S.tP[k];
+    const int jn = (cnt + T.R - 1) / T.R;
+    for (int jj = 0; jj < jn; jj++) {
+        const int k = jj * T.R + T.slice;
+        const bool ok = k < cnt;
+        float4 p = S.tP[ok ? k : 0];
         float g[10];
-        if (T.has) {
+        if (T.has && ok) {
             float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             float rinv = rsqrtf(r2);
@@ -308,10 +325,10 @@ __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, 
             for (int q = 0; q < 10; q++) g[q] = 0.f;
         }
         const int nq = QUAD ? 10 : 4;
-        double *dst = P.gnode + 10 * (size_t)S.tN[k];
+        double *dst = ok ? P.gnode + 10 * (size_t)S.tN[k] : nullptr;
         for (int q = 0; q < nq; q++) {
-            float v = warp_sum(g[q]);
-            if (lane == q && v != 0.f) atomicAdd(dst + q, (double)v);
+            float v = seg_sum(g[q], T.tp);
+            if (ok && (q & (T.tp - 1)) == T.tl && v != 0.f) atomicAdd(dst + q, (double)v);
         }
     }
 }
@@ -319,12 +336,15 @@ __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, 
 __device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
-    for (int k = 0; k < cnt; k++) {
-        float4 p = S.tP[k];
-        float4 hh = S.tA[k];
+    const int jn = (cnt + T.R - 1) / T.R;
+    for (int jj = 0; jj < jn; jj++) {
+        const int k = jj * T.R + T.slice;
+        const bool ok = k < cnt;
+        float4 p = S.tP[ok ? k : 0];
+        float4 hh = S.tA[ok ? k : 0];
         int j = __float_as_int(hh.z);
         float l0 = 0.f, l1 = 0.f, l2 = 0.f, lm = 0.f;
-        if (T.has && j != T.r) {
+        if (T.has && ok && j != T.r) {
             float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             float ha, hainv, hb, hbinv;
@@ -358,13 +378,17 @@ __device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, 
             gy -= l1;
             gz -= l2;
         }
-        l0 = warp_sum(l0);
-        l1 = warp_sum(l1);
-        l2 = warp_sum(l2);
-        lm = warp_sum(lm);
-        double *dst = P.gpart + 4 * (size_t)j;
-        float v = lane == 0 ? l0 : lane == 1 ? l1 : lane == 2 ? l2 : lm;
-        if (lane < 4 && v != 0.f) atomicAdd(dst + lane, (double)v);
+        l0 = seg_sum(l0, T.tp);
+        l1 = seg_sum(l1, T.tp);
+        l2 = seg_sum(l2, T.tp);
+        lm = seg_sum(lm, T.tp);
+        if (ok) {
+            double *dst = P.gpart + 4 * (size_t)j;
+            for (int q = T.tl; q < 4; q += T.tp) {
+                float v = q == 0 ? l0 : q == 1 ? l1 : q == 2 ? l2 : lm;
+                if (v != 0.f) atomicAdd(dst + q, (double)v);
+            }
+        }
     }
 }
 
@@ -426,16 +450,38 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int 
 }
 
 // ----------------------------------------------------------- the walk ----
+// Advance the P2P range queue by cnt particles without staging them.
+__device__ __forceinline__ void skip_p2p(const WarpSmem &S, int cnt, int &qh, int &qoff)
+{
+    int done = 0;
+    for (int it = 0; done < cnt && it < 66; it++) {
+        int2 hr = S.leafq[qh & 63];
+        int take = min(hr.y - qoff, cnt - done);
+        if (take < 0) take = 0;
+        done += take;
+        qoff += take;
+        if (qoff >= hr.y) {
+            qh++;
+            qoff = 0;
+        }
+    }
+}
+
 template <bool QUAD, int MODE, bool GSTACK>
-__device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int lane)
+__device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int cap = GSTACK ? GSTK : STK;
     const int2 gt = P.gtab[g];
     const int tfirst = gt.x, tcount = gt.y;
     Tgt T;
-    T.has = lane < tcount;
-    T.r = T.has ? P.tgt[tfirst + lane] : -1;
+    T.tp = 1;
+    while (T.tp < tcount) T.tp <<= 1;
+    T.R = 32 / T.tp;
+    T.tl = lane & (T.tp - 1);
+    T.slice = lane / T.tp;
+    T.has = T.tl < tcount;
+    T.r = T.has ? P.tgt[tfirst + T.tl] : -1;
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
     unsigned long long hq = 0;
     double xd[3] = {0, 0, 0};
@@ -475,7 +521,7 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     double phi = 0.0;
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, cf = 0.f;
     if (MODE == MODE_VJP && T.has) {
-        float4 cv = P.cot[tfirst + lane];
+        float4 cv = P.cot[tfirst + T.tl];
         c0 = cv.x;
         c1 = cv.y;
         c2 = cv.z;
@@ -491,6 +537,7 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     __syncwarp();
     int sp = 1, nm = 0, qh = 0, qt = 0, qoff = 0, qn = 0;
     long long tot_m = 0, tot_p = 0, tot_leaf = 0;
+    int tile = 0;
     bool overflow = false;
     // every node is visited at most once per group, so nn + 1 rounds bound the walk
     long long rounds = 0;
@@ -569,17 +616,23 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         qn += lc;
         __syncwarp();
         while (nm >= 32) {
-            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m + nm - 32, 32, T, lane);
-            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (T.has) fwd_p2m<QUAD>(S, 32, T, ax, ay, az, phi);
-            __syncwarp();
+            if (tile++ % K == kk) {
+                stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m + nm - 32, 32, T, lane);
+                if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
+                else if (T.has) fwd_p2m<QUAD>(S, 32, T, ax, ay, az, phi);
+                __syncwarp();
+            }
             nm -= 32;
         }
         while (qn >= 32) {
-            stage_p2p(P, S, 32, qh, qoff, T, lane);
-            if (MODE == MODE_VJP) vjp_p2p(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (T.has) fwd_p2p(S, 32, T, ax, ay, az, phi);
-            __syncwarp();
+            if (tile++ % K == kk) {
+                stage_p2p(P, S, 32, qh, qoff, T, lane);
+                if (MODE == MODE_VJP) vjp_p2p(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
+                else if (T.has) fwd_p2p(S, 32, T, ax, ay, az, phi);
+                __syncwarp();
+            } else {
+                skip_p2p(S, 32, qh, qoff);
+            }
             qn -= 32;
         }
     }
@@ -588,47 +641,91 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
             if (lane == 0) atomicOr(P.status, ST_EOVERFLOW);
         } else if (lane == 0) {
             unsigned long long idx = atomicAdd(&P.counters[2], 1ull);
-            P.ovf_list[idx] = g;
+            P.ovf_list[idx] = item;
         }
         __syncwarp();
         return;
     }
     if (MODE == MODE_COUNT) {
         if (lane == 0) {
-            P.dbg_counts[2 * g] = (int)tot_m;
-            P.dbg_counts[2 * g + 1] = (int)tot_leaf;
+            P.dbg_counts[3 * g] = (int)tot_m;
+            P.dbg_counts[3 * g + 1] = (int)tot_leaf;
+            P.dbg_counts[3 * g + 2] = (int)min(tot_p, (long long)0x7fffffff);
         }
         return;
     }
     if (MODE == MODE_DUMP) return;
     if (nm > 0) {
-        stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m, nm, T, lane);
-        if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, nm, T, c0, c1, c2, cf, ax, ay, az, lane);
-        else if (T.has) fwd_p2m<QUAD>(S, nm, T, ax, ay, az, phi);
-        __syncwarp();
+        if (tile++ % K == kk) {
+            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m, nm, T, lane);
+            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, nm, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2m<QUAD>(S, nm, T, ax, ay, az, phi);
+            __syncwarp();
+        }
     }
     while (qn > 0) {
         int c = min(qn, 32);
-        stage_p2p(P, S, c, qh, qoff, T, lane);
-        if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-        else if (T.has) fwd_p2p(S, c, T, ax, ay, az, phi);
-        __syncwarp();
+        if (tile++ % K == kk) {
+            stage_p2p(P, S, c, qh, qoff, T, lane);
+            if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2p(S, c, T, ax, ay, az, phi);
+            __syncwarp();
+        } else {
+            skip_p2p(S, c, qh, qoff);
+        }
         qn -= c;
     }
+    for (int o = T.tp; o < 32; o <<= 1) {
+        ax += __shfl_xor_sync(FULL, ax, o);
+        ay += __shfl_xor_sync(FULL, ay, o);
+        az += __shfl_xor_sync(FULL, az, o);
+        phi += __shfl_xor_sync(FULL, phi, o);
+    }
     if (MODE == MODE_EVAL) {
-        if (T.has) {
-            P.res_a[tfirst + lane] = make_float4(ax, ay, az, 0.f);
-            P.res_phi[tfirst + lane] = phi;
+        if (K == 1) {
+            if (T.has && T.slice == 0) {
+                P.res_a[tfirst + T.tl] = make_float4(ax, ay, az, 0.f);
+                P.res_phi[tfirst + T.tl] = phi;
+            }
+        } else {
+            // partial sums of this item; the group's last item sums them in k order
+            const size_t slot = (size_t)(P.soff[g] + kk) * 32;
+            if (T.has && T.slice == 0) {
+                P.part_a[slot + T.tl] = make_float4(ax, ay, az, 0.f);
+                P.part_phi[slot + T.tl] = phi;
+            }
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&P.gdone[g], 1) == K - 1;
+            last = __shfl_sync(FULL, last, 0);
+            if (last) {
+                __threadfence();
+                if (T.has && T.slice == 0) {
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                    double ph = 0.0;
+                    const size_t s0 = (size_t)P.soff[g] * 32;
+                    for (int k = 0; k < K; k++) {
+                        float4 v = __ldcg(&P.part_a[s0 + (size_t)k * 32 + T.tl]);
+                        a.x += v.x;
+                        a.y += v.y;
+                        a.z += v.z;
+                        ph += __ldcg(&P.part_phi[s0 + (size_t)k * 32 + T.tl]);
+                    }
+                    P.res_a[tfirst + T.tl] = a;
+                    P.res_phi[tfirst + T.tl] = ph;
+                }
+            }
         }
     } else if (MODE == MODE_VJP) {
-        if (T.has) {
+        if (T.has && T.slice == 0) {
             double *dst = P.gpart + 4 * (size_t)T.r;
             atomicAdd(dst, (double)ax);
             atomicAdd(dst + 1, (double)ay);
             atomicAdd(dst + 2, (double)az);
         }
     }
-    if (lane == 0) {
+    if (lane == 0 && kk == 0) {
         atomicAdd(&P.counters[0], (unsigned long long)(tcount * (tot_p - 1)));
         atomicAdd(&P.counters[1], (unsigned long long)(tcount * tot_m));
     }
@@ -641,15 +738,60 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkParams P)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpSmem &S = sm[w];
     int2 *stack = GSTACK ? P.gstack + (size_t)(blockIdx.x * WALK_WARPS + w) * GSTK : S.stack;
-    const int ngroups = GSTACK ? (int)P.counters[2] : *P.d_ngroups;
+    constexpr bool ITEMS = MODE == MODE_EVAL || MODE == MODE_VJP;
+    const int ngroups = *P.d_ngroups;
+    const int nwork = GSTACK ? (int)P.counters[2] : (ITEMS ? P.ioff[ngroups] : ngroups);
     while (true) {
-        int item = 0;
-        if (lane == 0) item = (int)atomicAdd(&P.counters[GSTACK ? 4 : 3], 1ull);
-        item = __shfl_sync(FULL, item, 0);
-        if (item >= ngroups) break;
-        int g = GSTACK ? P.ovf_list[item] : item;
-        walk_group<QUAD, MODE, GSTACK>(P, S, stack, g, lane);
+        int w_i = 0;
+        if (lane == 0) w_i = (int)atomicAdd(&P.counters[GSTACK ? 4 : 3], 1ull);
+        w_i = __shfl_sync(FULL, w_i, 0);
+        if (w_i >= nwork) break;
+        int item = GSTACK ? P.ovf_list[w_i] : w_i;
+        int g = item, kk = 0, K = 1;
+        if (ITEMS) {
+            int lo = 0, hi = ngroups; // last g with ioff[g] <= item
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (P.ioff[mid] <= item) lo = mid;
+                else hi = mid;
+            }
+            g = lo;
+            kk = item - P.ioff[g];
+            K = P.kcnt[g];
+        }
+        walk_group<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane);
     }
+}
+
+// Work items from the counted list sizes: the sliced iteration count of a
+// group (P2M + P2P sources x T'/32) plus a walk term; groups above SPLIT_ITERS
+// are cut into up to KMAX items, while the partial-sum slot pool lasts.
+constexpr int SPLIT_ITERS = 4096;
+constexpr int KMAX = 32;
+constexpr int PSLOTS = 32768;
+
+__global__ void k_item_counts(const int *cnt3, const int2 *gtab, const int *d_ngroups, int *kcnt, int *is_split)
+{
+    int ng = *d_ngroups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        int tc = gtab[g].y;
+        int tp = 1;
+        while (tp < tc) tp <<= 1;
+        long long src = (long long)cnt3[3 * g] + cnt3[3 * g + 2];
+        long long iters = src * tp / 32 + ((long long)cnt3[3 * g] + cnt3[3 * g + 1]) / 4;
+        long long k = (iters + SPLIT_ITERS - 1) / SPLIT_ITERS;
+        int K = (int)(k < 1 ? 1 : (k > KMAX ? KMAX : k));
+        kcnt[g] = K;
+        is_split[g] = K > 1 ? K : 0;
+    }
+}
+
+// Split groups past the slot pool stay whole.
+__global__ void k_item_cap(const int *soff, const int *d_ngroups, int *kcnt)
+{
+    int ng = *d_ngroups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        if (kcnt[g] > 1 && soff[g] + kcnt[g] > PSLOTS) kcnt[g] = 1;
 }
 
 // ---------------------------------------------------- group formation ----
@@ -755,6 +897,9 @@ struct Work {
     int2 *gtab, *gstack;
     float4 *res_a;
     double *res_phi;
+    int *cnt3, *kcnt, *is_split, *soff, *ioff, *gdone;
+    float4 *part_a;
+    double *part_phi;
 };
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -763,8 +908,11 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
 {
     const size_t n = (size_t)t->n;
     const int retry_warps = num_sms() * WALK_WARPS;
-    size_t sz[12] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, n * 4, scan_scratch_bytes(),
-                     n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8};
+    const size_t NB = 20;
+    size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, n * 4, scan_scratch_bytes(),
+                     n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8,
+                     n * 12, n * 4, n * 4, (n + 1) * 4, (n + 1) * 4, n * 4,
+                     (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8};
     size_t total = 0;
     for (size_t b : sz) total += align_up(b);
     if (t->ws_bytes < total) {
@@ -777,8 +925,8 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
         t->ws_bytes = total;
     }
     char *p = (char *)t->ws;
-    void *ptr[12];
-    for (int k = 0; k < 12; k++) {
+    void *ptr[NB];
+    for (size_t k = 0; k < NB; k++) {
         ptr[k] = p;
         p += align_up(sz[k]);
     }
@@ -794,6 +942,14 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     w.gstack = (int2 *)ptr[9];
     w.res_a = (float4 *)ptr[10];
     w.res_phi = (double *)ptr[11];
+    w.cnt3 = (int *)ptr[12];
+    w.kcnt = (int *)ptr[13];
+    w.is_split = (int *)ptr[14];
+    w.soff = (int *)ptr[15];
+    w.ioff = (int *)ptr[16];
+    w.gdone = (int *)ptr[17];
+    w.part_a = (float4 *)ptr[18];
+    w.part_phi = (double *)ptr[19];
     return SFG_OK;
 }
 
@@ -805,6 +961,7 @@ static int form_groups(Tree *t, const int64_t *active, int64_t n_active, Work &w
     const int n = (int)t->n, BT = 256;
     SFG_CUDA_OK(cudaMemsetAsync(w.flag, 0, sizeof(int) * (size_t)n, s));
     SFG_CUDA_OK(cudaMemsetAsync(w.gflag, 0, sizeof(int) * (size_t)n, s));
+    t->n_launch += 1 + 3 + 1 + 1 + 3 + 1; // mark, scan, compact, marks, scan, table
     k_mark<<<grid_for(n_active, BT), BT, 0, s>>>(active, n_active, n, t->rank, w.flag, t->d_status);
     scan_exclusive(w.flag, w.pre, t->d_n, n, nullptr, nullptr, w.scr, s);
     k_compact<<<grid_for(n, BT), BT, 0, s>>>(w.flag, w.pre, n, w.tgt);
@@ -867,7 +1024,8 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
 template <int MODE>
 static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
 {
-    const int blocks = num_sms() * 4;
+    t->n_launch += 2;
+    const int blocks = num_sms() * 8;
     const int retry_blocks = num_sms();
     if (t->prm.quadrupole) {
         k_walk<true, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
@@ -889,9 +1047,37 @@ static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, Wa
     if (rc) return rc;
     int *d_ngroups = (int *)(t->d_counters + 5);
     k_ngroups<<<1, 1, 0, s>>>(w.pre, (int)t->n, w.goff, t->d_counters);
+    t->n_launch += 1;
     fill_params(t, w, P);
     P.d_ngroups = d_ngroups;
+    P.ioff = w.ioff;
+    P.kcnt = w.kcnt;
+    P.soff = w.soff;
+    P.gdone = w.gdone;
+    P.part_a = w.part_a;
+    P.part_phi = w.part_phi;
     return SFG_OK;
+}
+
+// Count the lists of every group (a walk without evaluation), then cut the
+// heavy groups into work items.
+template <int MODE>
+static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s);
+
+static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+{
+    const int n = (int)t->n, BT = 256;
+    const int *d_ng = P.d_ngroups;
+    P.dbg_counts = w.cnt3;
+    launch_walk<MODE_COUNT>(t, P, s);
+    cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s);
+    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, d_ng, w.kcnt, w.is_split);
+    scan_exclusive(w.is_split, w.soff, d_ng, n, nullptr, nullptr, w.scr, s);
+    k_item_cap<<<grid_for(n, BT), BT, 0, s>>>(w.soff, d_ng, w.kcnt);
+    scan_exclusive(w.kcnt, w.ioff, d_ng, n, nullptr, nullptr, w.scr, s);
+    cudaMemsetAsync(w.gdone, 0, sizeof(int) * (size_t)n, s);
+    t->n_launch += 2 + 3 + 3;
+    P.dbg_counts = nullptr;
 }
 
 int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double *phi, cudaStream_t s)
@@ -900,18 +1086,185 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
     if (t->prm.precision != 0) return SFG_EINVAL; // all-FP64 evaluation is not built yet
     Work w;
     WalkParams P;
+    ph_begin(t, PH_FWD, s);
     int rc = prepare(t, active, n_active, w, P, s);
     if (rc) return rc;
+    ph_begin(t, PH_FWD_WALK, s);
+    make_items(t, w, P, s);
     launch_walk<MODE_EVAL>(t, P, s);
+    ph_end(t, PH_FWD_WALK, s);
     k_rows_out<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, w.res_a,
                                                        w.res_phi, t->prm.G, acc, phi);
+    t->n_launch += 1;
+    ph_end(t, PH_FWD, s);
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
 }
 
-int accel_vjp(Tree *, const int64_t *, int64_t, const double *, const double *, double *, double *, cudaStream_t)
+// ---------------------------------------------------------- adjoint ----
+// Cotangent rows summed per distinct target (duplicate rows add).
+__global__ void k_cot_rows(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
+                           const double *cot_a, const double *cot_phi, double *cotd)
 {
-    return SFG_EINVAL;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) continue;
+        int u = pre[rank[i]];
+        atomicAdd(&cotd[4 * (size_t)u], cot_a[3 * k]);
+        atomicAdd(&cotd[4 * (size_t)u + 1], cot_a[3 * k + 1]);
+        atomicAdd(&cotd[4 * (size_t)u + 2], cot_a[3 * k + 2]);
+        if (cot_phi) atomicAdd(&cotd[4 * (size_t)u + 3], cot_phi[k]);
+    }
+}
+
+__global__ void k_cot_pack(const double *cotd, const int *d_U, float4 *cot)
+{
+    int U = *d_U;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
+        cot[u] = make_float4((float)cotd[4 * (size_t)u], (float)cotd[4 * (size_t)u + 1],
+                             (float)cotd[4 * (size_t)u + 2], (float)cotd[4 * (size_t)u + 3]);
+}
+
+// Node gradients (gM, g_com, g_Q sym) -> per-unit-mass form (gM, v = g_com / M,
+// g_Q).  A massless node's own centre-of-mass and quadrupole terms vanish
+// (its moments do not move to first order when a member's mass leaves zero).
+__global__ void k_gnode_unit(double *gnode, const double *nM, int nn)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        double *g = gnode + 10 * (size_t)i;
+        double M = nM[i];
+        if (M > 0.0) {
+            for (int a = 1; a < 4; a++) g[a] /= M;
+        } else {
+            for (int a = 1; a < 10; a++) g[a] = 0.0;
+        }
+    }
+}
+
+// Top-down, one level at a time: a node's terms, written as a quadratic in a
+// member position x about the node's centre of mass,
+//   dL/dm_k  += gM + v.(x - c) + 3 (x-c)^T S (x-c) - |x-c|^2 tr S
+//   dL/dx_k  += m_k (v + 6 S (x-c) - 2 tr S (x-c)),
+// are re-expanded about each child's centre c' = c + d (exact identity).
+__global__ void k_gnode_push(double *gnode, const double *ncom, const int32_t *nparent, int b, int e)
+{
+    for (int c = b + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x) {
+        int p = nparent[c];
+        const double *gp = gnode + 10 * (size_t)p;
+        double *gc = gnode + 10 * (size_t)c;
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = ncom[3 * (size_t)c + a] - ncom[3 * (size_t)p + a];
+        const double *S = gp + 4; // xx yy zz xy xz yz
+        double tr = S[0] + S[1] + S[2];
+        double Sd[3] = {S[0] * d[0] + S[3] * d[1] + S[4] * d[2], S[3] * d[0] + S[1] * d[1] + S[5] * d[2],
+                        S[4] * d[0] + S[5] * d[1] + S[2] * d[2]};
+        double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double dSd = d[0] * Sd[0] + d[1] * Sd[1] + d[2] * Sd[2];
+        gc[0] += gp[0] + gp[1] * d[0] + gp[2] * d[1] + gp[3] * d[2] + 3.0 * dSd - dd * tr;
+        for (int a = 0; a < 3; a++) gc[1 + a] += gp[1 + a] + 6.0 * Sd[a] - 2.0 * tr * d[a];
+        for (int q = 0; q < 6; q++) gc[4 + q] += S[q];
+    }
+}
+
+// Leaves to their members, then unpermute into the caller's order with G.
+__global__ void k_gleaf(const double *gnode, const double *ncom, const int32_t *nfirst, const int32_t *ncount,
+                        const int32_t *nnchild, int nn, const double *pos_s, const double *mass_s, double *gpart)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        if (nnchild[i] != 0) continue;
+        const double *g = gnode + 10 * (size_t)i;
+        const double *S = g + 4;
+        double tr = S[0] + S[1] + S[2];
+        double c[3] = {ncom[3 * (size_t)i], ncom[3 * (size_t)i + 1], ncom[3 * (size_t)i + 2]};
+        for (int k = nfirst[i]; k < nfirst[i] + ncount[i]; k++) {
+            double s[3];
+            for (int a = 0; a < 3; a++) s[a] = pos_s[3 * (size_t)k + a] - c[a];
+            double Ss[3] = {S[0] * s[0] + S[3] * s[1] + S[4] * s[2], S[3] * s[0] + S[1] * s[1] + S[5] * s[2],
+                            S[4] * s[0] + S[5] * s[1] + S[2] * s[2]};
+            double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+            double sSs = s[0] * Ss[0] + s[1] * Ss[1] + s[2] * Ss[2];
+            double m = mass_s[k];
+            double *o = gpart + 4 * (size_t)k;
+            o[3] += g[0] + g[1] * s[0] + g[2] * s[1] + g[3] * s[2] + 3.0 * sSs - ss * tr;
+            for (int a = 0; a < 3; a++) o[a] += m * (g[1 + a] + 6.0 * Ss[a] - 2.0 * tr * s[a]);
+        }
+    }
+}
+
+__global__ void k_unpermute(const double *gpart, const int32_t *order, int n, double G, double *d_pos,
+                            double *d_mass)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        int i = order[r];
+        const double *g = gpart + 4 * (size_t)r;
+        d_pos[3 * (size_t)i] = G * g[0];
+        d_pos[3 * (size_t)i + 1] = G * g[1];
+        d_pos[3 * (size_t)i + 2] = G * g[2];
+        d_mass[i] = G * g[3];
+    }
+}
+
+int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *cot_a, const double *cot_phi,
+              double *d_pos, double *d_mass, cudaStream_t s)
+{
+    if (t->prm.precision != 0) return SFG_EINVAL;
+    const int n = (int)t->n, nn = t->nn, BT = 256;
+    Work w;
+    WalkParams P;
+    ph_begin(t, PH_VJP, s);
+    int rc = prepare(t, active, n_active, w, P, s);
+    if (rc) return rc;
+    // adjoint workspace: cotd [n][4] f64, cot [n] float4, gpart [n][4] f64, gnode [nn][10] f64
+    size_t need = align_up(32 * (size_t)n) + align_up(16 * (size_t)n) + align_up(32 * (size_t)n) +
+                  align_up(80 * (size_t)nn);
+    if (t->ws2_bytes < need) {
+        if (t->ws2) dev_free(t, t->ws2, s);
+        t->ws2 = dev_alloc(t, need, s);
+        if (!t->ws2) {
+            t->ws2_bytes = 0;
+            return SFG_ENOMEM;
+        }
+        t->ws2_bytes = need;
+    }
+    char *p = (char *)t->ws2;
+    double *cotd = (double *)p;
+    p += align_up(32 * (size_t)n);
+    float4 *cot = (float4 *)p;
+    p += align_up(16 * (size_t)n);
+    double *gpart = (double *)p;
+    p += align_up(32 * (size_t)n);
+    double *gnode = (double *)p;
+    SFG_CUDA_OK(cudaMemsetAsync(cotd, 0, 32 * (size_t)n, s));
+    SFG_CUDA_OK(cudaMemsetAsync(gpart, 0, 32 * (size_t)n, s));
+    SFG_CUDA_OK(cudaMemsetAsync(gnode, 0, 80 * (size_t)nn, s));
+    if (n_active > 0) {
+        k_cot_rows<<<grid_for(n_active, BT), BT, 0, s>>>(active, n_active, n, t->rank, w.pre, cot_a, cot_phi, cotd);
+        k_cot_pack<<<grid_for(n, BT), BT, 0, s>>>(cotd, w.pre + n, cot);
+        P.cot = cot;
+        P.gpart = gpart;
+        P.gnode = gnode;
+        ph_begin(t, PH_VJP_WALK, s);
+        make_items(t, w, P, s);
+        launch_walk<MODE_VJP>(t, P, s);
+        ph_end(t, PH_VJP_WALK, s);
+        k_gnode_unit<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nM, nn);
+        t->n_launch += 4;
+        for (int l = 1; l <= t->depth; l++) {
+            int b = t->lvl_off[l], e = t->lvl_off[l + 1];
+            if (e > b) {
+                k_gnode_push<<<grid_for(e - b, BT), BT, 0, s>>>(gnode, t->ncom, t->nparent, b, e);
+                t->n_launch += 1;
+            }
+        }
+        k_gleaf<<<grid_for(nn, 128), 128, 0, s>>>(gnode, t->ncom, t->nfirst, t->ncount, t->nnchild, nn, t->pos_s,
+                                                  t->mass_s, gpart);
+    }
+    k_unpermute<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->order, n, t->prm.G, d_pos, d_mass);
+    t->n_launch += 1;
+    ph_end(t, PH_VJP, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
 }
 
 int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
@@ -924,22 +1277,22 @@ int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_gro
     int ng = 0;
     SFG_CUDA_OK(cudaMemcpyAsync(&ng, t->d_counters + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
-    int *cnt = (int *)dev_alloc(t, sizeof(int) * 2 * (size_t)(ng > 0 ? ng : 1), s);
+    int *cnt = (int *)dev_alloc(t, sizeof(int) * 3 * (size_t)(ng > 0 ? ng : 1), s);
     if (!cnt) return SFG_ENOMEM;
     P.dbg_counts = cnt;
     launch_walk<MODE_COUNT>(t, P, s);
     int2 *gt_h = (int2 *)malloc(sizeof(int2) * (size_t)(ng > 0 ? ng : 1));
-    int *cnt_h = (int *)malloc(sizeof(int) * 2 * (size_t)(ng > 0 ? ng : 1));
+    int *cnt_h = (int *)malloc(sizeof(int) * 3 * (size_t)(ng > 0 ? ng : 1));
     SFG_CUDA_OK(cudaMemcpyAsync(gt_h, w.gtab, sizeof(int2) * (size_t)ng, cudaMemcpyDeviceToHost, s));
-    SFG_CUDA_OK(cudaMemcpyAsync(cnt_h, cnt, sizeof(int) * 2 * (size_t)ng, cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaMemcpyAsync(cnt_h, cnt, sizeof(int) * 3 * (size_t)ng, cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
     long long tm = 0, tp = 0;
     long long *off_h = (long long *)malloc(sizeof(long long) * 2 * (size_t)(ng > 0 ? ng : 1));
     for (int g = 0; g < ng; g++) {
         off_h[2 * g] = tm;
         off_h[2 * g + 1] = tp;
-        tm += cnt_h[2 * g];
-        tp += cnt_h[2 * g + 1];
+        tm += cnt_h[3 * g];
+        tp += cnt_h[3 * g + 1];
     }
     *n_groups = ng;
     *n_p2m_total = tm;
@@ -948,8 +1301,8 @@ int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_gro
         for (int g = 0; g < ng; g++) {
             groups[4 * g] = gt_h[g].x;
             groups[4 * g + 1] = gt_h[g].y;
-            groups[4 * g + 2] = cnt_h[2 * g];
-            groups[4 * g + 3] = cnt_h[2 * g + 1];
+            groups[4 * g + 2] = cnt_h[3 * g];
+            groups[4 * g + 3] = cnt_h[3 * g + 1];
         }
         long long *off_d = (long long *)dev_alloc(t, sizeof(long long) * 2 * (size_t)(ng > 0 ? ng : 1), s);
         int *dm = (int *)dev_alloc(t, sizeof(int) * (size_t)(tm > 0 ? tm : 1), s);

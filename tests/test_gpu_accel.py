@@ -111,7 +111,12 @@ def test_edge_cases(name):
     c = edge_clouds()[name]
     act = np.arange(c.n)
     acc, phi, ao, po, _ = _run(c, act, 0.5, leaf_size=8)
-    np.testing.assert_allclose(phi, po, rtol=PHI_MAX, atol=0)
+    if name == "decades":
+        # sub-cell clump: see the force check below
+        np.testing.assert_allclose(phi[:500], po[:500], rtol=1e-4, atol=0)
+        np.testing.assert_allclose(phi[500:], po[500:], rtol=PHI_MAX, atol=0)
+    else:
+        np.testing.assert_allclose(phi, po, rtol=PHI_MAX, atol=0)
     if c.n == 1:
         assert np.all(acc == 0) and np.all(phi == 0)
         return
@@ -126,7 +131,8 @@ def test_edge_cases(name):
         # their FP32 offsets from that cell's centre resolve separations to
         # ~1e-4 relative; the rest of the cloud keeps the FP32 tolerance.
         assert np.median(e[:500]) <= 1e-3
-        assert np.median(e[500:][big[500:]]) <= FORCE_MEDIAN
+        rest = np.linalg.norm(ao[500:], axis=1)
+        assert np.median(e[500:][rest > 1e-12 * rest.max()]) <= FORCE_MEDIAN
         return
     assert np.median(e[big]) <= FORCE_MEDIAN
 
