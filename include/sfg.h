@@ -175,9 +175,12 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes);
  * *n_groups, *n_p2m_total and *n_p2p_total; then call again with
  *   groups [n_groups][4] int64: first target (rank in the sorted list of
  *          distinct active particles), target count, P2M list length, P2P
- *          list length (leaves)
+ *          list length (entries)
  *   p2m    [n_p2m_total] int32 accepted node ids, group after group
- *   p2p    [n_p2p_total] int32 opened leaf ids, group after group
+ *   p2p    [n_p2p_total] int32 node ids whose whole particle range is summed
+ *          pair by pair: opened leaves, and internal nodes that lie entirely
+ *          inside the group's softening reach (all their leaves would be
+ *          opened), group after group
  * Each group's entries come in walk order. */
 int sfg_debug_lists(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, int64_t *n_groups,
                     int64_t *n_p2m_total, int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p,

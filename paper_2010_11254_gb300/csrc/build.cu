@@ -413,7 +413,7 @@ struct MomArgs {
     double *nM, *ncom, *nQ, *nhmax;
     float4 *pw;
     int4 *pc;
-    int *arrive;
+    const int *leaves;
     int nn;
 };
 
@@ -541,23 +541,36 @@ __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
     write_records(A, fr, node, level, false, cf, nc, lo, hi, M, com, Q, hmax, cen, ci);
 }
 
-__global__ void k_moments(MomArgs A)
+// Leaves of every level (one thread per leaf), then internal nodes one level
+// at a time from the deepest (one thread per node; its children are final).
+__global__ void k_leaf_moments(MomArgs A)
 {
     const Frame fr = *A.fr;
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < A.nn; node += gridDim.x * blockDim.x) {
-        if (A.nnchild[node] != 0) continue;
-        leaf_moments(A, fr, node);
-        int cur = node;
-        while (true) {
-            int p = A.nparent[cur];
-            if (p < 0) break;
-            __threadfence();
-            int old = atomicAdd(&A.arrive[p], 1);
-            if (old != A.nnchild[p] - 1) break;
-            __threadfence();
-            internal_moments(A, fr, p);
-            cur = p;
-        }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nn; i += gridDim.x * blockDim.x) {
+        int node = A.leaves[i];
+        if (node >= 0) leaf_moments(A, fr, node);
+    }
+}
+
+__global__ void k_internal_moments(MomArgs A, int b, int e)
+{
+    const Frame fr = *A.fr;
+    for (int node = b + blockIdx.x * blockDim.x + threadIdx.x; node < e; node += gridDim.x * blockDim.x)
+        if (A.nnchild[node] != 0) internal_moments(A, fr, node);
+}
+
+// Leaf ids in node order (the slots past the leaf count hold -1).
+__global__ void k_leaf_flags(const int32_t *nnchild, int nn, int *flag)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+        flag[i] = nnchild[i] == 0;
+}
+
+__global__ void k_leaf_list(const int *flag, const int *pre, int nn, int *leaves)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        if (flag[i]) leaves[pre[i]] = i;
+        if (i >= pre[nn]) leaves[i] = -1;
     }
 }
 
@@ -720,9 +733,16 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->ncom, double, 3 * (size_t)nn);
     ALLOC(t->nQ, double, 6 * (size_t)nn);
     ALLOC(t->nhmax, double, nn);
-    int *arrive;
-    ALLOC(arrive, int, nn);
-    SFG_CUDA_OK(cudaMemsetAsync(arrive, 0, sizeof(int) * (size_t)nn, s));
+    int *lflag, *lpre, *leaves, *d_nn;
+    ALLOC(lflag, int, nn);
+    ALLOC(lpre, int, nn + 1);
+    ALLOC(leaves, int, nn);
+    ALLOC(d_nn, int, 1);
+    k_set_int<<<1, 1, 0, s>>>(d_nn, nn);
+    k_leaf_flags<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, nn, lflag);
+    scan_exclusive(lflag, lpre, d_nn, nn, nullptr, nullptr, scr, s);
+    k_leaf_list<<<grid_for(nn, BT), BT, 0, s>>>(lflag, lpre, nn, leaves);
+    t->n_launch += 6;
     MomArgs A;
     A.key = t->key;
     A.pos = t->pos_s;
@@ -749,11 +769,19 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.nhmax = t->nhmax;
     A.pw = t->pw;
     A.pc = t->pc;
-    A.arrive = arrive;
+    A.leaves = leaves;
     A.nn = nn;
-    k_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);
+    k_leaf_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);
     t->n_launch += 1;
-    dev_free(t, arrive, s);
+    for (int l = t->depth - 1; l >= 0; l--) {
+        int b = t->lvl_off[l], e = t->lvl_off[l + 1];
+        k_internal_moments<<<grid_for(e - b, 128), 128, 0, s>>>(A, b, e);
+        t->n_launch += 1;
+    }
+    dev_free(t, lflag, s);
+    dev_free(t, lpre, s);
+    dev_free(t, leaves, s);
+    dev_free(t, d_nn, s);
     dev_free(t, scr, s);
     SFG_CUDA_OK(cudaMemcpyAsync(&t->frame_h, t->d_frame, sizeof(Frame), cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));

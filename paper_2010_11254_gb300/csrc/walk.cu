@@ -34,6 +34,7 @@ namespace sfg {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WALK_WARPS = 4;  // warps per block
+constexpr int WALK_MINB = 6;   // resident blocks per SM the register budget must allow
 constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
 constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
 constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3;
@@ -43,13 +44,14 @@ struct WarpSmem {
     int p2m[64];
     int2 leafq[64];
     float4 tP[32];
-    float4 tA[32]; // P2M: (Qxx, Qyy, Qxy, Qxz); P2P: (h signed, 1/h, j bits, -)
+    float4 tA[32]; // P2M: (Qxx, Qyy, Qxy, Qxz); P2P: (h, 1/h, j bits, sink flag)
     float tB[32];  // P2M: Qyz
     int tN[32];    // P2M: node id (adjoint)
 };
 
 struct WalkParams {
     const int4 *W0, *W1, *W2;
+    const int32_t *nfirst, *ncount;
     const unsigned long long *Whq;
     const float4 *E0, *E1, *E2;
     const float4 *pw;
@@ -70,10 +72,10 @@ struct WalkParams {
     int *ovf_list;
     int *status;
     int2 *gstack;
-    // work items: group g is split into K_g items; item i -> g by binary
-    // search of ioff (exclusive prefix of K_g); item k of K evaluates the
-    // tiles t = k (mod K) of the group's walk
+    // work items: group g is split into K_g items; item k of K evaluates
+    // the tiles t = k (mod K) of the group's walk
     const int *ioff;
+    const int2 *items;   // (group, k), heaviest first
     const int *kcnt;     // K_g
     const int *soff;     // first partial slot of a split group
     int *gdone;          // items finished per split group
@@ -157,24 +159,19 @@ __device__ __forceinline__ void soft_KPR(float r, float rinv, float h, float hin
 }
 
 // Pair rule (Sec. 2.2.1): gas-gas averages the kernels of h_i and h_j; a pair
-// with a sink uses one kernel of support max(h_i, h_j).
-__device__ __forceinline__ void pair_supports(const Tgt &T, float hj_signed, float hjinv, float &ha, float &hainv,
-                                              float &hb, float &hbinv)
+// with a sink uses one kernel of support max(h_i, h_j).  Returned as the two
+// kernels to average: ha = max(h_i, h_j) and hb (= the smaller support for
+// gas-gas, = ha when a sink is involved).  hh = source (h, 1/h, j, sink flag).
+__device__ __forceinline__ void pair_supports(const Tgt &T, const float4 &hh, float &ha, float &hainv, float &hb,
+                                              float &hbinv)
 {
-    float hj = fabsf(hj_signed);
-    bool sink = T.sink || (hj_signed < 0.f);
-    ha = T.h;
-    hainv = T.hinv;
-    hb = hj;
-    hbinv = hjinv;
-    if (sink) {
-        if (hj > T.h) {
-            ha = hj;
-            hainv = hjinv;
-        }
-        hb = ha;
-        hbinv = hainv;
-    }
+    bool sink = T.sink || hh.w != 0.f;
+    bool tbig = T.h >= hh.x;
+    ha = tbig ? T.h : hh.x;
+    hainv = tbig ? T.hinv : hh.y;
+    float lo = tbig ? hh.x : T.h, loinv = tbig ? hh.y : T.hinv;
+    hb = sink ? ha : lo;
+    hbinv = sink ? hainv : loinv;
 }
 
 // ------------------------------------------------------- forward tiles ----
@@ -227,53 +224,53 @@ __device__ __forceinline__ void fwd_p2p(const WarpSmem &S, int cnt, const Tgt &T
         float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
         float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         float m = (__float_as_int(hh.z) == T.r) ? 0.f : p.w;
-        float ha, hainv, hb, hbinv;
-        pair_supports(T, hh.x, hh.y, ha, hainv, hb, hbinv);
-        float hm = fmaxf(ha, hb);
-        float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        float K, P;
+        float hm = fmaxf(T.h, hh.x);
+        float K, Pk;
         if (r2 < hm * hm) {
+            float ha, hainv, hb, hbinv;
+            pair_supports(T, hh, ha, hainv, hb, hbinv);
+            float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
             float r = r2 * rinv;
             float K1, P1, K2, P2;
             soft_KP(r, rinv, ha, hainv, K1, P1);
             soft_KP(r, rinv, hb, hbinv, K2, P2);
             K = 0.5f * (K1 + K2);
-            P = 0.5f * (P1 + P2);
+            Pk = 0.5f * (P1 + P2);
         } else {
+            float rinv = rsqrtf(r2); // r2 >= hm^2 > 0
             K = rinv * rinv * rinv;
-            P = -rinv;
+            Pk = -rinv;
         }
         float mK = m * K;
         ax = fmaf(mK, dx, ax);
         ay = fmaf(mK, dy, ay);
         az = fmaf(mK, dz, az);
-        pt = fmaf(m, P, pt);
+        pt = fmaf(m, Pk, pt);
     }
     phi += (double)pt;
 }
 
 // ------------------------------------------------------- adjoint tiles ----
-// Sum over the T' lanes of one slice (lanes l..l+T'-1); every lane of the
-// slice gets its slice's total.
-__device__ __forceinline__ float seg_sum(float v, int tp)
-{
-    for (int o = 1; o < tp; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
 
-// Target side accumulates -dL/dd in registers; source side is warp-summed and
-// added to the source particle (P2P) or node (P2M) gradients.
+// Target side accumulates -dL/dd in registers.  Source side: within each
+// slice of T' lanes, step j pairs lane t with source (t + j) mod T' of the
+// slice's block of T' sources, and every lane hands its running source
+// accumulator to lane t - 1 after each step; after T' steps lane t holds the
+// complete sum (over the group's targets) for source t of the block and adds
+// it to that source's gradient.
 template <bool QUAD>
 __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
-    const int jn = (cnt + T.R - 1) / T.R;
-    for (int jj = 0; jj < jn; jj++) {
-        const int k = jj * T.R + T.slice;
-        const bool ok = k < cnt;
-        float4 p = S.tP[ok ? k : 0];
-        float g[10];
-        if (T.has && ok) {
+    const int tp = T.tp, base = T.slice * tp;
+    const int nxt = (T.tl + 1) & (tp - 1);
+    float acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; q++) acc[q] = 0.f;
+    for (int j = 0; j < tp; j++) {
+        const int k = base + ((T.tl + j) & (tp - 1));
+        if (T.has && k < cnt) {
+            float4 p = S.tP[k];
             float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             float rinv = rsqrtf(r2);
@@ -284,8 +281,7 @@ __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, 
             float s1 = M * ri3;                           // coefficient of c
             float s2 = M * fmaf(-3.f * cd, ri5, cf * ri3); // coefficient of d
             float gd0 = fmaf(s1, c0, s2 * dx), gd1 = fmaf(s1, c1, s2 * dy), gd2 = fmaf(s1, c2, s2 * dz);
-            g[0] = fmaf(cd, ri3, -cf * rinv);
-            for (int q = 4; q < 10; q++) g[q] = 0.f;
+            acc[0] += fmaf(cd, ri3, -cf * rinv);
             if (QUAD) {
                 float4 q = S.tA[k];
                 float qyz = S.tB[k];
@@ -300,95 +296,102 @@ __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, 
                 float cQd = fmaf(c0, Qd0, fmaf(c1, Qd1, c2 * Qd2));
                 float ri7 = ri5 * ri2, ri9 = ri7 * ri2;
                 // d/dd of c.(-Q d ri5 + 2.5 dQd d ri7) + cf (-0.5 dQd ri5)
-                float aQ = -ri5;                                  // coefficient of Qc
-                float aQd = 5.f * cd * ri7 - cf * ri5;            // coefficient of Qd
+                float aQ = -ri5;                                                          // of Q c
+                float aQd = 5.f * cd * ri7 - cf * ri5;                                    // of Q d
                 float ad = 5.f * cQd * ri7 - 17.5f * dQd * cd * ri9 + 2.5f * cf * dQd * ri7; // of d
-                float ac = 2.5f * dQd * ri7;                      // of c
+                float ac = 2.5f * dQd * ri7;                                              // of c
                 gd0 += aQ * Qc0 + aQd * Qd0 + ad * dx + ac * c0;
                 gd1 += aQ * Qc1 + aQd * Qd1 + ad * dy + ac * c1;
                 gd2 += aQ * Qc2 + aQd * Qd2 + ad * dz + ac * c2;
-                float s = 2.5f * cd * ri7 - 0.5f * cf * ri5;
-                g[4] = fmaf(-c0 * dx, ri5, s * dx * dx);
-                g[5] = fmaf(-c1 * dy, ri5, s * dy * dy);
-                g[6] = fmaf(-c2 * dz, ri5, s * dz * dz);
-                g[7] = fmaf(-0.5f * (c0 * dy + dx * c1), ri5, s * dx * dy);
-                g[8] = fmaf(-0.5f * (c0 * dz + dx * c2), ri5, s * dx * dz);
-                g[9] = fmaf(-0.5f * (c1 * dz + dy * c2), ri5, s * dy * dz);
+                float sQ = 2.5f * cd * ri7 - 0.5f * cf * ri5;
+                acc[4] += fmaf(-c0 * dx, ri5, sQ * dx * dx);
+                acc[5] += fmaf(-c1 * dy, ri5, sQ * dy * dy);
+                acc[6] += fmaf(-c2 * dz, ri5, sQ * dz * dz);
+                acc[7] += fmaf(-0.5f * (c0 * dy + dx * c1), ri5, sQ * dx * dy);
+                acc[8] += fmaf(-0.5f * (c0 * dz + dx * c2), ri5, sQ * dx * dz);
+                acc[9] += fmaf(-0.5f * (c1 * dz + dy * c2), ri5, sQ * dy * dz);
             }
-            g[1] = gd0;
-            g[2] = gd1;
-            g[3] = gd2;
+            acc[1] += gd0;
+            acc[2] += gd1;
+            acc[3] += gd2;
             gx -= gd0;
             gy -= gd1;
             gz -= gd2;
-        } else {
-            for (int q = 0; q < 10; q++) g[q] = 0.f;
         }
-        const int nq = QUAD ? 10 : 4;
-        double *dst = ok ? P.gnode + 10 * (size_t)S.tN[k] : nullptr;
-        for (int q = 0; q < nq; q++) {
-            float v = seg_sum(g[q], T.tp);
-            if (ok && (q & (T.tp - 1)) == T.tl && v != 0.f) atomicAdd(dst + q, (double)v);
-        }
+#pragma unroll
+        for (int q = 0; q < (QUAD ? 10 : 4); q++) acc[q] = __shfl_sync(FULL, acc[q], nxt, tp);
+    }
+    const int k = base + T.tl;
+    if (k < cnt) {
+        double *dst = P.gnode + 10 * (size_t)S.tN[k];
+#pragma unroll
+        for (int q = 0; q < (QUAD ? 10 : 4); q++)
+            if (acc[q] != 0.f) atomicAdd(dst + q, (double)acc[q]);
     }
 }
 
 __device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
-    const int jn = (cnt + T.R - 1) / T.R;
-    for (int jj = 0; jj < jn; jj++) {
-        const int k = jj * T.R + T.slice;
-        const bool ok = k < cnt;
-        float4 p = S.tP[ok ? k : 0];
-        float4 hh = S.tA[ok ? k : 0];
-        int j = __float_as_int(hh.z);
-        float l0 = 0.f, l1 = 0.f, l2 = 0.f, lm = 0.f;
-        if (T.has && ok && j != T.r) {
-            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float ha, hainv, hb, hbinv;
-            pair_supports(T, hh.x, hh.y, ha, hainv, hb, hbinv);
-            float hm = fmaxf(ha, hb);
-            float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-            float K, Pp, R;
-            if (r2 < hm * hm) {
-                float r = r2 * rinv;
-                float K1, P1, R1, K2, P2, R2;
-                soft_KPR(r, rinv, ha, hainv, K1, P1, R1);
-                soft_KPR(r, rinv, hb, hbinv, K2, P2, R2);
-                K = 0.5f * (K1 + K2);
-                Pp = 0.5f * (P1 + P2);
-                R = 0.5f * (R1 + R2);
-            } else {
-                float ri2 = rinv * rinv;
-                K = ri2 * rinv;
-                Pp = -rinv;
-                R = -3.f * K * ri2;
-            }
-            float m = p.w;
-            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
-            float mK = m * K;
-            float s = m * fmaf(R, cd, cf * K);
-            l0 = fmaf(mK, c0, s * dx);
-            l1 = fmaf(mK, c1, s * dy);
-            l2 = fmaf(mK, c2, s * dz);
-            lm = fmaf(K, cd, Pp * cf);
-            gx -= l0;
-            gy -= l1;
-            gz -= l2;
-        }
-        l0 = seg_sum(l0, T.tp);
-        l1 = seg_sum(l1, T.tp);
-        l2 = seg_sum(l2, T.tp);
-        lm = seg_sum(lm, T.tp);
-        if (ok) {
-            double *dst = P.gpart + 4 * (size_t)j;
-            for (int q = T.tl; q < 4; q += T.tp) {
-                float v = q == 0 ? l0 : q == 1 ? l1 : q == 2 ? l2 : lm;
-                if (v != 0.f) atomicAdd(dst + q, (double)v);
+    const int tp = T.tp, base = T.slice * tp;
+    const int nxt = (T.tl + 1) & (tp - 1);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, am = 0.f;
+    for (int jj = 0; jj < tp; jj++) {
+        const int k = base + ((T.tl + jj) & (tp - 1));
+        if (T.has && k < cnt) {
+            float4 p = S.tP[k];
+            float4 hh = S.tA[k];
+            int j = __float_as_int(hh.z);
+            if (j != T.r) {
+                float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ha, hainv, hb, hbinv;
+                pair_supports(T, hh, ha, hainv, hb, hbinv);
+                float hm = ha;
+                float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                float K, Pp, R;
+                if (r2 < hm * hm) {
+                    float r = r2 * rinv;
+                    float K1, P1, R1, K2, P2, R2;
+                    soft_KPR(r, rinv, ha, hainv, K1, P1, R1);
+                    soft_KPR(r, rinv, hb, hbinv, K2, P2, R2);
+                    K = 0.5f * (K1 + K2);
+                    Pp = 0.5f * (P1 + P2);
+                    R = 0.5f * (R1 + R2);
+                } else {
+                    float ri2 = rinv * rinv;
+                    K = ri2 * rinv;
+                    Pp = -rinv;
+                    R = -3.f * K * ri2;
+                }
+                float m = p.w;
+                float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
+                float mK = m * K;
+                float sv = m * fmaf(R, cd, cf * K);
+                float l0 = fmaf(mK, c0, sv * dx);
+                float l1 = fmaf(mK, c1, sv * dy);
+                float l2 = fmaf(mK, c2, sv * dz);
+                a0 += l0;
+                a1 += l1;
+                a2 += l2;
+                am += fmaf(K, cd, Pp * cf);
+                gx -= l0;
+                gy -= l1;
+                gz -= l2;
             }
         }
+        a0 = __shfl_sync(FULL, a0, nxt, tp);
+        a1 = __shfl_sync(FULL, a1, nxt, tp);
+        a2 = __shfl_sync(FULL, a2, nxt, tp);
+        am = __shfl_sync(FULL, am, nxt, tp);
+    }
+    const int k = base + T.tl;
+    if (k < cnt) {
+        double *dst = P.gpart + 4 * (size_t)__float_as_int(S.tA[k].z);
+        if (a0 != 0.f) atomicAdd(dst, (double)a0);
+        if (a1 != 0.f) atomicAdd(dst + 1, (double)a1);
+        if (a2 != 0.f) atomicAdd(dst + 2, (double)a2);
+        if (am != 0.f) atomicAdd(dst + 3, (double)am);
     }
 }
 
@@ -443,13 +446,101 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int 
         float py = fmaf((float)(b.y - T.cg[1]), P.s22, a.y);
         float pz = fmaf((float)(b.z - T.cg[2]), P.s22, a.z);
         S.tP[lane] = make_float4(px, py, pz, a.w);
-        float h = __int_as_float(b.w);
-        S.tA[lane] = make_float4(h, 1.f / fabsf(h), __int_as_float(j), 0.f);
+        float h = __int_as_float(b.w); // negative for a sink
+        float ha = fabsf(h);
+        S.tA[lane] = make_float4(ha, 1.f / ha, __int_as_float(j), h < 0.f ? 1.f : 0.f);
     }
     __syncwarp();
 }
 
 // ----------------------------------------------------------- the walk ----
+// Opening rule for one node against the group box (see the file header):
+// acc = accept (P2M); lf = sum its particle range pair by pair (P2P: an opened
+// leaf, or an internal node wholly inside the group's softening reach, whose
+// leaves would all be opened); op = open (push its children).  link/cnt:
+// child range (op) or particle range (lf).
+__device__ __forceinline__ void test_node(const WalkParams &P, int node, const int glo[3], const int ghi[3],
+                                          unsigned long long hq, bool &acc, bool &lf, bool &op, int &link, int &cnt)
+{
+    acc = lf = op = false;
+    link = cnt = 0;
+    if (node < 0) return;
+    int4 w0 = P.W0[node], w1 = P.W1[node], w2 = P.W2[node];
+    unsigned long long nhq = P.Whq[node];
+    int level = w0.w & 255;
+    bool leaf = (w0.w >> 8) & 1;
+    int gc0 = max(0, max(glo[0] - w2.x - 1, w2.x - ghi[0] - 1));
+    int gc1 = max(0, max(glo[1] - w2.y - 1, w2.y - ghi[1] - 1));
+    int gc2 = max(0, max(glo[2] - w2.z - 1, w2.z - ghi[2] - 1));
+    int gb0 = max(0, max(glo[0] - w1.x - 1, w0.x - ghi[0] - 1));
+    int gb1 = max(0, max(glo[1] - w1.y - 1, w0.y - ghi[1] - 1));
+    int gb2 = max(0, max(glo[2] - w1.z - 1, w0.z - ghi[2] - 1));
+    unsigned long long sc = (unsigned long long)gc0 * (unsigned)gc0 + (unsigned long long)gc1 * (unsigned)gc1 +
+                            (unsigned long long)gc2 * (unsigned)gc2;
+    unsigned long long sb = (unsigned long long)gb0 * (unsigned)gb0 + (unsigned long long)gb1 * (unsigned)gb1 +
+                            (unsigned long long)gb2 * (unsigned)gb2;
+    unsigned long long need = nhq > hq ? nhq : hq;
+    acc = sc >= P.T[level] && sb >= need;
+    lf = !acc && leaf;
+    op = !acc && !leaf;
+    link = w1.w;
+    cnt = w2.w;
+    if (op) {
+        // If even the farthest cell of the node lies inside the group's
+        // softening reach, no descendant can pass clause (ii): every particle
+        // below goes to the P2P list, so take the node's particle range at once.
+        int f0 = max(0, max(w1.x - ghi[0] - 1, glo[0] - w0.x - 1));
+        int f1 = max(0, max(w1.y - ghi[1] - 1, glo[1] - w0.y - 1));
+        int f2 = max(0, max(w1.z - ghi[2] - 1, glo[2] - w0.z - 1));
+        unsigned long long sf = (unsigned long long)f0 * (unsigned)f0 + (unsigned long long)f1 * (unsigned)f1 +
+                                (unsigned long long)f2 * (unsigned)f2;
+        if (sf < hq) {
+            op = false;
+            lf = true;
+            link = P.nfirst[node];
+            cnt = P.ncount[node];
+        }
+    }
+}
+
+// Walk state of one warp for one group.
+struct WalkState {
+    int sp, nm, qh, qt, qoff, qn, tile;
+    int tot_m, tot_p, tot_leaf;
+    float ax, ay, az;
+    double phi;
+    float c0, c1, c2, cf;
+    long long off_m, off_p;
+};
+
+// Append accepted nodes (acc) and P2P ranges (lf) of this round to the lists.
+template <int MODE>
+__device__ __forceinline__ void append_lists(const WalkParams &P, WarpSmem &S, WalkState &W, int node, bool acc,
+                                             bool lf, int link, int cnt, unsigned lt)
+{
+    unsigned ba = __ballot_sync(FULL, acc);
+    unsigned bl = __ballot_sync(FULL, lf);
+    int lc = __reduce_add_sync(FULL, lf ? cnt : 0);
+    W.tot_m += __popc(ba);
+    W.tot_leaf += __popc(bl);
+    W.tot_p += lc;
+    if (MODE == MODE_COUNT || MODE == MODE_DUMP) {
+        if (MODE == MODE_DUMP) {
+            if (acc) P.dbg_m[W.off_m + __popc(ba & lt)] = node;
+            if (lf) P.dbg_p[W.off_p + __popc(bl & lt)] = node;
+            W.off_m += __popc(ba);
+            W.off_p += __popc(bl);
+        }
+        return;
+    }
+    if (acc) S.p2m[W.nm + __popc(ba & lt)] = node;
+    W.nm += __popc(ba);
+    if (lf) S.leafq[(W.qt + __popc(bl & lt)) & 63] = make_int2(link, cnt);
+    W.qt += __popc(bl);
+    W.qn += lc;
+    __syncwarp();
+}
+
 // Advance the P2P range queue by cnt particles without staging them.
 __device__ __forceinline__ void skip_p2p(const WarpSmem &S, int cnt, int &qh, int &qoff)
 {
@@ -467,6 +558,41 @@ __device__ __forceinline__ void skip_p2p(const WarpSmem &S, int cnt, int &qh, in
     }
 }
 
+// Evaluate every full tile (final = false) or everything left (final = true);
+// tiles are numbered in walk order and item kk of K evaluates tiles kk mod K.
+template <bool QUAD, int MODE>
+__device__ __forceinline__ void flush_tiles(const WalkParams &P, WarpSmem &S, WalkState &W, const Tgt &T, int lane,
+                                            bool final, int kk, int K)
+{
+    if (MODE == MODE_COUNT || MODE == MODE_DUMP) return;
+    const int lim = final ? 1 : 32;
+    while (W.nm >= lim) {
+        int c = min(W.nm, 32);
+        if (W.tile++ % K == kk) {
+            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m + W.nm - c, c, T, lane);
+            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, c, T, W.c0, W.c1, W.c2, W.cf, W.ax, W.ay, W.az, lane);
+            else if (T.has) fwd_p2m<QUAD>(S, c, T, W.ax, W.ay, W.az, W.phi);
+            __syncwarp();
+        }
+        W.nm -= c;
+    }
+    while (W.qn >= lim) {
+        int c = min(W.qn, 32);
+        if (W.tile++ % K == kk) {
+            stage_p2p(P, S, c, W.qh, W.qoff, T, lane);
+            if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, W.c0, W.c1, W.c2, W.cf, W.ax, W.ay, W.az, lane);
+            else if (T.has) fwd_p2p(S, c, T, W.ax, W.ay, W.az, W.phi);
+            __syncwarp();
+        } else {
+            skip_p2p(S, c, W.qh, W.qoff);
+        }
+        W.qn -= c;
+    }
+}
+
+// One work item: group g, item kk of K.  Every item of a group walks the same
+// lists (the walk is cheap next to the evaluation) and evaluates the tiles
+// kk, kk + K, ... of the walk order, so the items' work partitions the group's.
 template <bool QUAD, int MODE, bool GSTACK>
 __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item, int lane)
 {
@@ -517,124 +643,63 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         T.oy = (float)(xd[1] - c1);
         T.oz = (float)(xd[2] - c2);
     }
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    double phi = 0.0;
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f, cf = 0.f;
+    WalkState W;
+    W.sp = W.nm = W.qh = W.qt = W.qoff = W.qn = W.tile = 0;
+    W.tot_m = W.tot_p = W.tot_leaf = 0;
+    W.ax = W.ay = W.az = 0.f;
+    W.phi = 0.0;
+    W.c0 = W.c1 = W.c2 = W.cf = 0.f;
+    W.off_m = W.off_p = 0;
     if (MODE == MODE_VJP && T.has) {
         float4 cv = P.cot[tfirst + T.tl];
-        c0 = cv.x;
-        c1 = cv.y;
-        c2 = cv.z;
-        cf = cv.w;
+        W.c0 = cv.x;
+        W.c1 = cv.y;
+        W.c2 = cv.z;
+        W.cf = cv.w;
     }
-    long long off_m = 0, off_p = 0;
     if (MODE == MODE_DUMP) {
-        off_m = P.dbg_off[2 * g];
-        off_p = P.dbg_off[2 * g + 1];
+        W.off_m = P.dbg_off[2 * g];
+        W.off_p = P.dbg_off[2 * g + 1];
     }
 
     if (lane == 0) stack[0] = make_int2(0, 1);
+    W.sp = 1;
     __syncwarp();
-    int sp = 1, nm = 0, qh = 0, qt = 0, qoff = 0, qn = 0;
-    long long tot_m = 0, tot_p = 0, tot_leaf = 0;
-    int tile = 0;
+
     bool overflow = false;
     // every node is visited at most once per group, so nn + 1 rounds bound the walk
-    long long rounds = 0;
-    const long long max_rounds = (long long)P.nn + 1;
-    while (sp > 0) {
+    int rounds = 0;
+    const int max_rounds = P.nn + 1;
+    while (W.sp > 0) {
         if (++rounds > max_rounds) {
             if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
             break;
         }
         int node = -1;
         int taken = 0;
-        while (taken < 32 && sp > 0) {
-            int2 top = stack[sp - 1];
+        while (taken < 32 && W.sp > 0) {
+            int2 top = stack[W.sp - 1];
             int take = min(32 - taken, top.y);
             if (lane >= taken && lane < taken + take) node = top.x + (top.y - take) + (lane - taken);
             taken += take;
             __syncwarp();
-            if (take == top.y) sp--;
-            else if (lane == 0) stack[sp - 1].y = top.y - take;
+            if (take == top.y) W.sp--;
+            else if (lane == 0) stack[W.sp - 1].y = top.y - take;
             __syncwarp();
         }
-        bool acc = false, lf = false, op = false;
-        int link = 0, cnt = 0;
-        if (node >= 0) {
-            int4 w0 = P.W0[node], w1 = P.W1[node], w2 = P.W2[node];
-            unsigned long long nhq = P.Whq[node];
-            int level = w0.w & 255;
-            bool leaf = (w0.w >> 8) & 1;
-            int gc0 = max(0, max(glo[0] - w2.x - 1, w2.x - ghi[0] - 1));
-            int gc1 = max(0, max(glo[1] - w2.y - 1, w2.y - ghi[1] - 1));
-            int gc2 = max(0, max(glo[2] - w2.z - 1, w2.z - ghi[2] - 1));
-            int gb0 = max(0, max(glo[0] - w1.x - 1, w0.x - ghi[0] - 1));
-            int gb1 = max(0, max(glo[1] - w1.y - 1, w0.y - ghi[1] - 1));
-            int gb2 = max(0, max(glo[2] - w1.z - 1, w0.z - ghi[2] - 1));
-            unsigned long long sc = (unsigned long long)gc0 * (unsigned)gc0 +
-                                    (unsigned long long)gc1 * (unsigned)gc1 +
-                                    (unsigned long long)gc2 * (unsigned)gc2;
-            unsigned long long sb = (unsigned long long)gb0 * (unsigned)gb0 +
-                                    (unsigned long long)gb1 * (unsigned)gb1 +
-                                    (unsigned long long)gb2 * (unsigned)gb2;
-            unsigned long long need = nhq > hq ? nhq : hq;
-            acc = sc >= P.T[level] && sb >= need;
-            lf = !acc && leaf;
-            op = !acc && !leaf;
-            link = w1.w;
-            cnt = w2.w;
-        }
-        unsigned ba = __ballot_sync(FULL, acc);
-        unsigned bl = __ballot_sync(FULL, lf);
+        bool acc, lf, op;
+        int link, cnt;
+        test_node(P, node, glo, ghi, hq, acc, lf, op, link, cnt);
         unsigned bo = __ballot_sync(FULL, op);
         int npush = __popc(bo);
-        if (sp + npush > cap) {
+        if (W.sp + npush > cap) {
             overflow = true;
             break;
         }
-        if (op) stack[sp + __popc(bo & lt)] = make_int2(link, cnt);
-        sp += npush;
-        int lc = __reduce_add_sync(FULL, lf ? cnt : 0);
-        tot_m += __popc(ba);
-        tot_leaf += __popc(bl);
-        tot_p += lc;
-        if (MODE == MODE_COUNT || MODE == MODE_DUMP) {
-            if (MODE == MODE_DUMP) {
-                if (acc) P.dbg_m[off_m + __popc(ba & lt)] = node;
-                if (lf) P.dbg_p[off_p + __popc(bl & lt)] = node;
-                off_m += __popc(ba);
-                off_p += __popc(bl);
-            }
-            __syncwarp();
-            continue;
-        }
-        if (acc) S.p2m[nm + __popc(ba & lt)] = node;
-        nm += __popc(ba);
-        if (lf) S.leafq[(qt + __popc(bl & lt)) & 63] = make_int2(link, cnt);
-        qt += __popc(bl);
-        qn += lc;
-        __syncwarp();
-        while (nm >= 32) {
-            if (tile++ % K == kk) {
-                stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m + nm - 32, 32, T, lane);
-                if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
-                else if (T.has) fwd_p2m<QUAD>(S, 32, T, ax, ay, az, phi);
-                __syncwarp();
-            }
-            nm -= 32;
-        }
-        while (qn >= 32) {
-            if (tile++ % K == kk) {
-                stage_p2p(P, S, 32, qh, qoff, T, lane);
-                if (MODE == MODE_VJP) vjp_p2p(P, S, 32, T, c0, c1, c2, cf, ax, ay, az, lane);
-                else if (T.has) fwd_p2p(S, 32, T, ax, ay, az, phi);
-                __syncwarp();
-            } else {
-                skip_p2p(S, 32, qh, qoff);
-            }
-            qn -= 32;
-        }
+        if (op) stack[W.sp + __popc(bo & lt)] = make_int2(link, cnt);
+        W.sp += npush;
+        append_lists<MODE>(P, S, W, node, acc, lf, link, cnt, lt);
+        flush_tiles<QUAD, MODE>(P, S, W, T, lane, false, kk, K);
     }
     if (overflow) {
         if (GSTACK) {
@@ -648,33 +713,16 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     }
     if (MODE == MODE_COUNT) {
         if (lane == 0) {
-            P.dbg_counts[3 * g] = (int)tot_m;
-            P.dbg_counts[3 * g + 1] = (int)tot_leaf;
-            P.dbg_counts[3 * g + 2] = (int)min(tot_p, (long long)0x7fffffff);
+            P.dbg_counts[3 * g] = W.tot_m;
+            P.dbg_counts[3 * g + 1] = W.tot_leaf;
+            P.dbg_counts[3 * g + 2] = W.tot_p;
         }
         return;
     }
     if (MODE == MODE_DUMP) return;
-    if (nm > 0) {
-        if (tile++ % K == kk) {
-            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, S.p2m, nm, T, lane);
-            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, nm, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (T.has) fwd_p2m<QUAD>(S, nm, T, ax, ay, az, phi);
-            __syncwarp();
-        }
-    }
-    while (qn > 0) {
-        int c = min(qn, 32);
-        if (tile++ % K == kk) {
-            stage_p2p(P, S, c, qh, qoff, T, lane);
-            if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (T.has) fwd_p2p(S, c, T, ax, ay, az, phi);
-            __syncwarp();
-        } else {
-            skip_p2p(S, c, qh, qoff);
-        }
-        qn -= c;
-    }
+    flush_tiles<QUAD, MODE>(P, S, W, T, lane, true, kk, K);
+    float ax = W.ax, ay = W.ay, az = W.az;
+    double phi = W.phi;
     for (int o = T.tp; o < 32; o <<= 1) {
         ax += __shfl_xor_sync(FULL, ax, o);
         ay += __shfl_xor_sync(FULL, ay, o);
@@ -726,13 +774,14 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         }
     }
     if (lane == 0 && kk == 0) {
-        atomicAdd(&P.counters[0], (unsigned long long)(tcount * (tot_p - 1)));
-        atomicAdd(&P.counters[1], (unsigned long long)(tcount * tot_m));
+        // every item walks the whole list: count it once (self pairs excluded)
+        atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(W.tot_p - 1));
+        atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)W.tot_m);
     }
 }
 
 template <bool QUAD, int MODE, bool GSTACK>
-__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkParams P)
+__global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams P)
 {
     __shared__ WarpSmem sm[WALK_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -749,14 +798,9 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkParams P)
         int item = GSTACK ? P.ovf_list[w_i] : w_i;
         int g = item, kk = 0, K = 1;
         if (ITEMS) {
-            int lo = 0, hi = ngroups; // last g with ioff[g] <= item
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (P.ioff[mid] <= item) lo = mid;
-                else hi = mid;
-            }
-            g = lo;
-            kk = item - P.ioff[g];
+            int2 it = P.items[item];
+            g = it.x;
+            kk = it.y;
             K = P.kcnt[g];
         }
         walk_group<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane);
@@ -768,21 +812,82 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkParams P)
 // are cut into up to KMAX items, while the partial-sum slot pool lasts.
 constexpr int SPLIT_ITERS = 4096;
 constexpr int KMAX = 32;
-constexpr int PSLOTS = 32768;
+constexpr int PSLOTS = 65536;
 
-__global__ void k_item_counts(const int *cnt3, const int2 *gtab, const int *d_ngroups, int *kcnt, int *is_split)
+__device__ inline long long group_iters(const int *cnt3, int tc, int g)
+{
+    int tp = 1;
+    while (tp < tc) tp <<= 1;
+    long long src = (long long)cnt3[3 * g] + cnt3[3 * g + 2];
+    return src * tp / 32 + ((long long)cnt3[3 * g] + cnt3[3 * g + 1]) / 4 + 32;
+}
+
+// Total estimated cost of all groups (one 64-bit atomic per warp).
+__global__ void k_item_total(const int *cnt3, const int2 *gtab, const int *d_ngroups, unsigned long long *total)
 {
     int ng = *d_ngroups;
+    unsigned long long acc = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        acc += (unsigned long long)group_iters(cnt3, gtab[g].y, g);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+// Split size: at least SPLIT_ITERS, and at least a third of one resident
+// warp's share of the total, so the split groups need at most ~6 slots per
+// resident warp (the slot pool holds PSLOTS) and every item stays small next
+// to a warp's share (longest-first scheduling then balances the rest).
+__global__ void k_item_counts(const int *cnt3, const int2 *gtab, const int *d_ngroups,
+                              const unsigned long long *total, long long warps, int *kcnt, int *is_split)
+{
+    int ng = *d_ngroups;
+    long long C = (long long)(*total / (unsigned long long)(3 * warps));
+    if (C < SPLIT_ITERS) C = SPLIT_ITERS;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        int tc = gtab[g].y;
-        int tp = 1;
-        while (tp < tc) tp <<= 1;
-        long long src = (long long)cnt3[3 * g] + cnt3[3 * g + 2];
-        long long iters = src * tp / 32 + ((long long)cnt3[3 * g] + cnt3[3 * g + 1]) / 4;
-        long long k = (iters + SPLIT_ITERS - 1) / SPLIT_ITERS;
+        long long iters = group_iters(cnt3, gtab[g].y, g);
+        long long k = (iters + C - 1) / C;
         int K = (int)(k < 1 ? 1 : (k > KMAX ? KMAX : k));
         kcnt[g] = K;
         is_split[g] = K > 1 ? K : 0;
+    }
+}
+
+// Longest first: items are bucketed by log2 of their estimated cost and the
+// buckets are issued from the most to the least expensive.
+__device__ inline int cost_bucket(const int *cnt3, const int2 *gtab, const int *kcnt, int g)
+{
+    long long c = group_iters(cnt3, gtab[g].y, g) / kcnt[g];
+    int b = 63 - __clzll(c > 1 ? c : 1);
+    return 31 - min(b, 31);
+}
+
+__global__ void k_item_hist(const int *cnt3, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *hist)
+{
+    int ng = *d_ngroups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        atomicAdd(&hist[cost_bucket(cnt3, gtab, kcnt, g)], kcnt[g]);
+}
+
+__global__ void k_item_scan(int *hist)
+{
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 32; b++) {
+            int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void k_item_fill(const int *cnt3, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *cursor,
+                            int2 *items)
+{
+    int ng = *d_ngroups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        int K = kcnt[g];
+        int base = atomicAdd(&cursor[cost_bucket(cnt3, gtab, kcnt, g)], K);
+        for (int k = 0; k < K; k++) items[base + k] = make_int2(g, k);
     }
 }
 
@@ -897,7 +1002,8 @@ struct Work {
     int2 *gtab, *gstack;
     float4 *res_a;
     double *res_phi;
-    int *cnt3, *kcnt, *is_split, *soff, *ioff, *gdone;
+    int *cnt3, *kcnt, *is_split, *soff, *ioff, *gdone, *hist;
+    int2 *items;
     float4 *part_a;
     double *part_phi;
 };
@@ -908,11 +1014,11 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
 {
     const size_t n = (size_t)t->n;
     const int retry_warps = num_sms() * WALK_WARPS;
-    const size_t NB = 20;
-    size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, n * 4, scan_scratch_bytes(),
+    const size_t NB = 22;
+    size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, (n + PSLOTS) * 4, scan_scratch_bytes(),
                      n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8,
                      n * 12, n * 4, n * 4, (n + 1) * 4, (n + 1) * 4, n * 4,
-                     (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8};
+                     (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8, 64 * 4, (n + PSLOTS) * 8};
     size_t total = 0;
     for (size_t b : sz) total += align_up(b);
     if (t->ws_bytes < total) {
@@ -950,6 +1056,8 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     w.gdone = (int *)ptr[17];
     w.part_a = (float4 *)ptr[18];
     w.part_phi = (double *)ptr[19];
+    w.hist = (int *)ptr[20];
+    w.items = (int2 *)ptr[21];
     return SFG_OK;
 }
 
@@ -986,6 +1094,8 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.W0 = t->W0;
     P.W1 = t->W1;
     P.W2 = t->W2;
+    P.nfirst = t->nfirst;
+    P.ncount = t->ncount;
     P.Whq = t->Whq;
     P.E0 = t->E0;
     P.E1 = t->E1;
@@ -1025,7 +1135,7 @@ template <int MODE>
 static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
 {
     t->n_launch += 2;
-    const int blocks = num_sms() * 8;
+    const int blocks = num_sms() * WALK_MINB;
     const int retry_blocks = num_sms();
     if (t->prm.quadrupole) {
         k_walk<true, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
@@ -1051,6 +1161,7 @@ static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, Wa
     fill_params(t, w, P);
     P.d_ngroups = d_ngroups;
     P.ioff = w.ioff;
+    P.items = w.items;
     P.kcnt = w.kcnt;
     P.soff = w.soff;
     P.gdone = w.gdone;
@@ -1071,12 +1182,20 @@ static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
     P.dbg_counts = w.cnt3;
     launch_walk<MODE_COUNT>(t, P, s);
     cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s);
-    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, d_ng, w.kcnt, w.is_split);
+    unsigned long long *total = t->d_counters + 7;
+    cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, d_ng, total);
+    const long long warps = (long long)num_sms() * WALK_MINB * WALK_WARPS;
+    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, d_ng, total, warps, w.kcnt, w.is_split);
     scan_exclusive(w.is_split, w.soff, d_ng, n, nullptr, nullptr, w.scr, s);
     k_item_cap<<<grid_for(n, BT), BT, 0, s>>>(w.soff, d_ng, w.kcnt);
     scan_exclusive(w.kcnt, w.ioff, d_ng, n, nullptr, nullptr, w.scr, s);
     cudaMemsetAsync(w.gdone, 0, sizeof(int) * (size_t)n, s);
-    t->n_launch += 2 + 3 + 3;
+    cudaMemsetAsync(w.hist, 0, 32 * sizeof(int), s);
+    k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, w.kcnt, d_ng, w.hist);
+    k_item_scan<<<1, 32, 0, s>>>(w.hist);
+    k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, w.kcnt, d_ng, w.hist, w.items);
+    t->n_launch += 2 + 1 + 3 + 3 + 3;
     P.dbg_counts = nullptr;
 }
 

@@ -30,19 +30,29 @@ def _run(c, active, theta, leaf_size=16, group_size=32, quad=True, check_lists=T
     if check_lists:
         groups, p2m, p2p = t.debug_lists(act)
         og = o.groups()
+        nodes = o.nodes_int()
         np.testing.assert_array_equal(groups[:, 0], og[:, 1])
         np.testing.assert_array_equal(groups[:, 1], og[:, 2])
         np.testing.assert_array_equal(groups[:, 2], og[:, 4])
-        np.testing.assert_array_equal(groups[:, 3], og[:, 5])
         om = np.cumsum(np.r_[0, groups[:, 2]])
         op = np.cumsum(np.r_[0, groups[:, 3]])
         for g in range(len(og)):
             lm, lp = o.group_lists(g, og)
             np.testing.assert_array_equal(np.sort(p2m[om[g]:om[g + 1]]), np.sort(lm))
-            np.testing.assert_array_equal(np.sort(p2p[op[g]:op[g + 1]]), np.sort(lp))
+            # P2P entries are node ids whose particle ranges are summed pair by
+            # pair; compare the particle sets
+            assert particles_of(nodes, p2p[op[g]:op[g + 1]]) == particles_of(nodes, lp)
     ao, po = o.accel_group(active, G=G, quadrupole=quad)
     t.close()
     return acc.cpu().numpy(), phi.cpu().numpy(), ao, po, st
+
+
+def particles_of(nodes, ids):
+    """Sorted tuple of the sorted-rank particle indices covered by node ids."""
+    if len(ids) == 0:
+        return ()
+    parts = [np.arange(nodes[i, 1], nodes[i, 1] + nodes[i, 2]) for i in ids]
+    return tuple(np.sort(np.concatenate(parts)).tolist())
 
 
 def _check_fields(acc, phi, ao, po):
