@@ -186,6 +186,29 @@ int sfg_debug_lists(sfg_tree *tree, const int64_t *active_idx, int64_t n_active,
                     int64_t *n_p2m_total, int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p,
                     void *stream);
 
+/* ---- allocation-free variant ----
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory at call time, e.g. an application whose device
+ * memory is entirely reserved up front by its own pool, or a latency-bound
+ * loop that must not run cudaMalloc (which can block the host and serialize
+ * work on the device).
+ *
+ * sfg_sort_keys_static computes what sfg_build computes first -- the frame,
+ * the 63-bit Morton keys and their stable sort -- for n <= SFG_STATIC_MAX_N
+ * particles without allocating anything:
+ *   pos       [n][3] float64, device, finite (not checked)
+ *   key_out   [n] uint64, device: the sorted keys (as SFG_FIELD_KEYS)
+ *   order_out [n] int32, device: sorted rank -> original index (as SFG_FIELD_ORDER)
+ * Temporary buffers live in one fixed array of about 6.5 MB that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (make it before any stream
+ * capture); later calls reuse it.  All calls share the array, so calls that
+ * overlap on the GPU (different streams or threads) race: serialize them.
+ * Returns SFG_EINVAL for NULL pointers, n <= 0 or n > SFG_STATIC_MAX_N, and
+ * SFG_ECUDA if the address lookup or a launch fails. */
+#define SFG_STATIC_MAX_N (1 << 19)
+int sfg_sort_keys_static(const double *pos, int64_t n, uint64_t *key_out, int32_t *order_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "sfg_internal.cuh"
 
 namespace sfg {
@@ -790,3 +792,117 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
 }
 
 } // namespace sfg
+
+// ------------------------------------------------ fixed-scratch key sort ----
+// Frame, Morton keys and their stable sort order for up to SFG_STATIC_MAX_N
+// particles, with every temporary buffer carved from one file-scope device
+// array, so the call performs no device allocation.  The caller's outputs
+// double as one side of the radix sort's ping-pong buffers.
+namespace sfg {
+
+constexpr int ST_NB = (SFG_STATIC_MAX_N + RS_TILE - 1) / RS_TILE;
+constexpr size_t st_al(size_t x) { return (x + 255) & ~(size_t)255; } // every region starts on 256 bytes
+constexpr size_t ST_OFF_MINMAX = 0;                                             // 6 x u64
+constexpr size_t ST_OFF_FRAME = 256;                                            // Frame
+constexpr size_t ST_OFF_HN = 512;                                               // 2 ints
+constexpr size_t ST_OFF_SCAN = 1024;                                            // SCAN_NB ints
+constexpr size_t ST_OFF_HIST = st_al(ST_OFF_SCAN + SCAN_NB * 4);                // 256 * ST_NB ints
+constexpr size_t ST_OFF_HOFF = st_al(ST_OFF_HIST + 256 * (size_t)ST_NB * 4);    // 256 * ST_NB + 1 ints
+constexpr size_t ST_OFF_KEYS = st_al(ST_OFF_HOFF + (256 * (size_t)ST_NB + 1) * 4);
+constexpr size_t ST_OFF_VALS = st_al(ST_OFF_KEYS + (size_t)SFG_STATIC_MAX_N * 8);
+constexpr size_t ST_BYTES = st_al(ST_OFF_VALS + (size_t)SFG_STATIC_MAX_N * 4);
+static_assert(ST_OFF_KEYS % 256 == 0 && ST_OFF_VALS % 256 == 0 && ST_OFF_HIST % 256 == 0, "scratch alignment");
+static_assert(sizeof(Frame) <= 256 && SCAN_NB * 4 <= 4096, "scratch layout");
+
+static __device__ __align__(256) unsigned char g_sort_scratch[ST_BYTES];
+
+__global__ void k_minmax_pos(const double *pos, int n, unsigned long long *mm)
+{
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; a++) {
+            unsigned long long u = ord_of(pos[3 * (size_t)i + a]);
+            lo[a] = u < lo[a] ? u : lo[a];
+            hi[a] = u > hi[a] ? u : hi[a];
+        }
+    for (int a = 0; a < 3; a++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo[a], o);
+            unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi[a], o);
+            lo[a] = l2 < lo[a] ? l2 : lo[a];
+            hi[a] = h2 > hi[a] ? h2 : hi[a];
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[a], lo[a]);
+            atomicMax(&mm[3 + a], hi[a]);
+        }
+    }
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the symbol's host-side name is not a device address).
+static int static_scratch(unsigned char **out)
+{
+    static std::mutex mu;
+    static unsigned char *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SFG_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SFG_ECUDA;
+        }
+        addr[dev] = (unsigned char *)p;
+    }
+    *out = addr[dev];
+    return SFG_OK;
+}
+
+} // namespace sfg
+
+extern "C" int sfg_sort_keys_static(const double *pos, int64_t n, uint64_t *key_out, int32_t *order_out,
+                                    void *stream)
+{
+    using namespace sfg;
+    if (!pos || !key_out || !order_out || n <= 0) return SFG_EINVAL;
+    if (n > SFG_STATIC_MAX_N) return SFG_EINVAL;
+    unsigned char *base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc != SFG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nn = (int)n, BT = 256;
+    unsigned long long *mm = (unsigned long long *)(base + ST_OFF_MINMAX);
+    Frame *fr = (Frame *)(base + ST_OFF_FRAME);
+    int *hn = (int *)(base + ST_OFF_HN);
+    int *scr = (int *)(base + ST_OFF_SCAN);
+    int *hist = (int *)(base + ST_OFF_HIST);
+    int *hoff = (int *)(base + ST_OFF_HOFF);
+    uint64_t *kb = (uint64_t *)(base + ST_OFF_KEYS);
+    uint32_t *vb = (uint32_t *)(base + ST_OFF_VALS);
+    const int nb = (nn + RS_TILE - 1) / RS_TILE;
+    int *scratch_status = hn + 1; // k_frame reports an unsupported extent here; positions must be finite
+    k_minmax_init<<<1, 32, 0, s>>>(mm);
+    k_minmax_pos<<<grid_for(nn, BT), BT, 0, s>>>(pos, nn, mm);
+    k_frame<<<1, 1, 0, s>>>(mm, fr, scratch_status);
+    uint64_t *ka = key_out, *kx = kb;
+    uint32_t *va = (uint32_t *)order_out, *vx = vb;
+    k_keys<<<grid_for(nn, BT), BT, 0, s>>>(pos, nn, fr, ka, va);
+    k_set_int<<<1, 1, 0, s>>>(hn, 256 * nb);
+    for (int pass = 0; pass < 8; pass++) {
+        int shift = 8 * pass;
+        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(ka, nn, shift, hist, nb);
+        scan_exclusive(hist, hoff, hn, 256 * nb, nullptr, nullptr, scr, s);
+        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(ka, va, kx, vx, nn, shift, hoff, nb);
+        uint64_t *tk = ka;
+        ka = kx;
+        kx = tk;
+        uint32_t *tv = va;
+        va = vx;
+        vx = tv;
+    }
+    // 8 passes: the sorted keys and order are back in the caller's buffers
+    if (cudaGetLastError() != cudaSuccess) return SFG_ECUDA;
+    return SFG_OK;
+}
