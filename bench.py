@@ -45,6 +45,14 @@ if ROOT not in sys.path:
 FLOP_P2P = 21
 FLOP_P2M_QUAD = 55
 FLOP_P2M_MONO = 20
+# Adjoint (walk.cu: vjp_p2p Newtonian branch, vjp_p2m with quadrupole), same
+# counting rule; the source-side rotation shuffles are not counted.
+FLOP_VJP_P2P = 43
+FLOP_VJP_P2M_QUAD = 174
+# DRAM bytes per launch of the walk kernels on the default workload
+# (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture; see
+# profiles/), valid only for the walk source they were taken on.
+WALK_TRAFFIC = {"sha256": None, "fwd": None, "vjp": None}
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576
@@ -153,6 +161,32 @@ def cpu_baseline(wl: dict, c, act, ca, cp, sample: int = 4096, seed: int = 0) ->
             "cpu_seconds_measured": round(t4 - t0, 3), "est_step_s": round(t_step, 4)}
 
 
+def force_error(c, act, acc, phi, sample: int = 1000, seed: int = 0) -> dict:
+    """Median and 99th-percentile relative force error of the GPU result
+    against the FP64 direct sum (the oracle) on sampled active rows."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(act.size, min(sample, act.size), replace=False))
+    ad, pd = oracle.direct(c.pos, c.mass, c.soft, c.is_sink, act[pick])
+    e = np.linalg.norm(acc[pick] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    ep = np.abs(phi[pick] - pd) / np.abs(pd)
+    return {"vs": "FP64 direct sum", "sample": int(pick.size), "median": float(np.median(e)),
+            "p99": float(np.percentile(e, 99)), "phi_median": float(np.median(ep)),
+            "phi_p99": float(np.percentile(ep, 99))}
+
+
+def aggregate(local_ms: float, units_per_rank: int, world: int, dist=None, device=None):
+    """Whole-job throughput: every rank did `units_per_rank` in local_ms; the
+    job time is the slowest rank's (max over ranks)."""
+    t = local_ms
+    if dist is not None and world > 1:
+        import torch
+        v = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+    return t, world * units_per_rank / (t * 1e-3)
+
+
 def run_reference(args, wl, rank, world):
     """--impl reference: the CPU oracle on this workload (rank 0 only)."""
     if rank != 0:
@@ -187,6 +221,8 @@ def main():
     ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS))
     ap.add_argument("--active-frac", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
@@ -218,7 +254,7 @@ def main():
     d_cp = torch.from_numpy(cp).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    kw = dict(theta=wl["theta"], leaf_size=16, group_size=32, quadrupole=True)
+    kw = dict(theta=wl["theta"], leaf_size=16, group_size=32, quadrupole=True, precision=args.precision)
 
     def one_step():
         tree = sfg.Tree(d_pos, d_mass, d_soft, d_sink, **kw)
@@ -261,14 +297,10 @@ def main():
         tree.close()
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    total_ms = sum(times)
+    acc_h, phi_h = out[0].cpu().numpy(), out[1].cpu().numpy()
     if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = world * act.size / (ms_per_step * 1e-3)
+    ms_per_step, value = aggregate(sum(times) / args.steps, act.size, world, dist, dev)
 
     # end to end: pinned host inputs -> device, the three calls, results -> pinned host
     h_in = [torch.from_numpy(x).pin_memory() for x in (c.pos, c.mass, c.soft, c.is_sink, act, ca, cp)]
@@ -295,35 +327,46 @@ def main():
         tree.close()
         if k >= args.warmup:
             e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.mean(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms, e2e_value = aggregate(statistics.mean(e2e_times), act.size, world, dist, dev)
 
     peaks, peak_src = load_peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
-    flops = p2p * FLOP_P2P + p2m * FLOP_P2M_QUAD
+    import hashlib
+    src = os.path.join(ROOT, "paper_2010_11254_gb300", "csrc", "walk.cu")
+    same_src = WALK_TRAFFIC["sha256"] == hashlib.sha256(open(src, "rb").read()).hexdigest()
+
+    def roof(kernel, flops, ms, traffic_key, model):
+        a = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": kernel, "achieved": round(a, 3), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(a / fp32_peak, 4),
+                "traffic": WALK_TRAFFIC[traffic_key] if (same_src and args.workload == "clumpy-2M") else None,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
+                "flops_per_launch": int(flops), "launch_ms": round(ms, 4), "flop_model": model}
+
     wk = statistics.mean(walk_ms)
-    achieved = flops / (wk * 1e-3) / 1e12
+    vk = statistics.mean(vjp_walk_ms)
+    r_fwd = roof("k_walk<QUAD, MODE_EVAL> (forward walk + FP32 evaluation)",
+                 p2p * FLOP_P2P + p2m * FLOP_P2M_QUAD, wk, "fwd",
+                 f"P2P {FLOP_P2P}, P2M quadrupole {FLOP_P2M_QUAD} FP32 flops per interaction")
+    r_vjp = roof("k_walk<QUAD, MODE_VJP> (adjoint walk + FP32 tidal-tensor products)",
+                 p2p * FLOP_VJP_P2P + p2m * FLOP_VJP_P2M_QUAD, vk, "vjp",
+                 f"P2P {FLOP_VJP_P2P}, P2M quadrupole {FLOP_VJP_P2M_QUAD} FP32 flops per interaction")
+    dominant, other = (r_vjp, r_fwd) if vk >= wk else (r_fwd, r_vjp)
     line = {
         "metric": "active-particle gravity evaluations per second (build + field + adjoint)",
         "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f32+f64" if args.precision == 0 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
                    "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"], "leaf_size": 16,
-                   "group_size": 32, "quadrupole": True, "l2": "flushed (512 MB write) before every timed step",
+                   "group_size": 32, "quadrupole": True, "precision": args.precision,
+                   "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"independent clouds x{world}"},
-        "roofline": {"bound": "alu", "kernel": "k_walk (forward walk + FP32 evaluation)",
-                     "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
-                     "flops_per_launch": flops, "launch_ms": round(wk, 4),
-                     "flop_model": f"P2P {FLOP_P2P}, P2M quadrupole {FLOP_P2M_QUAD} per interaction"},
+        "roofline": dominant,
+        "roofline_other_walk": other,
         "phases_ms": {"build": round(statistics.mean(build_ms), 4), "fwd": round(statistics.mean(fwd_ms), 4),
                       "fwd_walk": round(wk, 4), "vjp": round(statistics.mean(vjp_ms), 4),
                       "vjp_walk": round(statistics.mean(vjp_walk_ms), 4)},
@@ -334,11 +377,13 @@ def main():
         "build_hbm": {"algorithmic_GBps": round(BUILD_BYTES_PER_PARTICLE * c.n / (statistics.mean(build_ms) * 1e-3)
                                                 / 1e9, 1), "peak_GBps": peaks.get("hbm_gbs")},
         "particles_per_s": c.n * world / (ms_per_step * 1e-3),
-        "e2e": {"value": world * act.size / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": bi,
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if rank == 0:
+        line["force_error"] = force_error(c, act, acc_h, phi_h)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, c, act, ca, cp)
     if rank == 0:

@@ -86,9 +86,9 @@ typedef struct sfg_stats {
      * from CUDA events on the call's stream (0 when off) */
     float build_ms;       /* whole sfg_build */
     float fwd_ms;         /* whole sfg_accel */
-    float fwd_walk_ms;    /* its walk + evaluation kernels */
+    float fwd_walk_ms;    /* its walk + evaluation launches (after the list-counting pass) */
     float vjp_ms;         /* whole sfg_accel_vjp */
-    float vjp_walk_ms;    /* its walk + adjoint kernels */
+    float vjp_walk_ms;    /* its walk + adjoint launches (after the list-counting pass) */
 } sfg_stats;
 
 /* Fill *p with the defaults: G = 1, theta = 0.5, leaf_size = 16, group_size = 32,
@@ -131,6 +131,9 @@ int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, doubl
  *   d_pos[n][3] = dL/dpos  and  d_mass[n] = dL/dmass
  * (original particle order, overwritten), including the dependence of node
  * moments on member positions and masses.  The softening radii are constants.
+ * The adjoint always uses the FP32 pair/multipole arithmetic on node-centred
+ * offsets (with FP64 node-gradient and particle-gradient accumulation), under
+ * either precision setting of the tree.
  *   cot_a   [n_active][3] float64, device
  *   cot_phi [n_active]    float64, device, or NULL (zero)
  * Duplicate rows sum.  Errors as for sfg_accel. */

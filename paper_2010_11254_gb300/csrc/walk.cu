@@ -37,7 +37,7 @@ constexpr int WALK_WARPS = 4;  // warps per block
 constexpr int WALK_MINB = 6;   // resident blocks per SM the register budget must allow
 constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
 constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
-constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3;
+constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4;
 
 struct WarpSmem {
     int2 stack[STK];
@@ -47,6 +47,9 @@ struct WarpSmem {
     float4 tA[32]; // P2M: (Qxx, Qyy, Qxy, Qxz); P2P: (h, 1/h, j bits, sink flag)
     float tB[32];  // P2M: Qyz
     int tN[32];    // P2M: node id (adjoint)
+    // all-FP64 evaluation: source (x, y, z, m) and P2M Q[6] / P2P (h, 1/h, j, sink)
+    double dP[32][4];
+    double dA[32][6];
 };
 
 struct WalkParams {
@@ -57,8 +60,9 @@ struct WalkParams {
     const float4 *pw;
     const int4 *pc;
     const uint64_t *key;
-    const double *pos_s, *soft_s;
+    const double *pos_s, *soft_s, *mass_s;
     const uint8_t *sink_s;
+    const double *nM, *ncom, *nQ;
     Frame fr;
     float s22;
     unsigned long long T[SFG_LMAX + 1];
@@ -68,6 +72,7 @@ struct WalkParams {
     const int *tgt;
     float4 *res_a;
     double *res_phi;
+    double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     unsigned long long *counters; // [0] p2p [1] p2m [2] overflowed groups [3] work [4] retry work
     int *ovf_list;
     int *status;
@@ -103,6 +108,7 @@ struct Tgt {
     bool sink;
     int cg[3];
     int tp, R, tl, slice;
+    double x64[3], h64, hinv64; // all-FP64 evaluation only
 };
 
 // ------------------------------------------------------------ kernels ----
@@ -395,6 +401,133 @@ __device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, 
     }
 }
 
+// ------------------------------------------------- all-FP64 evaluation ----
+__device__ __forceinline__ void soft_KP64(double r, double rinv, double h, double hinv, double &K, double &P)
+{
+    double u = r * hinv;
+    if (u >= 1.0) {
+        K = rinv * rinv * rinv;
+        P = -rinv;
+        return;
+    }
+    double h3inv = hinv * hinv * hinv, u2 = u * u;
+    if (u < 0.5) {
+        K = h3inv * (32.0 / 3.0 + u2 * (-192.0 / 5.0 + 32.0 * u));
+        P = hinv * (-14.0 / 5.0 + u2 * (16.0 / 3.0 + u2 * (-48.0 / 5.0 + 32.0 / 5.0 * u)));
+    } else {
+        double uinv = h * rinv;
+        K = h3inv * (64.0 / 3.0 + u * (-48.0 + u * (192.0 / 5.0 - 32.0 / 3.0 * u)) - uinv * uinv * uinv / 15.0);
+        P = hinv * (uinv / 15.0 + u2 * (32.0 / 3.0 + u * (-16.0 + u * (48.0 / 5.0 - 32.0 / 15.0 * u))) - 16.0 / 5.0);
+    }
+}
+
+template <bool QUAD>
+__device__ __forceinline__ void stage_p2m64(const WalkParams &P, WarpSmem &S, const int *list, int cnt, int lane)
+{
+    if (lane < cnt) {
+        int id = list[lane];
+        for (int a = 0; a < 3; a++) S.dP[lane][a] = P.ncom[3 * (size_t)id + a];
+        S.dP[lane][3] = P.nM[id];
+        if (QUAD)
+            for (int q = 0; q < 6; q++) S.dA[lane][q] = P.nQ[6 * (size_t)id + q];
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void stage_p2p64(const WalkParams &P, WarpSmem &S, int cnt, int &qh, int &qoff, int lane)
+{
+    int j = -1, filled = 0;
+    for (int it = 0; filled < cnt && it < 66; it++) {
+        int2 hr = S.leafq[qh & 63];
+        int take = min(hr.y - qoff, cnt - filled);
+        if (take < 0) take = 0;
+        if (lane >= filled && lane < filled + take) j = hr.x + qoff + (lane - filled);
+        filled += take;
+        qoff += take;
+        if (qoff >= hr.y) {
+            qh++;
+            qoff = 0;
+        }
+    }
+    if (filled < cnt) {
+        if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
+        if (lane >= filled) j = -1;
+    }
+    if (lane < cnt && j >= 0) {
+        for (int a = 0; a < 3; a++) S.dP[lane][a] = P.pos_s[3 * (size_t)j + a];
+        S.dP[lane][3] = P.mass_s[j];
+        double h = P.soft_s[j];
+        S.dA[lane][0] = h;
+        S.dA[lane][1] = 1.0 / h;
+        S.dA[lane][2] = (double)j;
+        S.dA[lane][3] = P.sink_s[j] ? 1.0 : 0.0;
+    }
+    __syncwarp();
+}
+
+template <bool QUAD>
+__device__ __forceinline__ void fwd_p2m64(const WarpSmem &S, int cnt, const Tgt &T, double &ax, double &ay,
+                                          double &az, double &phi)
+{
+    for (int k = T.slice; k < cnt; k += T.R) {
+        double dx = S.dP[k][0] - T.x64[0], dy = S.dP[k][1] - T.x64[1], dz = S.dP[k][2] - T.x64[2];
+        double M = S.dP[k][3];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        double rinv = 1.0 / sqrt(r2);
+        double ri3 = rinv * rinv * rinv;
+        ax += M * dx * ri3;
+        ay += M * dy * ri3;
+        az += M * dz * ri3;
+        phi -= M * rinv;
+        if (QUAD) {
+            const double *Q = S.dA[k]; // xx yy zz xy xz yz
+            double Qd0 = Q[0] * dx + Q[3] * dy + Q[4] * dz;
+            double Qd1 = Q[3] * dx + Q[1] * dy + Q[5] * dz;
+            double Qd2 = Q[4] * dx + Q[5] * dy + Q[2] * dz;
+            double dQd = dx * Qd0 + dy * Qd1 + dz * Qd2;
+            double ri5 = ri3 * rinv * rinv, ri7 = ri5 * rinv * rinv;
+            ax += -Qd0 * ri5 + 2.5 * dQd * dx * ri7;
+            ay += -Qd1 * ri5 + 2.5 * dQd * dy * ri7;
+            az += -Qd2 * ri5 + 2.5 * dQd * dz * ri7;
+            phi += -0.5 * dQd * ri5;
+        }
+    }
+}
+
+__device__ __forceinline__ void fwd_p2p64(const WarpSmem &S, int cnt, const Tgt &T, double &ax, double &ay,
+                                          double &az, double &phi)
+{
+    for (int k = T.slice; k < cnt; k += T.R) {
+        int j = (int)S.dA[k][2];
+        if (j == T.r) continue;
+        double dx = S.dP[k][0] - T.x64[0], dy = S.dP[k][1] - T.x64[1], dz = S.dP[k][2] - T.x64[2];
+        double m = S.dP[k][3];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        double hj = S.dA[k][0], hjinv = S.dA[k][1];
+        bool sink = T.sink || S.dA[k][3] != 0.0;
+        bool tbig = T.h64 >= hj;
+        double ha = tbig ? T.h64 : hj, hainv = tbig ? T.hinv64 : hjinv;
+        double lo = tbig ? hj : T.h64, loinv = tbig ? hjinv : T.hinv64;
+        double hb = sink ? ha : lo, hbinv = sink ? hainv : loinv;
+        double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+        double K, Pk;
+        if (r2 < ha * ha) {
+            double r = r2 * rinv, K1, P1, K2, P2;
+            soft_KP64(r, rinv, ha, hainv, K1, P1);
+            soft_KP64(r, rinv, hb, hbinv, K2, P2);
+            K = 0.5 * (K1 + K2);
+            Pk = 0.5 * (P1 + P2);
+        } else {
+            K = rinv * rinv * rinv;
+            Pk = -rinv;
+        }
+        ax += m * K * dx;
+        ay += m * K * dy;
+        az += m * K * dz;
+        phi += m * Pk;
+    }
+}
+
 // --------------------------------------------------------- tile staging ----
 template <bool QUAD, bool NODEID>
 __device__ __forceinline__ void stage_p2m(const WalkParams &P, WarpSmem &S, const int *list, int cnt, const Tgt &T,
@@ -509,6 +642,7 @@ struct WalkState {
     int tot_m, tot_p, tot_leaf;
     float ax, ay, az;
     double phi;
+    double dax, day, daz;
     float c0, c1, c2, cf;
     long long off_m, off_p;
 };
@@ -566,6 +700,26 @@ __device__ __forceinline__ void flush_tiles(const WalkParams &P, WarpSmem &S, Wa
 {
     if (MODE == MODE_COUNT || MODE == MODE_DUMP) return;
     const int lim = final ? 1 : 32;
+    while (MODE == MODE_EVAL64 && W.nm >= lim) {
+        int c = min(W.nm, 32);
+        if (W.tile++ % K == kk) {
+            stage_p2m64<QUAD>(P, S, S.p2m + W.nm - c, c, lane);
+            if (T.has) fwd_p2m64<QUAD>(S, c, T, W.dax, W.day, W.daz, W.phi);
+            __syncwarp();
+        }
+        W.nm -= c;
+    }
+    while (MODE == MODE_EVAL64 && W.qn >= lim) {
+        int c = min(W.qn, 32);
+        if (W.tile++ % K == kk) {
+            stage_p2p64(P, S, c, W.qh, W.qoff, lane);
+            if (T.has) fwd_p2p64(S, c, T, W.dax, W.day, W.daz, W.phi);
+            __syncwarp();
+        } else {
+            skip_p2p(S, c, W.qh, W.qoff);
+        }
+        W.qn -= c;
+    }
     while (W.nm >= lim) {
         int c = min(W.nm, 32);
         if (W.tile++ % K == kk) {
@@ -625,6 +779,11 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         T.sink = P.sink_s[T.r] != 0;
     }
     T.hinv = 1.f / T.h;
+    if (MODE == MODE_EVAL64) {
+        for (int a = 0; a < 3; a++) T.x64[a] = xd[a];
+        T.h64 = T.has ? P.soft_s[T.r] : 1.0;
+        T.hinv64 = 1.0 / T.h64;
+    }
     int glo[3], ghi[3];
     for (int a = 0; a < 3; a++) {
         glo[a] = (int)__reduce_min_sync(FULL, lo[a]);
@@ -648,6 +807,7 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     W.tot_m = W.tot_p = W.tot_leaf = 0;
     W.ax = W.ay = W.az = 0.f;
     W.phi = 0.0;
+    W.dax = W.day = W.daz = 0.0;
     W.c0 = W.c1 = W.c2 = W.cf = 0.f;
     W.off_m = W.off_p = 0;
     if (MODE == MODE_VJP && T.has) {
@@ -721,6 +881,27 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     }
     if (MODE == MODE_DUMP) return;
     flush_tiles<QUAD, MODE>(P, S, W, T, lane, true, kk, K);
+    if (MODE == MODE_EVAL64) {
+        double dax = W.dax, day = W.day, daz = W.daz, dph = W.phi;
+        for (int o = T.tp; o < 32; o <<= 1) {
+            dax += __shfl_xor_sync(FULL, dax, o);
+            day += __shfl_xor_sync(FULL, day, o);
+            daz += __shfl_xor_sync(FULL, daz, o);
+            dph += __shfl_xor_sync(FULL, dph, o);
+        }
+        if (T.has && T.slice == 0) {
+            double *dst = P.res64 + 4 * (size_t)(tfirst + T.tl);
+            atomicAdd(dst, dax);
+            atomicAdd(dst + 1, day);
+            atomicAdd(dst + 2, daz);
+            atomicAdd(dst + 3, dph);
+        }
+        if (lane == 0 && kk == 0) {
+            atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(W.tot_p - 1));
+            atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)W.tot_m);
+        }
+        return;
+    }
     float ax = W.ax, ay = W.ay, az = W.az;
     double phi = W.phi;
     for (int o = T.tp; o < 32; o <<= 1) {
@@ -787,7 +968,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpSmem &S = sm[w];
     int2 *stack = GSTACK ? P.gstack + (size_t)(blockIdx.x * WALK_WARPS + w) * GSTK : S.stack;
-    constexpr bool ITEMS = MODE == MODE_EVAL || MODE == MODE_VJP;
+    constexpr bool ITEMS = MODE == MODE_EVAL || MODE == MODE_VJP || MODE == MODE_EVAL64;
     const int ngroups = *P.d_ngroups;
     const int nwork = GSTACK ? (int)P.counters[2] : (ITEMS ? P.ioff[ngroups] : ngroups);
     while (true) {
@@ -986,6 +1167,21 @@ __global__ void k_rows_out(const int64_t *idx, int64_t n_active, int n, const in
     }
 }
 
+__global__ void k_rows_out64(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
+                             const double *res64, double G, double *accel, double *phi)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) continue;
+        const double *r = res64 + 4 * (size_t)pre[rank[i]];
+        accel[3 * k] = G * r[0];
+        accel[3 * k + 1] = G * r[1];
+        accel[3 * k + 2] = G * r[2];
+        if (phi) phi[k] = G * r[3];
+    }
+}
+
 // --------------------------------------------------------- host side ----
 static int grid_for(int64_t n, int bt)
 {
@@ -1002,6 +1198,7 @@ struct Work {
     int2 *gtab, *gstack;
     float4 *res_a;
     double *res_phi;
+    double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     int *cnt3, *kcnt, *is_split, *soff, *ioff, *gdone, *hist;
     int2 *items;
     float4 *part_a;
@@ -1105,6 +1302,11 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.key = t->key;
     P.pos_s = t->pos_s;
     P.soft_s = t->soft_s;
+    P.mass_s = t->mass_s;
+    P.nM = t->nM;
+    P.ncom = t->ncom;
+    P.nQ = t->nQ;
+    P.res64 = nullptr;
     P.sink_s = t->sink_s;
     P.fr = t->frame_h;
     P.nn = t->nn;
@@ -1202,18 +1404,32 @@ static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
 int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double *phi, cudaStream_t s)
 {
     if (n_active == 0) return SFG_OK;
-    if (t->prm.precision != 0) return SFG_EINVAL; // all-FP64 evaluation is not built yet
     Work w;
     WalkParams P;
     ph_begin(t, PH_FWD, s);
     int rc = prepare(t, active, n_active, w, P, s);
     if (rc) return rc;
-    ph_begin(t, PH_FWD_WALK, s);
+    const bool f64 = t->prm.precision == 1;
+    double *res64 = nullptr;
+    if (f64) {
+        res64 = (double *)dev_alloc(t, 32 * (size_t)t->n, s);
+        if (!res64) return SFG_ENOMEM;
+        SFG_CUDA_OK(cudaMemsetAsync(res64, 0, 32 * (size_t)t->n, s));
+        P.res64 = res64;
+    }
     make_items(t, w, P, s);
-    launch_walk<MODE_EVAL>(t, P, s);
+    ph_begin(t, PH_FWD_WALK, s);
+    if (f64) launch_walk<MODE_EVAL64>(t, P, s);
+    else launch_walk<MODE_EVAL>(t, P, s);
     ph_end(t, PH_FWD_WALK, s);
-    k_rows_out<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, w.res_a,
-                                                       w.res_phi, t->prm.G, acc, phi);
+    if (f64) {
+        k_rows_out64<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, res64,
+                                                             t->prm.G, acc, phi);
+        dev_free(t, res64, s);
+    } else {
+        k_rows_out<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, w.res_a,
+                                                           w.res_phi, t->prm.G, acc, phi);
+    }
     t->n_launch += 1;
     ph_end(t, PH_FWD, s);
     SFG_CUDA_OK(cudaGetLastError());
@@ -1327,7 +1543,6 @@ __global__ void k_unpermute(const double *gpart, const int32_t *order, int n, do
 int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *cot_a, const double *cot_phi,
               double *d_pos, double *d_mass, cudaStream_t s)
 {
-    if (t->prm.precision != 0) return SFG_EINVAL;
     const int n = (int)t->n, nn = t->nn, BT = 256;
     Work w;
     WalkParams P;
@@ -1363,8 +1578,8 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         P.cot = cot;
         P.gpart = gpart;
         P.gnode = gnode;
-        ph_begin(t, PH_VJP_WALK, s);
         make_items(t, w, P, s);
+        ph_begin(t, PH_VJP_WALK, s);
         launch_walk<MODE_VJP>(t, P, s);
         ph_end(t, PH_VJP_WALK, s);
         k_gnode_unit<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nM, nn);

@@ -207,3 +207,34 @@ def test_clumpy_2e21_sampled_full_size():
     ao, po = o.accel_group(act[pick])
     _check_fields(acc.cpu().numpy()[pick], phi.cpu().numpy()[pick], ao, po)
     t.close()
+
+
+@pytest.mark.parametrize("quad", [True, False])
+def test_all_fp64_mode_matches_oracle_to_rounding(quad):
+    """precision = 1: the same lists evaluated in FP64 on the GPU agree with the
+    FP64 oracle to summation-order rounding."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.clumpy_cloud(1 << 15, n_clumps=64, n_sink=32, seed=15)
+    act = gen.active_subset(c.n, 0.3, seed=5)
+    pos, mass, soft, sink = to_dev(c, torch)
+    t = sfg.Tree(pos, mass, soft, sink, theta=0.5, quadrupole=quad, precision=1)
+    acc, phi = t.accel(torch.from_numpy(act).cuda())
+    assert t.status() == sfg.SFG_OK
+    t.close()
+    o = oracle_tree(c, 16)
+    o.walk(act, 32, 0.5)
+    ao, po = o.accel_group(act, quadrupole=quad)
+    e = rel_err(acc.cpu().numpy(), ao)
+    assert np.median(e) <= 1e-13 and e.max() <= 1e-10
+    assert rel_err(phi.cpu().numpy(), po).max() <= 1e-12
+    # the decades case: sub-cell structure is resolved in FP64
+    cd = edge_clouds()["decades"]
+    pos, mass, soft, sink = to_dev(cd, torch)
+    t = sfg.Tree(pos, mass, soft, sink, theta=0.5, leaf_size=8, precision=1)
+    acc, phi = t.accel(None)
+    t.close()
+    o = oracle_tree(cd, 8)
+    o.walk(np.arange(cd.n), 32, 0.5)
+    ao, po = o.accel_group(np.arange(cd.n))
+    assert np.median(rel_err(acc.cpu().numpy(), ao)) <= 1e-12
