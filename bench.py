@@ -221,6 +221,8 @@ def main():
     ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS))
     ap.add_argument("--active-frac", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf-size", type=int, default=16)
+    ap.add_argument("--group-size", type=int, default=32)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     args = ap.parse_args()
@@ -254,7 +256,8 @@ def main():
     d_cp = torch.from_numpy(cp).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    kw = dict(theta=wl["theta"], leaf_size=16, group_size=32, quadrupole=True, precision=args.precision)
+    kw = dict(theta=wl["theta"], leaf_size=args.leaf_size, group_size=args.group_size, quadrupole=True,
+              precision=args.precision)
 
     def one_step():
         tree = sfg.Tree(d_pos, d_mass, d_soft, d_sink, **kw)
@@ -361,8 +364,9 @@ def main():
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == 0 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
-                   "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"], "leaf_size": 16,
-                   "group_size": 32, "quadrupole": True, "precision": args.precision,
+                   "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"],
+                   "leaf_size": args.leaf_size, "group_size": args.group_size, "quadrupole": True,
+                   "precision": args.precision,
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"independent clouds x{world}"},
         "roofline": dominant,

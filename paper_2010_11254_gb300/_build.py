@@ -3,6 +3,10 @@
 build.cu (frame, keys, sort, octree, FP64 moments) is compiled without FMA
 contraction so that its FP64 results are reproducible operation by operation;
 the walk/eval file may contract FP32 multiply-adds.
+
+Environment: SFG_NVCC_EXTRA adds nvcc flags (e.g. -D defines) and
+SFG_LIB_NAME names the output library (default libsfg.so), so that builds
+with different flags can sit side by side in _lib/.
 """
 from __future__ import annotations
 
@@ -14,7 +18,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
-LIB = os.path.join(LIBDIR, "libsfg.so")
+LIB = os.path.join(LIBDIR, os.environ.get("SFG_LIB_NAME", "libsfg.so"))
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,11 +48,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     nvcc = _nvcc()
-    extra = list(extra_flags or [])
+    extra = list(extra_flags or []) + os.environ.get("SFG_NVCC_EXTRA", "").split()
 
     def compile_one(name: str) -> str:
         src = os.path.join(CSRC, name)
-        obj = os.path.join(LIBDIR, name.replace(".cu", ".o"))
+        stem = os.path.splitext(os.path.basename(LIB))[0]
+        obj = os.path.join(LIBDIR, f"{stem}.{name.replace('.cu', '.o')}")
         cmd = [nvcc, "-c", src, "-o", obj] + ARCH + COMMON + SOURCES[name] + extra
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
