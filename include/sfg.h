@@ -81,6 +81,7 @@ typedef struct sfg_stats {
     int64_t n_p2p;        /* particle-particle interactions of the last call (self excluded) */
     int64_t n_p2m;        /* particle-node interactions of the last call */
     int64_t n_overflow;   /* groups that needed the spill traversal buffer */
+    int32_t n_clouds;     /* independent clouds in the tree (sfg_build_batch), 1 otherwise */
     int64_t n_launches;   /* kernels this tree has launched since it was built (build included) */
     /* with timing on (sfg_set_timing), milliseconds of the last call of each kind,
      * from CUDA events on the call's stream (0 when off) */
@@ -111,6 +112,17 @@ void sfg_default_params(sfg_params *p);
  * out-of-domain inputs), SFG_ENOMEM, SFG_ECUDA. */
 int sfg_build(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink, int64_t n,
               const sfg_params *params, void *stream, sfg_tree **out);
+
+/* Build one forest over an ensemble of independent clouds (no gravity acts
+ * between clouds): cloud c is the particle range [offsets[c], offsets[c+1])
+ * of the concatenated arrays, with its own frame and root; every later call
+ * (sfg_accel, sfg_accel_vjp and the *_batch aliases below) solves all clouds
+ * together in one walk launch, with particle indices over the concatenation.
+ *   offsets [n_clouds + 1] int64, HOST: offsets[0] = 0, strictly increasing
+ *           (no empty cloud), offsets[n_clouds] = n < 2^31; 1 <= n_clouds <= 65535
+ * Other arguments and errors as sfg_build (which is the one-cloud case). */
+int sfg_build_batch(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink,
+                    const int64_t *offsets, int n_clouds, const sfg_params *params, void *stream, sfg_tree **out);
 
 /* Field at the active particles (Sec. 2.2, the active set of a timestep bin,
  * Sec. 2.3): for row k, the particle i = active_idx[k] gets
@@ -144,6 +156,13 @@ int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, c
  * records a few events per call on the call's stream; it does not synchronize. */
 int sfg_set_timing(sfg_tree *tree, int on);
 
+/* The same calls under the names of the ensemble interface (a batched tree
+ * is an ordinary tree; these forward to sfg_accel / sfg_accel_vjp). */
+int sfg_accel_batch(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
+                    void *stream);
+int sfg_accel_vjp_batch(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
+                        const double *cot_phi, double *d_pos, double *d_mass, void *stream);
+
 /* Statistics of the tree and of its last call (host pointer).  Synchronizes. */
 int sfg_get_stats(sfg_tree *tree, sfg_stats *out);
 
@@ -162,10 +181,13 @@ const char *sfg_status_string(int status);
  *   SFG_FIELD_KEYS      uint64 [n]        sorted Morton keys
  *   SFG_FIELD_ORDER     int32  [n]        sorted rank -> original index
  *   SFG_FIELD_NODE_INT  int32  [nn][16]   level, first, count, parent, child_first,
- *                                         nchild, lo[3], hi[3], cq[3], pad
+ *                                         nchild, lo[3], hi[3], cq[3], cloud
  *   SFG_FIELD_NODE_HQ   uint64 [nn]       ceil((h_max / cell)^2), capped at 2^62
  *   SFG_FIELD_NODE_F64  float64 [nn][11]  M, com[3], Q[6] (xx yy zz xy xz yz), h_max
- * `bytes` must equal the field's size. */
+ *   SFG_FIELD_FRAMES    float64 [n_clouds][4]  x0[3], L0 of every cloud
+ * `bytes` must equal the field's size.  With several clouds, node ids are
+ * breadth-first over the whole forest (the roots are nodes 0..n_clouds-1). */
+#define SFG_FIELD_FRAMES 6
 #define SFG_FIELD_KEYS 1
 #define SFG_FIELD_ORDER 2
 #define SFG_FIELD_NODE_INT 3

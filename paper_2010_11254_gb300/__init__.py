@@ -25,7 +25,7 @@ import torch
 from . import _build
 
 SFG_OK, SFG_EINVAL, SFG_ENOMEM, SFG_ECUDA, SFG_EOVERFLOW, SFG_ETIMEOUT = range(6)
-FIELD_KEYS, FIELD_ORDER, FIELD_NODE_INT, FIELD_NODE_HQ, FIELD_NODE_F64 = 1, 2, 3, 4, 5
+FIELD_KEYS, FIELD_ORDER, FIELD_NODE_INT, FIELD_NODE_HQ, FIELD_NODE_F64, FIELD_FRAMES = 1, 2, 3, 4, 5, 6
 
 _lock = threading.Lock()
 _lib = None
@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("depth", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("x0", ctypes.c_double * 3), ("L0", ctypes.c_double),
                 ("n_groups", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("n_p2p", ctypes.c_int64),
-                ("n_p2m", ctypes.c_int64), ("n_overflow", ctypes.c_int64), ("n_launches", ctypes.c_int64),
+                ("n_p2m", ctypes.c_int64), ("n_overflow", ctypes.c_int64), ("n_clouds", ctypes.c_int32),
+                ("n_launches", ctypes.c_int64),
                 ("build_ms", ctypes.c_float), ("fwd_ms", ctypes.c_float), ("fwd_walk_ms", ctypes.c_float),
                 ("vjp_ms", ctypes.c_float), ("vjp_walk_ms", ctypes.c_float)]
 
@@ -78,6 +79,9 @@ def _load():
         lib.sfg_status_string.restype = ctypes.c_char_p
         lib.sfg_build.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
         lib.sfg_build.restype = i32
+        lib.sfg_build_batch.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64), i32, ctypes.POINTER(Params), vp,
+                                        ctypes.POINTER(vp)]
+        lib.sfg_build_batch.restype = i32
         lib.sfg_accel.argtypes = [vp, vp, i64, vp, vp, vp]
         lib.sfg_accel.restype = i32
         lib.sfg_accel_vjp.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
@@ -132,7 +136,9 @@ class Tree:
     """A built tree over one cloud (``sfg_build``); owns its device memory."""
 
     def __init__(self, pos, mass, soft, is_sink=None, *, G: float = 1.0, theta: float = 0.5, leaf_size: int = 16,
-                 group_size: int = 32, quadrupole: bool = True, precision: int = 0):
+                 group_size: int = 32, quadrupole: bool = True, precision: int = 0, offsets=None):
+        """offsets (host sequence of n_clouds + 1 ints) builds one forest over an
+        ensemble of independent clouds (sfg_build_batch)."""
         lib = _load()
         pos = _dev(pos, torch.float64, "pos")
         mass = _dev(mass, torch.float64, "mass")
@@ -152,9 +158,18 @@ class Tree:
                                      quadrupole=quadrupole, precision=precision)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            rc = lib.sfg_build(pos.data_ptr(), mass.data_ptr(), soft.data_ptr(), sink_ptr, n,
-                               ctypes.byref(self.params), _stream(self.device), ctypes.byref(self._h))
-        _check(rc, "sfg_build")
+            if offsets is None:
+                rc = lib.sfg_build(pos.data_ptr(), mass.data_ptr(), soft.data_ptr(), sink_ptr, n,
+                                   ctypes.byref(self.params), _stream(self.device), ctypes.byref(self._h))
+            else:
+                if len(offsets) < 2 or int(offsets[-1]) != n:
+                    # the library only sees pointers: the total must match the arrays
+                    raise SfgError(SFG_EINVAL, "sfg_build_batch: offsets[-1] must equal the number of particles")
+                off = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+                rc = lib.sfg_build_batch(pos.data_ptr(), mass.data_ptr(), soft.data_ptr(), sink_ptr, off,
+                                         len(offsets) - 1, ctypes.byref(self.params), _stream(self.device),
+                                         ctypes.byref(self._h))
+        _check(rc, "sfg_build" if offsets is None else "sfg_build_batch")
 
     # -- calls ------------------------------------------------------------
     def _active(self, active):
@@ -205,7 +220,8 @@ class Tree:
         st = self.stats()
         n, nn = st["n"], st["n_nodes"]
         shapes = {FIELD_KEYS: ((n,), np.uint64), FIELD_ORDER: ((n,), np.int32), FIELD_NODE_INT: ((nn, 16), np.int32),
-                  FIELD_NODE_HQ: ((nn,), np.uint64), FIELD_NODE_F64: ((nn, 11), np.float64)}
+                  FIELD_NODE_HQ: ((nn,), np.uint64), FIELD_NODE_F64: ((nn, 11), np.float64),
+                  FIELD_FRAMES: ((st["n_clouds"], 4), np.float64)}
         shape, dt = shapes[field]
         out = np.zeros(shape, dt)
         _check(_load().sfg_export(self._h, field, out.ctypes.data, out.nbytes), "sfg_export")

@@ -100,12 +100,18 @@ const char *sfg_status_string(int st)
     }
 }
 
-int sfg_build(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink, int64_t n,
-              const sfg_params *params, void *stream, sfg_tree **out)
+static int build_forest(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink,
+                        const int64_t *offsets, int n_clouds, const sfg_params *params, void *stream,
+                        sfg_tree **out)
 {
     if (!out) return SFG_EINVAL;
     *out = nullptr;
-    if (!pos || !mass || !soft || n <= 0 || n >= 0x7fffffffLL) return SFG_EINVAL;
+    if (!pos || !mass || !soft || !offsets || n_clouds < 1 || n_clouds > 65535) return SFG_EINVAL;
+    if (offsets[0] != 0) return SFG_EINVAL;
+    for (int c = 0; c < n_clouds; c++)
+        if (offsets[c + 1] <= offsets[c]) return SFG_EINVAL; // every cloud holds at least one particle
+    const int64_t n = offsets[n_clouds];
+    if (n <= 0 || n >= 0x7fffffffLL) return SFG_EINVAL;
     sfg_params p;
     if (params) p = *params;
     else sfg_default_params(&p);
@@ -117,6 +123,8 @@ int sfg_build(const double *pos, const double *mass, const double *soft, const u
     sfg_tree *T = new sfg_tree;
     T->t.prm = p;
     T->t.n = n;
+    T->t.nclouds = n_clouds;
+    T->t.off_h.assign(offsets, offsets + n_clouds + 1);
     T->t.stream = (cudaStream_t)stream;
     const char *env = getenv("SFG_TIMING");
     T->t.timing = env && env[0] == '1';
@@ -131,6 +139,33 @@ int sfg_build(const double *pos, const double *mass, const double *soft, const u
     T->t.last.n = n;
     *out = T;
     return SFG_OK;
+}
+
+int sfg_build(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink, int64_t n,
+              const sfg_params *params, void *stream, sfg_tree **out)
+{
+    if (out) *out = nullptr;
+    if (n <= 0 || n >= 0x7fffffffLL) return SFG_EINVAL;
+    const int64_t off[2] = {0, n};
+    return build_forest(pos, mass, soft, is_sink, off, 1, params, stream, out);
+}
+
+int sfg_build_batch(const double *pos, const double *mass, const double *soft, const uint8_t *is_sink,
+                    const int64_t *offsets, int n_clouds, const sfg_params *params, void *stream, sfg_tree **out)
+{
+    return build_forest(pos, mass, soft, is_sink, offsets, n_clouds, params, stream, out);
+}
+
+int sfg_accel_batch(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
+                    void *stream)
+{
+    return sfg_accel(tree, active_idx, n_active, accel, phi, stream);
+}
+
+int sfg_accel_vjp_batch(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
+                        const double *cot_phi, double *d_pos, double *d_mass, void *stream)
+{
+    return sfg_accel_vjp(tree, active_idx, n_active, cot_a, cot_phi, d_pos, d_mass, stream);
 }
 
 int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi, void *stream)
@@ -167,6 +202,7 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
     s.n_p2p = (int64_t)c[0];
     s.n_p2m = (int64_t)c[1];
     s.n_overflow = (int64_t)c[2];
+    s.n_clouds = t->nclouds;
     s.n_groups = (int64_t)(*(int *)&c[5]);
     s.n_targets = (int64_t)c[6];
     s.n_launches = t->n_launch;
@@ -228,7 +264,7 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
         return SFG_OK;
     case SFG_FIELD_NODE_INT: {
         if (bytes != 64 * nn) return SFG_EINVAL;
-        std::vector<int32_t> a(6 * nn);
+        std::vector<int32_t> a(7 * nn);
         std::vector<int4> w(3 * nn);
         SFG_CUDA_OK(cudaMemcpy(&a[0], t->nlevel, 4 * nn, cudaMemcpyDeviceToHost));
         SFG_CUDA_OK(cudaMemcpy(&a[nn], t->nfirst, 4 * nn, cudaMemcpyDeviceToHost));
@@ -236,6 +272,7 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
         SFG_CUDA_OK(cudaMemcpy(&a[3 * nn], t->nparent, 4 * nn, cudaMemcpyDeviceToHost));
         SFG_CUDA_OK(cudaMemcpy(&a[4 * nn], t->nchild_first, 4 * nn, cudaMemcpyDeviceToHost));
         SFG_CUDA_OK(cudaMemcpy(&a[5 * nn], t->nnchild, 4 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&a[6 * nn], t->ncloud, 4 * nn, cudaMemcpyDeviceToHost));
         SFG_CUDA_OK(cudaMemcpy(&w[0], t->W0, 16 * nn, cudaMemcpyDeviceToHost));
         SFG_CUDA_OK(cudaMemcpy(&w[nn], t->W1, 16 * nn, cudaMemcpyDeviceToHost));
         SFG_CUDA_OK(cudaMemcpy(&w[2 * nn], t->W2, 16 * nn, cudaMemcpyDeviceToHost));
@@ -247,7 +284,7 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
             r[6] = w0.x; r[7] = w0.y; r[8] = w0.z;
             r[9] = w1.x; r[10] = w1.y; r[11] = w1.z;
             r[12] = w2.x; r[13] = w2.y; r[14] = w2.z;
-            r[15] = 0;
+            r[15] = a[6 * nn + i];
         }
         return SFG_OK;
     }
@@ -265,6 +302,16 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
             for (int a = 0; a < 3; a++) r[1 + a] = com[3 * i + a];
             for (int k = 0; k < 6; k++) r[4 + k] = Q[6 * i + k];
             r[10] = h[i];
+        }
+        return SFG_OK;
+    }
+    case SFG_FIELD_FRAMES: {
+        const size_t C = (size_t)t->nclouds;
+        if (bytes != 32 * C) return SFG_EINVAL;
+        double *o = (double *)host_dst;
+        for (size_t c = 0; c < C; c++) {
+            for (int a = 0; a < 3; a++) o[4 * c + a] = t->frames_h[c].x0[a];
+            o[4 * c + 3] = t->frames_h[c].L0;
         }
         return SFG_OK;
     }

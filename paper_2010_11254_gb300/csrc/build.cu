@@ -22,6 +22,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "sfg_internal.cuh"
@@ -154,18 +155,22 @@ __device__ inline double from_ord(unsigned long long u)
     return __longlong_as_double(b);
 }
 
-__global__ void k_minmax_init(unsigned long long *mm)
+__global__ void k_minmax_init(unsigned long long *mm, int C)
 {
-    if (threadIdx.x < 3) mm[threadIdx.x] = ~0ull;
-    else if (threadIdx.x < 6) mm[threadIdx.x] = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 * C; i += gridDim.x * blockDim.x)
+        mm[i] = (i % 6) < 3 ? ~0ull : 0ull;
 }
 
-__global__ void k_validate_minmax(const double *pos, const double *mass, const double *soft, int n,
-                                  unsigned long long *mm, int *status)
+// Grid (chunks, C): block (x, c) strides over cloud c's range only.
+__global__ void k_validate_minmax(const double *pos, const double *mass, const double *soft, const int64_t *off,
+                                  unsigned long long *mm_all, int *status)
 {
+    const int c = blockIdx.y;
+    const int b = (int)off[c], e = (int)off[c + 1];
+    unsigned long long *mm = mm_all + 6 * (size_t)c;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
     bool bad = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
         for (int a = 0; a < 3; a++) {
             double x = pos[3 * (size_t)i + a];
             if (!isfinite(x)) bad = true;
@@ -191,8 +196,12 @@ __global__ void k_validate_minmax(const double *pos, const double *mass, const d
     if (bad) atomicOr(status, ST_EINVAL);
 }
 
-__global__ void k_frame(const unsigned long long *mm, Frame *fr, int *status)
+__global__ void k_frame(const unsigned long long *mm_all, Frame *fr_all, int C, int *status)
 {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const unsigned long long *mm = mm_all + 6 * (size_t)c;
+    Frame *fr = fr_all + c;
     double E = 0.0;
     for (int a = 0; a < 3; a++) {
         double lo = from_ord(mm[a]), hi = from_ord(mm[3 + a]);
@@ -220,10 +229,16 @@ __global__ void k_frame(const unsigned long long *mm, Frame *fr, int *status)
 }
 
 // ------------------------------------------------------------------ keys ----
-__global__ void k_keys(const double *pos, int n, const Frame *fr, uint64_t *key, uint32_t *val)
+// Grid (chunks, C); also records the cloud of every input particle.
+__global__ void k_keys(const double *pos, const int64_t *off, const Frame *frames, uint64_t *key, uint32_t *val,
+                       uint16_t *cloud_of)
 {
+    const int c = blockIdx.y;
+    const int b = (int)off[c], e = (int)off[c + 1];
+    const Frame *fr = frames + c;
     const double x0 = fr->x0[0], y0 = fr->x0[1], z0 = fr->x0[2], sc = fr->scale;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+        if (cloud_of) cloud_of[i] = (uint16_t)c;
         uint32_t qx = cell_of(pos[3 * (size_t)i], x0, sc);
         uint32_t qy = cell_of(pos[3 * (size_t)i + 1], y0, sc);
         uint32_t qz = cell_of(pos[3 * (size_t)i + 2], z0, sc);
@@ -237,20 +252,28 @@ constexpr int RS_WARPS = 8;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_WARPS * 32 * RS_ITEMS; // 4096
 
-__global__ void __launch_bounds__(RS_WARPS * 32) k_rs_hist(const uint64_t *key, int n, int shift, int *hist, int nb)
+// Digit of element (k, v): 8 key bits at `shift`, or, with a cloud table,
+// 8 bits of the cloud id of value v.
+__device__ __forceinline__ int rs_digit(uint64_t k, uint32_t v, int shift, const uint16_t *cl)
+{
+    return cl ? (int)((cl[v] >> shift) & 255) : (int)((k >> shift) & 255);
+}
+
+__global__ void __launch_bounds__(RS_WARPS * 32)
+    k_rs_hist(const uint64_t *key, const uint32_t *val, int n, int shift, int *hist, int nb, const uint16_t *cl)
 {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     int base = blockIdx.x * RS_TILE, end = min(n, base + RS_TILE);
-    for (int i = base + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&h[(key[i] >> shift) & 255], 1);
+    for (int i = base + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&h[rs_digit(key[i], val[i], shift, cl)], 1);
     __syncthreads();
     hist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(RS_WARPS * 32)
     k_rs_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n, int shift,
-                 const int *off, int nb)
+                 const int *off, int nb, const uint16_t *cl)
 {
     __shared__ int wcnt[RS_WARPS][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -267,7 +290,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32)
         bool valid = i < n;
         k[r] = valid ? kin[i] : 0;
         v[r] = valid ? vin[i] : 0;
-        int d = valid ? (int)((k[r] >> shift) & 255) : 256;
+        int d = valid ? rs_digit(k[r], v[r], shift, cl) : 256;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int before = __popc(peers & lt);
         int c0 = valid ? wcnt[w][d] : 0;
@@ -303,10 +326,11 @@ __global__ void __launch_bounds__(RS_WARPS * 32)
 // --------------------------------------------------------------- gather ----
 __global__ void k_pack(const double *pos, const double *mass, const double *soft, const uint8_t *sink, int n,
                        const uint32_t *val, int32_t *order, int32_t *rank, double *pos_s, double *mass_s,
-                       double *soft_s, uint8_t *sink_s)
+                       double *soft_s, uint8_t *sink_s, const uint16_t *cloud_of, int32_t *pcloud)
 {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         int i = (int)val[r];
+        if (pcloud) pcloud[r] = cloud_of[i];
         order[r] = i;
         rank[i] = r;
         pos_s[3 * (size_t)r] = pos[3 * (size_t)i];
@@ -331,14 +355,21 @@ __device__ inline int lower_digit(const uint64_t *key, int lo, int hi, int cshif
     return lo;
 }
 
-__global__ void k_oct_root(int n, int32_t *nfirst, int32_t *ncount, int32_t *nparent, int32_t *nlevel, int *lvl)
+// One root per cloud: node c covers cloud c's sorted range.
+__global__ void k_oct_root(const int64_t *off, int C, int32_t *nfirst, int32_t *ncount, int32_t *nparent,
+                           int32_t *nlevel, int32_t *ncloud, int *lvl)
 {
-    nfirst[0] = 0;
-    ncount[0] = n;
-    nparent[0] = -1;
-    nlevel[0] = 0;
-    lvl[0] = 0;
-    lvl[1] = 1;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        nfirst[c] = (int)off[c];
+        ncount[c] = (int)(off[c + 1] - off[c]);
+        nparent[c] = -1;
+        nlevel[c] = 0;
+        ncloud[c] = c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        lvl[0] = 0;
+        lvl[1] = C;
+    }
 }
 
 __global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int leaf_size, int cap,
@@ -367,7 +398,7 @@ __global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int 
 
 __global__ void k_oct_write(const uint64_t *key, const int *lvl, int level, int leaf_size, int cap, int32_t *nfirst,
                             int32_t *ncount, int32_t *nparent, int32_t *nchild_first, int32_t *nnchild,
-                            int32_t *nlevel, const int *tmp_off, int *status)
+                            int32_t *nlevel, int32_t *ncloud, const int *tmp_off, int *status)
 {
     int b = lvl[level], e = min(lvl[level + 1], cap);
     int next = lvl[level + 1];
@@ -390,6 +421,7 @@ __global__ void k_oct_write(const uint64_t *key, const int *lvl, int level, int 
                     ncount[id] = s - prev;
                     nparent[id] = node;
                     nlevel[id] = level + 1;
+                    ncloud[id] = ncloud[node];
                 } else {
                     atomicOr(status, ST_NODECAP);
                 }
@@ -407,8 +439,8 @@ struct MomArgs {
     const uint64_t *key;
     const double *pos, *mass, *soft;
     const uint8_t *sink;
-    const int32_t *nfirst, *ncount, *nparent, *nchild_first, *nnchild, *nlevel;
-    const Frame *fr;
+    const int32_t *nfirst, *ncount, *nparent, *nchild_first, *nnchild, *nlevel, *ncloud;
+    const Frame *fr; // [C]
     int4 *W0, *W1, *W2;
     unsigned long long *Whq;
     float4 *E0, *E1, *E2;
@@ -547,18 +579,16 @@ __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
 // at a time from the deepest (one thread per node; its children are final).
 __global__ void k_leaf_moments(MomArgs A)
 {
-    const Frame fr = *A.fr;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nn; i += gridDim.x * blockDim.x) {
         int node = A.leaves[i];
-        if (node >= 0) leaf_moments(A, fr, node);
+        if (node >= 0) leaf_moments(A, A.fr[A.ncloud[node]], node);
     }
 }
 
 __global__ void k_internal_moments(MomArgs A, int b, int e)
 {
-    const Frame fr = *A.fr;
     for (int node = b + blockIdx.x * blockDim.x + threadIdx.x; node < e; node += gridDim.x * blockDim.x)
-        if (A.nnchild[node] != 0) internal_moments(A, fr, node);
+        if (A.nnchild[node] != 0) internal_moments(A, A.fr[A.ncloud[node]], node);
 }
 
 // Leaf ids in node order (the slots past the leaf count hold -1).
@@ -601,6 +631,7 @@ static int alloc_nodes(Tree *t, int cap, cudaStream_t s)
     ALLOC(t->nchild_first, int32_t, cap);
     ALLOC(t->nnchild, int32_t, cap);
     ALLOC(t->nlevel, int32_t, cap);
+    ALLOC(t->ncloud, int32_t, cap);
     return SFG_OK;
 }
 
@@ -612,37 +643,55 @@ static void free_nodes(Tree *t, cudaStream_t s)
     dev_free(t, t->nchild_first, s);
     dev_free(t, t->nnchild, s);
     dev_free(t, t->nlevel, s);
-    t->nfirst = t->ncount = t->nparent = t->nchild_first = t->nnchild = t->nlevel = nullptr;
+    dev_free(t, t->ncloud, s);
+    t->nfirst = t->ncount = t->nparent = t->nchild_first = t->nnchild = t->nlevel = t->ncloud = nullptr;
+}
+
+// Launch grid (chunks, C) whose blocks each stride over one cloud's range.
+static dim3 cloud_grid(const Tree *t, int bt)
+{
+    int64_t big = 1;
+    for (int c = 0; c < t->nclouds; c++) big = std::max(big, t->off_h[c + 1] - t->off_h[c]);
+    int64_t chunks = (big + bt - 1) / bt;
+    int64_t cap = std::max<int64_t>(1, (int64_t)num_sms() * 8 / t->nclouds);
+    return dim3((unsigned)std::max<int64_t>(1, std::min(chunks, cap)), (unsigned)t->nclouds);
 }
 
 int build_tree(Tree *t, const double *pos, const double *mass, const double *soft, const uint8_t *is_sink,
                cudaStream_t s)
 {
     const int n = (int)t->n;
+    const int C = t->nclouds;
     const int BT = 256;
     ALLOC(t->d_status, int, 1);
-    ALLOC(t->d_frame, Frame, 1);
-    ALLOC(t->d_minmax, unsigned long long, 6);
+    ALLOC(t->d_frame, Frame, C);
+    ALLOC(t->d_off, int64_t, C + 1);
+    ALLOC(t->d_minmax, unsigned long long, 6 * (size_t)C);
     ALLOC(t->d_lvl, int, SFG_LMAX + 3);
     ALLOC(t->d_counters, unsigned long long, 8);
     ALLOC(t->d_n, int, 1);
+    SFG_CUDA_OK(cudaMemcpyAsync(t->d_off, t->off_h.data(), sizeof(int64_t) * (C + 1), cudaMemcpyHostToDevice, s));
     k_set_int<<<1, 1, 0, s>>>(t->d_n, n);
     SFG_CUDA_OK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
     SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, 8 * sizeof(unsigned long long), s));
 
+    const dim3 cg = cloud_grid(t, BT);
     t->n_launch += 2 + 3; // k_set_int, k_minmax_init, k_validate_minmax, k_frame, k_keys
-    k_minmax_init<<<1, 32, 0, s>>>(t->d_minmax);
-    k_validate_minmax<<<grid_for(n, BT), BT, 0, s>>>(pos, mass, soft, n, t->d_minmax, t->d_status);
-    k_frame<<<1, 1, 0, s>>>(t->d_minmax, t->d_frame, t->d_status);
+    k_minmax_init<<<grid_for(6 * C, BT), BT, 0, s>>>(t->d_minmax, C);
+    k_validate_minmax<<<cg, BT, 0, s>>>(pos, mass, soft, t->d_off, t->d_minmax, t->d_status);
+    k_frame<<<(C + 127) / 128, 128, 0, s>>>(t->d_minmax, t->d_frame, C, t->d_status);
 
-    // keys + sort
+    // keys + sort: 8 passes on the Morton key, then (several clouds) stable
+    // passes on the cloud id, so each cloud is contiguous and key-sorted
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
+    uint16_t *cloud_of = nullptr;
     ALLOC(k0, uint64_t, n);
     ALLOC(k1, uint64_t, n);
     ALLOC(v0, uint32_t, n);
     ALLOC(v1, uint32_t, n);
-    k_keys<<<grid_for(n, BT), BT, 0, s>>>(pos, n, t->d_frame, k0, v0);
+    if (C > 1) ALLOC(cloud_of, uint16_t, n);
+    k_keys<<<cg, BT, 0, s>>>(pos, t->d_off, t->d_frame, k0, v0, cloud_of);
     const int nb = (n + RS_TILE - 1) / RS_TILE;
     int *hist, *hoff, *d_hn, *scr;
     ALLOC(hist, int, 256 * (size_t)nb);
@@ -650,12 +699,15 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(d_hn, int, 1);
     ALLOC(scr, int, scan_scratch_bytes() / sizeof(int));
     k_set_int<<<1, 1, 0, s>>>(d_hn, 256 * nb);
-    t->n_launch += 1 + 8 * 5 + 1; // set, 8 x (hist, 3 scan, scatter), pack
-    for (int pass = 0; pass < 8; pass++) {
-        int shift = 8 * pass;
-        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(k0, n, shift, hist, nb);
+    const int cloud_passes = C <= 1 ? 0 : (C <= 256 ? 1 : 2);
+    t->n_launch += 1 + (8 + cloud_passes) * 5 + 1; // set, passes x (hist, 3 scan, scatter), pack
+    for (int pass = 0; pass < 8 + cloud_passes; pass++) {
+        const bool by_cloud = pass >= 8;
+        int shift = by_cloud ? 8 * (pass - 8) : 8 * pass;
+        const uint16_t *cl = by_cloud ? cloud_of : nullptr;
+        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, n, shift, hist, nb, cl);
         scan_exclusive(hist, hoff, d_hn, 256 * nb, nullptr, nullptr, scr, s);
-        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, k1, v1, n, shift, hoff, nb);
+        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, k1, v1, n, shift, hoff, nb, cl);
         uint64_t *tk = k0;
         k0 = k1;
         k1 = tk;
@@ -677,13 +729,15 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->sink_s, uint8_t, n);
     ALLOC(t->pw, float4, n);
     ALLOC(t->pc, int4, n);
+    if (C > 1) ALLOC(t->pcloud, int32_t, n);
     k_pack<<<grid_for(n, BT), BT, 0, s>>>(pos, mass, soft, is_sink, n, v0, t->order, t->rank, t->pos_s, t->mass_s,
-                                          t->soft_s, t->sink_s);
+                                          t->soft_s, t->sink_s, cloud_of, t->pcloud);
     dev_free(t, v0, s);
     dev_free(t, v1, s);
+    dev_free(t, cloud_of, s);
 
     // octree, retried with a larger node capacity if the estimate was short
-    int64_t cap64 = 4 * ((int64_t)n / (t->prm.leaf_size + 1)) + 4096;
+    int64_t cap64 = 4 * ((int64_t)n / (t->prm.leaf_size + 1)) + 4096 + 64 * (int64_t)C;
     int *tmp = nullptr, *tmpo = nullptr;
     for (int attempt = 0;; attempt++) {
         if (cap64 > 0x7fffffff) cap64 = 0x7fffffff;
@@ -692,7 +746,8 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         if (rc) return rc;
         ALLOC(tmp, int, cap + 1);
         ALLOC(tmpo, int, cap + 1);
-        k_oct_root<<<1, 1, 0, s>>>(n, t->nfirst, t->ncount, t->nparent, t->nlevel, t->d_lvl);
+        k_oct_root<<<(C + 127) / 128, 128, 0, s>>>(t->d_off, C, t->nfirst, t->ncount, t->nparent, t->nlevel,
+                                                   t->ncloud, t->d_lvl);
         t->n_launch += 1 + (SFG_LMAX + 1) * 5;
         for (int level = 0; level <= SFG_LMAX; level++) {
             k_oct_count<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
@@ -701,7 +756,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
                        t->d_lvl + level + 1, scr, s);
             k_oct_write<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, t->nparent, t->nchild_first, t->nnchild,
-                                                         t->nlevel, tmpo, t->d_status);
+                                                         t->nlevel, t->ncloud, tmpo, t->d_status);
         }
         int st = 0;
         SFG_CUDA_OK(cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -757,6 +812,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.nchild_first = t->nchild_first;
     A.nnchild = t->nnchild;
     A.nlevel = t->nlevel;
+    A.ncloud = t->ncloud;
     A.fr = t->d_frame;
     A.W0 = t->W0;
     A.W1 = t->W1;
@@ -785,8 +841,10 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     dev_free(t, leaves, s);
     dev_free(t, d_nn, s);
     dev_free(t, scr, s);
-    SFG_CUDA_OK(cudaMemcpyAsync(&t->frame_h, t->d_frame, sizeof(Frame), cudaMemcpyDeviceToHost, s));
+    t->frames_h.resize(C);
+    SFG_CUDA_OK(cudaMemcpyAsync(t->frames_h.data(), t->d_frame, sizeof(Frame) * C, cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
+    t->frame_h = t->frames_h[0];
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
 }
@@ -805,6 +863,7 @@ constexpr size_t st_al(size_t x) { return (x + 255) & ~(size_t)255; } // every r
 constexpr size_t ST_OFF_MINMAX = 0;                                             // 6 x u64
 constexpr size_t ST_OFF_FRAME = 256;                                            // Frame
 constexpr size_t ST_OFF_HN = 512;                                               // 2 ints
+constexpr size_t ST_OFF_RANGE = 768;                                            // 2 x int64: {0, n}
 constexpr size_t ST_OFF_SCAN = 1024;                                            // SCAN_NB ints
 constexpr size_t ST_OFF_HIST = st_al(ST_OFF_SCAN + SCAN_NB * 4);                // 256 * ST_NB ints
 constexpr size_t ST_OFF_HOFF = st_al(ST_OFF_HIST + 256 * (size_t)ST_NB * 4);    // 256 * ST_NB + 1 ints
@@ -837,6 +896,12 @@ __global__ void k_minmax_pos(const double *pos, int n, unsigned long long *mm)
             atomicMax(&mm[3 + a], hi[a]);
         }
     }
+}
+
+__global__ void k_set_range(int64_t *range, int64_t n)
+{
+    range[0] = 0;
+    range[1] = n;
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -883,18 +948,20 @@ extern "C" int sfg_sort_keys_static(const double *pos, int64_t n, uint64_t *key_
     uint32_t *vb = (uint32_t *)(base + ST_OFF_VALS);
     const int nb = (nn + RS_TILE - 1) / RS_TILE;
     int *scratch_status = hn + 1; // k_frame reports an unsupported extent here; positions must be finite
-    k_minmax_init<<<1, 32, 0, s>>>(mm);
+    int64_t *range = (int64_t *)(base + ST_OFF_RANGE);
+    k_set_range<<<1, 1, 0, s>>>(range, n);
+    k_minmax_init<<<1, 32, 0, s>>>(mm, 1);
     k_minmax_pos<<<grid_for(nn, BT), BT, 0, s>>>(pos, nn, mm);
-    k_frame<<<1, 1, 0, s>>>(mm, fr, scratch_status);
+    k_frame<<<1, 1, 0, s>>>(mm, fr, 1, scratch_status);
     uint64_t *ka = key_out, *kx = kb;
     uint32_t *va = (uint32_t *)order_out, *vx = vb;
-    k_keys<<<grid_for(nn, BT), BT, 0, s>>>(pos, nn, fr, ka, va);
+    k_keys<<<dim3(grid_for(nn, BT), 1), BT, 0, s>>>(pos, range, fr, ka, va, nullptr);
     k_set_int<<<1, 1, 0, s>>>(hn, 256 * nb);
     for (int pass = 0; pass < 8; pass++) {
         int shift = 8 * pass;
-        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(ka, nn, shift, hist, nb);
+        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(ka, va, nn, shift, hist, nb, nullptr);
         scan_exclusive(hist, hoff, hn, 256 * nb, nullptr, nullptr, scr, s);
-        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(ka, va, kx, vx, nn, shift, hoff, nb);
+        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(ka, va, kx, vx, nn, shift, hoff, nb, nullptr);
         uint64_t *tk = ka;
         ka = kx;
         kx = tk;

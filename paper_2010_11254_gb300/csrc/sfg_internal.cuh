@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include <unordered_set>
+#include <vector>
 
 #include "../../include/sfg.h"
 
@@ -50,11 +51,20 @@ struct Tree {
     int64_t n = 0;
     int nn = 0, cap = 0, depth = 0, n_levels = 0;
     int lvl_off[SFG_LMAX + 3] = {0};
-    Frame frame_h{};
+    // a tree holds C >= 1 independent clouds (a forest): cloud c is the
+    // particle range [off[c], off[c+1]) of the input and of the sorted order,
+    // with its own frame and root (node c)
+    int nclouds = 1;
+    std::vector<int64_t> off_h;
+    std::vector<Frame> frames_h;
+    Frame frame_h{}; // frames_h[0]
     cudaStream_t stream = nullptr;
     int *d_status = nullptr;
-    Frame *d_frame = nullptr;
-    unsigned long long *d_minmax = nullptr;
+    Frame *d_frame = nullptr; // [C]
+    int64_t *d_off = nullptr; // [C + 1]
+    unsigned long long *d_minmax = nullptr; // [C][6]
+    int32_t *pcloud = nullptr;              // sorted rank -> cloud (C > 1)
+    int32_t *ncloud = nullptr;              // node -> cloud
     int *d_lvl = nullptr; // device level offsets [SFG_LMAX + 3]
     // particles
     uint64_t *key = nullptr;

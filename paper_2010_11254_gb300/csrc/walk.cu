@@ -63,8 +63,9 @@ struct WalkParams {
     const double *pos_s, *soft_s, *mass_s;
     const uint8_t *sink_s;
     const double *nM, *ncom, *nQ;
-    Frame fr;
-    float s22;
+    const Frame *frames;   // [C] per-cloud frames
+    const int32_t *pcloud; // sorted rank -> cloud (NULL: one cloud)
+    int nclouds;
     unsigned long long T[SFG_LMAX + 1];
     int nn;
     const int2 *gtab;
@@ -108,6 +109,7 @@ struct Tgt {
     bool sink;
     int cg[3];
     int tp, R, tl, slice;
+    float s22;                  // half-cell size of the group's cloud (FP32)
     double x64[3], h64, hinv64; // all-FP64 evaluation only
 };
 
@@ -537,9 +539,9 @@ __device__ __forceinline__ void stage_p2m(const WalkParams &P, WarpSmem &S, cons
         int id = list[lane];
         float4 e0 = P.E0[id];
         float4 e2 = P.E2[id];
-        float px = fmaf((float)(__float_as_int(e2.y) - T.cg[0]), P.s22, e0.x);
-        float py = fmaf((float)(__float_as_int(e2.z) - T.cg[1]), P.s22, e0.y);
-        float pz = fmaf((float)(__float_as_int(e2.w) - T.cg[2]), P.s22, e0.z);
+        float px = fmaf((float)(__float_as_int(e2.y) - T.cg[0]), T.s22, e0.x);
+        float py = fmaf((float)(__float_as_int(e2.z) - T.cg[1]), T.s22, e0.y);
+        float pz = fmaf((float)(__float_as_int(e2.w) - T.cg[2]), T.s22, e0.z);
         S.tP[lane] = make_float4(px, py, pz, e0.w);
         if (QUAD) {
             S.tA[lane] = P.E1[id];
@@ -575,9 +577,9 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int 
     if (lane < cnt && j >= 0) {
         float4 a = P.pw[j];
         int4 b = P.pc[j];
-        float px = fmaf((float)(b.x - T.cg[0]), P.s22, a.x);
-        float py = fmaf((float)(b.y - T.cg[1]), P.s22, a.y);
-        float pz = fmaf((float)(b.z - T.cg[2]), P.s22, a.z);
+        float px = fmaf((float)(b.x - T.cg[0]), T.s22, a.x);
+        float py = fmaf((float)(b.y - T.cg[1]), T.s22, a.y);
+        float pz = fmaf((float)(b.z - T.cg[2]), T.s22, a.z);
         S.tP[lane] = make_float4(px, py, pz, a.w);
         float h = __int_as_float(b.w); // negative for a sink
         float ha = fabsf(h);
@@ -762,6 +764,10 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     T.slice = lane / T.tp;
     T.has = T.tl < tcount;
     T.r = T.has ? P.tgt[tfirst + T.tl] : -1;
+    // the group's cloud: its frame, and its root (node id = cloud id)
+    const int cloud = P.pcloud ? P.pcloud[P.tgt[tfirst]] : 0;
+    const Frame fr = P.frames[cloud];
+    T.s22 = (float)fr.half_cell;
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
     unsigned long long hq = 0;
     double xd[3] = {0, 0, 0};
@@ -774,7 +780,7 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         lo[2] = hi[2] = compact3(k);
         for (int a = 0; a < 3; a++) xd[a] = P.pos_s[3 * (size_t)T.r + a];
         double h = P.soft_s[T.r];
-        hq = hq_of(h, P.fr.scale);
+        hq = hq_of(h, fr.scale);
         T.h = (float)h;
         T.sink = P.sink_s[T.r] != 0;
     }
@@ -795,9 +801,9 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         hq = t > hq ? t : hq;
     }
     {
-        double c0 = P.fr.x0[0] + (double)T.cg[0] * P.fr.half_cell;
-        double c1 = P.fr.x0[1] + (double)T.cg[1] * P.fr.half_cell;
-        double c2 = P.fr.x0[2] + (double)T.cg[2] * P.fr.half_cell;
+        double c0 = fr.x0[0] + (double)T.cg[0] * fr.half_cell;
+        double c1 = fr.x0[1] + (double)T.cg[1] * fr.half_cell;
+        double c2 = fr.x0[2] + (double)T.cg[2] * fr.half_cell;
         T.ox = (float)(xd[0] - c0);
         T.oy = (float)(xd[1] - c1);
         T.oz = (float)(xd[2] - c2);
@@ -822,7 +828,7 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
         W.off_p = P.dbg_off[2 * g + 1];
     }
 
-    if (lane == 0) stack[0] = make_int2(0, 1);
+    if (lane == 0) stack[0] = make_int2(cloud, 1);
     W.sp = 1;
     __syncwarp();
 
@@ -1107,7 +1113,8 @@ __device__ inline void put_group(int *gflag, int *gcnt, int tf, int tc)
 }
 
 __global__ void k_group_marks(const int32_t *nfirst, const int32_t *ncount, const int32_t *nchild_first,
-                              const int32_t *nnchild, int nn, const int *pre, int G, int *gflag, int *gcnt)
+                              const int32_t *nnchild, int nn, int nroots, const int *pre, int G, int *gflag,
+                              int *gcnt)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
         int f = nfirst[i];
@@ -1115,8 +1122,9 @@ __global__ void k_group_marks(const int32_t *nfirst, const int32_t *ncount, cons
         int c = pre[f + ncount[i]] - tf;
         if (c == 0) continue;
         bool leaf = nnchild[i] == 0;
-        if (i == 0 && c <= G) put_group(gflag, gcnt, tf, c);
-        if (i == 0 && c > G && leaf)
+        const bool root = i < nroots;
+        if (root && c <= G) put_group(gflag, gcnt, tf, c);
+        if (root && c > G && leaf)
             for (int s = 0; s < c; s += G) put_group(gflag, gcnt, tf + s, min(G, c - s));
         if (c <= G || leaf) continue;
         int run_first = -1, run_count = 0;
@@ -1271,7 +1279,7 @@ static int form_groups(Tree *t, const int64_t *active, int64_t n_active, Work &w
     scan_exclusive(w.flag, w.pre, t->d_n, n, nullptr, nullptr, w.scr, s);
     k_compact<<<grid_for(n, BT), BT, 0, s>>>(w.flag, w.pre, n, w.tgt);
     k_group_marks<<<grid_for(t->nn, BT), BT, 0, s>>>(t->nfirst, t->ncount, t->nchild_first, t->nnchild, t->nn,
-                                                     w.pre, t->prm.group_size, w.gflag, w.gcnt);
+                                                     t->nclouds, w.pre, t->prm.group_size, w.gflag, w.gcnt);
     scan_exclusive(w.gflag, w.goff, w.pre + n, n, nullptr, nullptr, w.scr, s);
     k_group_table<<<grid_for(n, BT), BT, 0, s>>>(w.gflag, w.gcnt, w.goff, w.pre + n, w.gtab);
     *d_ngroups = nullptr;
@@ -1308,9 +1316,10 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.nQ = t->nQ;
     P.res64 = nullptr;
     P.sink_s = t->sink_s;
-    P.fr = t->frame_h;
+    P.frames = t->d_frame;
+    P.pcloud = t->pcloud;
+    P.nclouds = t->nclouds;
     P.nn = t->nn;
-    P.s22 = (float)t->frame_h.half_cell;
     const double th = t->prm.theta;
     for (int l = 0; l <= SFG_LMAX; l++) {
         double v = ldexp(1.0, 2 * (SFG_LMAX - l)) / (th * th);
