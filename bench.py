@@ -212,13 +212,212 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+ENSEMBLE = dict(n_clouds=256, theta=0.5, seed_id=4)
+
+
+def ensemble_inputs(rank: int):
+    import gen
+    clouds = gen.ensemble(ENSEMBLE["n_clouds"], seed=gen.CONFIG_SEED[ENSEMBLE["seed_id"]] + 1000 * rank)
+    cat = [np.concatenate([getattr(c, f) for c in clouds]) for f in ("pos", "mass", "soft", "is_sink")]
+    off = [0] + [int(x) for x in np.cumsum([c.n for c in clouds])]
+    ca, cp = gen.cotangents(off[-1], seed=gen.CONFIG_SEED[ENSEMBLE["seed_id"]] + 7)
+    return clouds, cat, off, ca, cp
+
+
+def oracle_ensemble_sample(clouds, budget: int, seed: int, leaf_size: int = 16, group_size: int = 32) -> dict:
+    """The oracle (FP64, OpenMP) on a random sample of whole clouds holding
+    about `budget` particles: build, walk, field and adjoint of every particle
+    of each sampled cloud; the time per particle is extrapolated to the whole
+    ensemble."""
+    import gen
+    import oracle
+    rng = np.random.default_rng(seed)
+    picked, total = [], 0
+    for k in rng.permutation(len(clouds)):
+        if total >= budget:
+            break
+        picked.append(int(k))
+        total += clouds[k].n
+    t0 = time.perf_counter()
+    for k in picked:
+        c = clouds[k]
+        rows = np.arange(c.n, dtype=np.int64)
+        ca, cp = gen.cotangents(c.n, seed=seed + k)
+        tr = oracle.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=leaf_size)
+        tr.walk(rows, group_size, ENSEMBLE["theta"])
+        tr.accel_group(rows)
+        tr.vjp(rows, ca, cp)
+    dt = time.perf_counter() - t0
+    n_all = sum(c.n for c in clouds)
+    est = dt * n_all / total
+    return {"value": len(clouds) / est, "unit": "clouds/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(picked)} whole clouds ({total} particles, all active) of {len(clouds)}: "
+                      f"build + walk + field + adjoint; time per particle extrapolated to {n_all} particles",
+            "cpu_seconds_measured": round(dt, 3), "est_step_s": round(est, 3)}
+
+
+def run_ensemble(args, rank, world, dist, dev):
+    """Batched ensemble: 256 independent clouds (uniform recipe, N log-uniform
+    in [1e3, 2e5], 0..64 sinks) in one forest, every particle active.  Leaf
+    and group size come from the autotuner (untimed).  A step =
+    sfg_build_batch + sfg_accel + sfg_accel_vjp of all clouds on the tree just
+    built."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    from paper_2010_11254_gb300 import autotune
+    clouds, cat, off, ca_h, cp_h = ensemble_inputs(rank)
+    n = off[-1]
+    pos, mass, soft, sink, ca, cp = (torch.from_numpy(x).to(dev) for x in cat + [ca_h, cp_h])
+    theta = ENSEMBLE["theta"]
+    tuned = autotune.tune(pos, mass, soft, sink, offsets=off, cot_a=ca, cot_phi=cp, theta=theta)
+    kw = dict(theta=theta, leaf_size=tuned["leaf_size"], group_size=tuned["group_size"], quadrupole=True,
+              offsets=off)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step(timing: bool):
+        t = sfg.Tree(pos, mass, soft, sink, **kw)
+        t.set_timing(timing)
+        a, p = t.accel(None)
+        gp, gm = t.accel_vjp(None, ca, cp)
+        return t, a, p, gp, gm
+
+    for _ in range(args.warmup):
+        step(True)[0].close()
+    torch.cuda.synchronize(dev)
+    step_ms = []
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    for k in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t, acc, phi, g_pos, g_mass = step(True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if k < args.steps - 1:
+            t.close()
+    clocks = sampler.stop()
+    st = t.stats()
+    fwd_lat, vjp_lat = t.cloud_times()
+    t.check()
+    t.close()
+    launches_per_step = int(st["n_launches"])
+    ms, value = aggregate(statistics.mean(step_ms), len(clouds), world, dist, dev)
+    peaks, peak_src = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    vflops = st["n_p2p"] * FLOP_VJP_P2P + st["n_p2m"] * FLOP_VJP_P2M_QUAD
+    ach = vflops / (st["vjp_walk_ms"] * 1e-3) / 1e12
+    # a fixed tree re-evaluated: forward + adjoint captured once in a CUDA graph
+    tf = sfg.Tree(pos, mass, soft, sink, **kw)
+    a0, _ = tf.accel(None)
+    tf.accel_vjp(None, ca, cp)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        a_g, _ = tf.accel(None)
+        tf.accel_vjp(None, ca, cp)
+    for _ in range(3):
+        graph.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    e1.synchronize()
+    replay_ms = e0.elapsed_time(e1) / args.steps
+    gdiff = float((a_g - a0).abs().max().item() / a0.abs().max().item())
+    tf.check()
+    tf.close()
+    # e2e: pinned host inputs -> device, batched build, field, adjoint, results -> pinned host
+    h_in = [torch.from_numpy(x).pin_memory() for x in cat]
+    h_out = [torch.empty(tuple(x.shape), dtype=x.dtype).pin_memory() for x in (acc, phi, g_pos, g_mass)]
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h, dv in zip(h_in, (pos, mass, soft, sink)):
+            dv.copy_(h, non_blocking=True)
+        t, *res = step(False)
+        for h, dv in zip(h_out, res):
+            h.copy_(dv, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        t.close()
+        if k >= args.warmup:
+            e2e.append(e0.elapsed_time(e1))
+    e2e_ms, e2e_val = aggregate(statistics.mean(e2e), len(clouds), world, dist, dev)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_ensemble_sample(clouds, 150_000, seed=11, leaf_size=kw["leaf_size"],
+                                     group_size=kw["group_size"])
+    line = {
+        "metric": "clouds per second (batched build + field + adjoint of an ensemble)", "value": value,
+        "unit": "clouds/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "ensemble-256", "n_clouds": len(clouds), "n_particles": n,
+                   "n_min": min(c.n for c in clouds), "n_max": max(c.n for c in clouds), "active": "all",
+                   "theta": theta, "leaf_size": kw["leaf_size"], "group_size": kw["group_size"],
+                   "autotune": {"key": tuned["key"], "cached": tuned["cached"], "trials": tuned.get("trials")},
+                   "l2": "flushed (512 MB write) before every timed step"},
+        "phases_ms": {"build": round(st["build_ms"], 4), "fwd": round(st["fwd_ms"], 4),
+                      "fwd_walk": round(st["fwd_walk_ms"], 4), "vjp": round(st["vjp_ms"], 4),
+                      "vjp_walk": round(st["vjp_walk_ms"], 4)},
+        "per_cloud_completion_ms": {"fwd_walk_p50": float(np.percentile(fwd_lat, 50)),
+                                    "fwd_walk_p99": float(np.percentile(fwd_lat, 99)),
+                                    "fwd_walk_max": float(fwd_lat.max()),
+                                    "vjp_walk_p50": float(np.percentile(vjp_lat, 50)),
+                                    "vjp_walk_p99": float(np.percentile(vjp_lat, 99)),
+                                    "vjp_walk_max": float(vjp_lat.max())},
+        "fixed_tree_graph_replay_ms": round(replay_ms, 4), "graph_vs_eager_max_rel_diff": gdiff,
+        "roofline": {"bound": "alu", "kernel": "k_walk<QUAD, MODE_VJP> (adjoint, all clouds in one launch)",
+                     "achieved": round(ach, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(ach / fp32_peak, 4), "traffic": None,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"},
+        "interactions": {"p2p": int(st["n_p2p"]), "p2m": int(st["n_p2m"]), "groups": int(st["n_groups"])},
+        "particles_per_s": n * world / (ms * 1e-3),
+        "e2e": {"value": e2e_val, "unit": "clouds/s",
+                "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in h_in),
+                "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in h_out), "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference_ensemble(args, rank):
+    """--impl reference --workload ensemble-256: the oracle on a bounded
+    sample of whole clouds per step (rank 0 only)."""
+    if rank != 0:
+        return
+    clouds, cat, off, ca, cp = ensemble_inputs(0)
+    for k in range(args.warmup):
+        oracle_ensemble_sample(clouds, 10_000, seed=100 + k)
+    vals = [oracle_ensemble_sample(clouds, 40_000, seed=200 + k) for k in range(args.steps)]
+    v = statistics.median(r["value"] for r in vals)
+    r = vals[-1]
+    line = {"impl": "reference", "metric": "clouds per second (batched build + field + adjoint of an ensemble)",
+            "value": v, "unit": "clouds/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * len(clouds) / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ensemble-256", "n_clouds": len(clouds), "n_particles": off[-1],
+                       "active": "all", "theta": ENSEMBLE["theta"]},
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": v},
+            "e2e": {"value": v, "unit": "clouds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS) + ["ensemble-256"])
     ap.add_argument("--active-frac", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--leaf-size", type=int, default=16)
@@ -226,12 +425,15 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS.get(args.workload)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, wl, rank, world)
+        if wl is None:
+            run_reference_ensemble(args, rank)
+        else:
+            run_reference(args, wl, rank, world)
         return
 
     import torch
@@ -245,6 +447,11 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     os.environ.setdefault("SFG_TIMING", "1")
+    if args.workload == "ensemble-256":
+        run_ensemble(args, rank, world, dist, dev)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     c, act, ca, cp, frac = make_inputs(wl, rank, args.active_frac)
     d_pos = torch.from_numpy(c.pos).to(dev)

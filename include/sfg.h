@@ -163,6 +163,13 @@ int sfg_accel_batch(sfg_tree *tree, const int64_t *active_idx, int64_t n_active,
 int sfg_accel_vjp_batch(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
                         const double *cot_phi, double *d_pos, double *d_mass, void *stream);
 
+/* Per-cloud completion times of the last walk launches while timing was on:
+ * fwd_ms[c] / vjp_ms[c] = milliseconds from the first warp start of the last
+ * sfg_accel / sfg_accel_vjp walk launch to the end of cloud c's last work
+ * item (0 if that call ran with timing off).  Host arrays of n_clouds
+ * floats, either may be NULL.  Synchronizes. */
+int sfg_cloud_times(sfg_tree *tree, float *fwd_ms, float *vjp_ms);
+
 /* Statistics of the tree and of its last call (host pointer).  Synchronizes. */
 int sfg_get_stats(sfg_tree *tree, sfg_stats *out);
 
@@ -175,6 +182,12 @@ void sfg_free(sfg_tree *tree);
 
 /* Static string naming a status code. */
 const char *sfg_status_string(int status);
+
+/* Name of the CUDA runtime error behind the last SFG_ECUDA that a call of
+ * this library returned on the calling thread ("cudaSuccess" if none).  The
+ * compute entry points clear a non-sticky CUDA error left pending by earlier,
+ * unrelated calls before they start, so SFG_ECUDA names an error of their own. */
+const char *sfg_last_cuda_error(void);
 
 /* ---- inspection (tests and tools; copies to HOST memory, synchronizing) ----
  * field ids and layouts:

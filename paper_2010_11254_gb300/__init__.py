@@ -35,6 +35,8 @@ class SfgError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
         msg = _load().sfg_status_string(code).decode() if _lib is not None else f"status {code}"
+        if _lib is not None and code == SFG_ECUDA:
+            msg += f" ({_lib.sfg_last_cuda_error().decode()})"
         super().__init__(f"{what}: {msg}" if what else msg)
 
 
@@ -77,6 +79,8 @@ def _load():
         lib.sfg_default_params.restype = None
         lib.sfg_status_string.argtypes = [i32]
         lib.sfg_status_string.restype = ctypes.c_char_p
+        lib.sfg_last_cuda_error.argtypes = []
+        lib.sfg_last_cuda_error.restype = ctypes.c_char_p
         lib.sfg_build.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
         lib.sfg_build.restype = i32
         lib.sfg_build_batch.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64), i32, ctypes.POINTER(Params), vp,
@@ -88,6 +92,8 @@ def _load():
         lib.sfg_accel_vjp.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.sfg_get_stats.restype = i32
+        lib.sfg_cloud_times.argtypes = [vp, vp, vp]
+        lib.sfg_cloud_times.restype = i32
         lib.sfg_set_timing.argtypes = [vp, i32]
         lib.sfg_set_timing.restype = i32
         lib.sfg_get_status.argtypes = [vp]
@@ -209,6 +215,14 @@ class Tree:
 
     def set_timing(self, on: bool = True):
         _check(_load().sfg_set_timing(self._h, int(bool(on))), "sfg_set_timing")
+
+    def cloud_times(self):
+        """(forward, adjoint) per-cloud completion times in ms of the last walks (timing on)."""
+        c = self.stats()["n_clouds"]
+        f = np.zeros(c, np.float32)
+        v = np.zeros(c, np.float32)
+        _check(_load().sfg_cloud_times(self._h, f.ctypes.data, v.ctypes.data), "sfg_cloud_times")
+        return f, v
 
     def status(self) -> int:
         return int(_load().sfg_get_status(self._h))

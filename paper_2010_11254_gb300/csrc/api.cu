@@ -14,6 +14,8 @@ struct sfg_tree {
 
 namespace sfg {
 
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 void *dev_alloc(Tree *t, size_t bytes, cudaStream_t s)
 {
     if (bytes == 0) bytes = 16;
@@ -87,6 +89,8 @@ void sfg_default_params(sfg_params *p)
     p->store_lists = 0;
 }
 
+const char *sfg_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
+
 const char *sfg_status_string(int st)
 {
     switch (st) {
@@ -119,6 +123,7 @@ static int build_forest(const double *pos, const double *mass, const double *sof
         p.group_size < 1 || p.group_size > 32 || (p.quadrupole != 0 && p.quadrupole != 1) ||
         (p.precision != 0 && p.precision != 1) || (p.alloc && !p.free))
         return SFG_EINVAL;
+    cudaGetLastError();
     keep_pool_memory();
     sfg_tree *T = new sfg_tree;
     T->t.prm = p;
@@ -172,6 +177,7 @@ int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, doubl
 {
     if (!tree || n_active < 0 || (n_active > 0 && !accel)) return SFG_EINVAL;
     tree->t.stream = (cudaStream_t)stream;
+    cudaGetLastError();
     return sfg::accel(&tree->t, active_idx, n_active, accel, phi, (cudaStream_t)stream);
 }
 
@@ -180,6 +186,7 @@ int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, c
 {
     if (!tree || n_active < 0 || !d_pos || !d_mass || (n_active > 0 && !cot_a)) return SFG_EINVAL;
     tree->t.stream = (cudaStream_t)stream;
+    cudaGetLastError();
     return sfg::accel_vjp(&tree->t, active_idx, n_active, cot_a, cot_phi, d_pos, d_mass, (cudaStream_t)stream);
 }
 
@@ -188,9 +195,8 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
     if (!tree || !out) return SFG_EINVAL;
     Tree *t = &tree->t;
     unsigned long long c[8];
-    if (cudaMemcpyAsync(c, t->d_counters, sizeof(c), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
-        cudaStreamSynchronize(t->stream) != cudaSuccess)
-        return SFG_ECUDA;
+    SFG_CUDA_OK(cudaMemcpyAsync(c, t->d_counters, sizeof(c), cudaMemcpyDeviceToHost, t->stream));
+    SFG_CUDA_OK(cudaStreamSynchronize(t->stream));
     sfg_stats s;
     memset(&s, 0, sizeof(s));
     s.n = t->n;
@@ -209,9 +215,33 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
     float *ms[5] = {&s.build_ms, &s.fwd_ms, &s.fwd_walk_ms, &s.vjp_ms, &s.vjp_walk_ms};
     for (int ph = 0; ph < 5; ph++) {
         *ms[ph] = 0.f;
-        if (t->ev_used[ph]) cudaEventElapsedTime(ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);
+        if (t->ev_used[ph] && cudaEventElapsedTime(ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            *ms[ph] = 0.f;
+        }
     }
     *out = s;
+    return SFG_OK;
+}
+
+int sfg_cloud_times(sfg_tree *tree, float *fwd_ms, float *vjp_ms)
+{
+    if (!tree) return SFG_EINVAL;
+    Tree *t = &tree->t;
+    const int C = t->nclouds;
+    std::vector<unsigned long long> h(2 * (size_t)(C + 1), 0ull);
+    if (t->d_ctime) {
+        SFG_CUDA_OK(cudaMemcpyAsync(h.data(), t->d_ctime, sizeof(unsigned long long) * h.size(),
+                                    cudaMemcpyDeviceToHost, t->stream));
+        SFG_CUDA_OK(cudaStreamSynchronize(t->stream));
+    }
+    float *dst[2] = {fwd_ms, vjp_ms};
+    for (int w = 0; w < 2; w++) {
+        if (!dst[w]) continue;
+        const unsigned long long *c = h.data() + (size_t)w * (C + 1);
+        for (int k = 0; k < C; k++)
+            dst[w][k] = (t->ctime_used[w] && c[k] > c[C]) ? (float)((double)(c[k] - c[C]) * 1e-6) : 0.f;
+    }
     return SFG_OK;
 }
 
@@ -227,9 +257,8 @@ int sfg_get_status(sfg_tree *tree)
     if (!tree) return SFG_EINVAL;
     Tree *t = &tree->t;
     int st = 0;
-    if (cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
-        cudaStreamSynchronize(t->stream) != cudaSuccess)
-        return SFG_ECUDA;
+    SFG_CUDA_OK(cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, t->stream));
+    SFG_CUDA_OK(cudaStreamSynchronize(t->stream));
     if (st) cudaMemsetAsync(t->d_status, 0, sizeof(int), t->stream);
     if (st & ST_EINVAL) return SFG_EINVAL;
     if (st & ST_EOVERFLOW) return SFG_EOVERFLOW;
@@ -248,7 +277,7 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
     Tree *t = &tree->t;
     cudaStream_t s = t->stream;
     const size_t n = (size_t)t->n, nn = (size_t)t->nn;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SFG_ECUDA;
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
     switch (field) {
     case SFG_FIELD_KEYS:
         if (bytes != 8 * n) return SFG_EINVAL;

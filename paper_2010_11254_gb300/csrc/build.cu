@@ -19,6 +19,7 @@
 //      is compiled without FMA contraction, so the FP64 moments are
 //      reproducible bit for bit.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -63,12 +64,20 @@ __device__ inline int block_incl_scan(int v, int *sh, int *total)
     return x + pre;
 }
 
-__device__ inline int scan_len(const int *d_lo, const int *d_hi) { return *d_hi - (d_lo ? *d_lo : 0); }
+// Length of the scanned range [lo, min(hi, max_n)): entries at max_n and
+// beyond were never written (a level of the octree clamped to the node
+// capacity), so they are not read.
+__device__ inline int scan_len(const int *d_lo, const int *d_hi, int max_n)
+{
+    int lo = d_lo ? *d_lo : 0;
+    int hi = min(*d_hi, max_n);
+    return hi > lo ? hi - lo : 0;
+}
 
 __global__ void k_scan_reduce(const int *in, const int *d_lo, const int *d_hi, int max_n, int *bsum)
 {
     __shared__ int sh[32];
-    int n = min(scan_len(d_lo, d_hi), max_n);
+    int n = scan_len(d_lo, d_hi, max_n);
     int chunk = (n + SCAN_NB - 1) / SCAN_NB;
     int b0 = min(n, blockIdx.x * chunk), b1 = min(n, b0 + chunk);
     int s = 0;
@@ -87,16 +96,16 @@ __global__ void k_scan_top(int *bsum, const int *d_lo, const int *d_hi, int max_
     int incl = block_incl_scan(v, sh, &tot);
     bsum[threadIdx.x] = incl - v;
     if (threadIdx.x == 0) {
-        int n = min(scan_len(d_lo, d_hi), max_n);
+        int n = scan_len(d_lo, d_hi, max_n);
         out[n] = tot;
-        if (extra_dst) *extra_dst = *extra_base + tot;
+        if (extra_dst) *extra_dst = (int)min((long long)*extra_base + tot, (long long)INT_MAX);
     }
 }
 
 __global__ void k_scan_down(const int *in, int *out, const int *d_lo, const int *d_hi, int max_n, const int *bsum)
 {
     __shared__ int sh[32];
-    int n = min(scan_len(d_lo, d_hi), max_n);
+    int n = scan_len(d_lo, d_hi, max_n);
     int chunk = (n + SCAN_NB - 1) / SCAN_NB;
     int b0 = min(n, blockIdx.x * chunk), b1 = min(n, b0 + chunk);
     int carry = bsum[blockIdx.x];
@@ -737,7 +746,9 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     dev_free(t, cloud_of, s);
 
     // octree, retried with a larger node capacity if the estimate was short
-    int64_t cap64 = 4 * ((int64_t)n / (t->prm.leaf_size + 1)) + 4096 + 64 * (int64_t)C;
+    // measured on uniform and clumpy clouds: nodes / n <= 1.5, 0.77, 0.52,
+    // 0.32, 0.16 for leaf sizes 1, 4, 8, 16, 32
+    int64_t cap64 = 6 * ((int64_t)n / (t->prm.leaf_size + 2)) + 4096 + 64 * (int64_t)C;
     int *tmp = nullptr, *tmpo = nullptr;
     for (int attempt = 0;; attempt++) {
         if (cap64 > 0x7fffffff) cap64 = 0x7fffffff;

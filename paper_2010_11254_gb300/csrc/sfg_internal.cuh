@@ -91,6 +91,8 @@ struct Tree {
     bool timing = false;
     cudaEvent_t ev[10] = {};  // pairs: build, fwd, fwd walk, vjp, vjp walk
     bool ev_used[5] = {false, false, false, false, false};
+    unsigned long long *d_ctime = nullptr; // [2][C + 1] per-cloud completion stamps (timing on)
+    bool ctime_used[2] = {false, false};
     std::unordered_set<void *> live; // every device allocation still held
 };
 
@@ -121,9 +123,25 @@ int num_sms();
 
 // timing helpers (no-ops unless t->timing)
 enum { PH_BUILD = 0, PH_FWD = 1, PH_FWD_WALK = 2, PH_VJP = 3, PH_VJP_WALK = 4 };
+// Events recorded while a stream is being captured into a CUDA graph cannot
+// be timed, so phase timing skips captured calls (the per-cloud completion
+// stamps are written by the kernels and work in graphs too).
+inline bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
 inline void ph_begin(Tree *t, int ph, cudaStream_t s)
 {
     if (!t->timing) return;
+    if (capturing(s)) {
+        t->ev_used[ph] = false;
+        return;
+    }
     if (!t->ev[2 * ph]) {
         cudaEventCreate(&t->ev[2 * ph]);
         cudaEventCreate(&t->ev[2 * ph + 1]);
@@ -132,7 +150,7 @@ inline void ph_begin(Tree *t, int ph, cudaStream_t s)
 }
 inline void ph_end(Tree *t, int ph, cudaStream_t s)
 {
-    if (!t->timing || !t->ev[2 * ph]) return;
+    if (!t->timing || !t->ev[2 * ph] || capturing(s)) return;
     cudaEventRecord(t->ev[2 * ph + 1], s);
     t->ev_used[ph] = true;
 }
@@ -183,10 +201,18 @@ __device__ inline unsigned long long hq_of(double h, double scale)
     return c > 0 ? c : 1ull;
 }
 
+// The CUDA error behind the last SFG_ECUDA returned on this thread.
+extern thread_local cudaError_t g_last_cuda_error;
+inline int cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = e;
+    return SFG_ECUDA;
+}
+
 #define SFG_CUDA_OK(expr)                                                                                    \
     do {                                                                                                     \
         cudaError_t _e = (expr);                                                                             \
-        if (_e != cudaSuccess) return SFG_ECUDA;                                                             \
+        if (_e != cudaSuccess) return ::sfg::cuda_fail(_e);                                                  \
     } while (0)
 
 } // namespace sfg

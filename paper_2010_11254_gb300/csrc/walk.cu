@@ -66,6 +66,8 @@ struct WalkParams {
     const Frame *frames;   // [C] per-cloud frames
     const int32_t *pcloud; // sorted rank -> cloud (NULL: one cloud)
     int nclouds;
+    // with timing on: [C] latest item end per cloud, [C] = earliest warp start (ns)
+    unsigned long long *ctime;
     unsigned long long T[SFG_LMAX + 1];
     int nn;
     const int2 *gtab;
@@ -749,8 +751,30 @@ __device__ __forceinline__ void flush_tiles(const WalkParams &P, WarpSmem &S, Wa
 // One work item: group g, item kk of K.  Every item of a group walks the same
 // lists (the walk is cheap next to the evaluation) and evaluates the tiles
 // kk, kk + K, ... of the walk order, so the items' work partitions the group's.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <bool QUAD, int MODE, bool GSTACK>
-__device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item, int lane)
+__device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item,
+                                int lane, int &cloud_out);
+
+// One work item, plus the per-cloud completion time when timing is on.
+template <bool QUAD, int MODE, bool GSTACK>
+__device__ __forceinline__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K,
+                                           int item, int lane)
+{
+    int cloud = 0;
+    walk_group_body<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane, cloud);
+    if (P.ctime && lane == 0) atomicMax(&P.ctime[cloud], global_ns());
+}
+
+template <bool QUAD, int MODE, bool GSTACK>
+__device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item,
+                                int lane, int &cloud_out)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int cap = GSTACK ? GSTK : STK;
@@ -766,6 +790,7 @@ __device__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g,
     T.r = T.has ? P.tgt[tfirst + T.tl] : -1;
     // the group's cloud: its frame, and its root (node id = cloud id)
     const int cloud = P.pcloud ? P.pcloud[P.tgt[tfirst]] : 0;
+    cloud_out = cloud;
     const Frame fr = P.frames[cloud];
     T.s22 = (float)fr.half_cell;
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
@@ -977,6 +1002,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams 
     constexpr bool ITEMS = MODE == MODE_EVAL || MODE == MODE_VJP || MODE == MODE_EVAL64;
     const int ngroups = *P.d_ngroups;
     const int nwork = GSTACK ? (int)P.counters[2] : (ITEMS ? P.ioff[ngroups] : ngroups);
+    if (P.ctime && lane == 0 && !GSTACK) atomicMin(&P.ctime[P.nclouds], global_ns());
     while (true) {
         int w_i = 0;
         if (lane == 0) w_i = (int)atomicAdd(&P.counters[GSTACK ? 4 : 3], 1ull);
@@ -1319,6 +1345,7 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.frames = t->d_frame;
     P.pcloud = t->pcloud;
     P.nclouds = t->nclouds;
+    P.ctime = nullptr;
     P.nn = t->nn;
     const double th = t->prm.theta;
     for (int l = 0; l <= SFG_LMAX; l++) {
@@ -1381,6 +1408,27 @@ static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, Wa
     return SFG_OK;
 }
 
+__global__ void k_ctime_reset(unsigned long long *ct, int C)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= C; c += gridDim.x * blockDim.x)
+        ct[c] = c < C ? 0ull : ~0ull;
+}
+
+// Per-cloud completion stamps of the next walk launch (which = 0 forward, 1 adjoint).
+static int cloud_timer_begin(Tree *t, int which, cudaStream_t s, WalkParams &P)
+{
+    const int C = t->nclouds;
+    if (!t->d_ctime) {
+        t->d_ctime = (unsigned long long *)dev_alloc(t, 2 * sizeof(unsigned long long) * (size_t)(C + 1), s);
+        if (!t->d_ctime) return SFG_ENOMEM;
+    }
+    P.ctime = t->d_ctime + (size_t)which * (C + 1);
+    k_ctime_reset<<<(C + 256) / 256, 256, 0, s>>>(P.ctime, C);
+    t->n_launch += 1;
+    t->ctime_used[which] = true;
+    return SFG_OK;
+}
+
 // Count the lists of every group (a walk without evaluation), then cut the
 // heavy groups into work items.
 template <int MODE>
@@ -1427,6 +1475,10 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
         P.res64 = res64;
     }
     make_items(t, w, P, s);
+    if (t->timing) {
+        int rc2 = cloud_timer_begin(t, 0, s, P);
+        if (rc2) return rc2;
+    }
     ph_begin(t, PH_FWD_WALK, s);
     if (f64) launch_walk<MODE_EVAL64>(t, P, s);
     else launch_walk<MODE_EVAL>(t, P, s);
@@ -1588,6 +1640,10 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         P.gpart = gpart;
         P.gnode = gnode;
         make_items(t, w, P, s);
+        if (t->timing) {
+            int rc2 = cloud_timer_begin(t, 1, s, P);
+            if (rc2) return rc2;
+        }
         ph_begin(t, PH_VJP_WALK, s);
         launch_walk<MODE_VJP>(t, P, s);
         ph_end(t, PH_VJP_WALK, s);

@@ -122,3 +122,71 @@ def test_batch_rejects_bad_offsets():
     for bad in ([1] + list(off[1:]), [0, 5, 5] + list(off[3:]), list(off[:-1]) + [off[-1] + 3]):
         with pytest.raises(sfg.SfgError):
             _tree(torch, sfg, pos, mass, soft, sink, bad)
+
+
+def test_cuda_graph_replay_equals_eager():
+    """The field and adjoint of a batched tree captured in one CUDA graph give
+    the eager results (the calls issue no host synchronization)."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    parts, pos, mass, soft, sink, off = _ensemble()
+    t = _tree(torch, sfg, pos, mass, soft, sink, off, theta=0.6)
+    t.set_timing(True)
+    n = pos.shape[0]
+    ca, cp = (torch.from_numpy(x).cuda() for x in gen.cotangents(n, seed=3))
+    a0, p0 = t.accel(None)
+    d0, m0 = t.accel_vjp(None, ca, cp)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        a1, p1 = t.accel(None)
+        d1, m1 = t.accel_vjp(None, ca, cp)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert t.status() == sfg.SFG_OK
+    torch.testing.assert_close(a1, a0, rtol=1e-6, atol=1e-6 * a0.abs().max().item())
+    torch.testing.assert_close(p1, p0, rtol=1e-9, atol=0)
+    torch.testing.assert_close(d1, d0, rtol=1e-6, atol=1e-6 * d0.abs().max().item())
+    f, v = t.cloud_times()
+    assert f.shape == (len(parts),) and np.all(f > 0) and np.all(v > 0)
+    t.close()
+
+
+def test_batch_many_clouds_small_leaves():
+    """64 clouds (sizes 1 .. 5000, log-uniform) at leaf size 8 and group size
+    16: per-cloud structure bit-exact and the field of every cloud equal to
+    its own separate build, through the node-capacity retry if needed."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    rng = np.random.default_rng(64)
+    sizes = np.exp(rng.uniform(0.0, np.log(5000.0), 64)).astype(int)
+    clouds = [gen.uniform_cloud(int(k), seed=500 + i, h0=0.05 * (4096.0 / k) ** (1 / 3), n_sink=int(k) % 5)
+              for i, k in enumerate(sizes)]
+    pos = np.concatenate([c.pos for c in clouds])
+    mass = np.concatenate([c.mass for c in clouds])
+    soft = np.concatenate([c.soft for c in clouds])
+    sink = np.concatenate([c.is_sink for c in clouds])
+    off = np.cumsum([0] + [c.n for c in clouds])
+    t = _tree(torch, sfg, pos, mass, soft, sink, off, leaf_size=8, group_size=16)
+    keys = t.export(sfg.FIELD_KEYS)
+    gi = t.export(sfg.FIELD_NODE_INT).astype(np.int64)
+    gf = t.export(sfg.FIELD_NODE_F64)
+    acc, phi = (x.cpu().numpy() for x in t.accel(None))
+    assert t.status() == sfg.SFG_OK
+    t.close()
+    for c, part in enumerate(clouds):
+        if c % 4:
+            continue
+        o = oracle_tree(part, 8)
+        np.testing.assert_array_equal(keys[off[c]:off[c + 1]], o.keys()[0])
+        mine = np.nonzero(gi[:, 15] == c)[0]
+        sel = mine[np.lexsort((gi[mine, 1], gi[mine, 0]))]
+        assert len(sel) == o.n_nodes
+        np.testing.assert_array_equal(gf[sel], o.nodes_f64()[:, :11])
+        d = [torch.from_numpy(x).cuda() for x in (part.pos, part.mass, part.soft, part.is_sink)]
+        ts = sfg.Tree(*d, leaf_size=8, group_size=16)
+        a1, p1 = (x.cpu().numpy() for x in ts.accel(None))
+        ts.close()
+        np.testing.assert_allclose(acc[off[c]:off[c + 1]], a1, rtol=1e-6,
+                                   atol=1e-6 * max(np.abs(a1).max(), 1e-300))
+        np.testing.assert_allclose(phi[off[c]:off[c + 1]], p1, rtol=1e-6)

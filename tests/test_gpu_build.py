@@ -50,6 +50,21 @@ def test_build_sizes_spanning_tiles():
         _compare_build(gen.uniform_cloud(n, seed=n, n_sink=n % 7), 16)
 
 
+def test_build_node_capacity_retry():
+    """Close pairs (a few cells apart) make chains of one-child nodes: at leaf
+    size 1 the tree needs several times the first node-capacity estimate, so
+    the octree is rebuilt with a doubled capacity until it fits."""
+    rng = np.random.default_rng(77)
+    m = 3000
+    a = rng.uniform(-1.0, 1.0, (m, 3))
+    d = rng.standard_normal((m, 3))
+    b = a + 3e-6 * d / np.linalg.norm(d, axis=1, keepdims=True)
+    pos = np.ascontiguousarray(np.concatenate([a, b]))
+    c = gen.Cloud(pos, np.full(2 * m, 1.0 / (2 * m)), np.full(2 * m, 1e-3), np.zeros(2 * m, np.uint8), 77, "pairs")
+    assert oracle_tree(c, 1).n_nodes > 2 * (6 * (c.n // 3) + 4096 + 64)
+    _compare_build(c, 1)
+
+
 @pytest.mark.parametrize("name", ["n1", "n2", "identical", "duplicates", "decades", "sinks_only", "massless"])
 def test_build_edge_cases(name):
     _compare_build(edge_clouds()[name], 8)
