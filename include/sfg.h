@@ -61,7 +61,12 @@ typedef struct sfg_params {
     int quadrupole;  /* 1: monopole + quadrupole node fields; 0: monopole only (Sec. 2.2) */
     int precision;   /* 0: FP32 pair/multipole arithmetic on node-centred offsets, FP64
                         frame/moments/potential sums; 1: all-FP64 evaluation */
-    int store_lists; /* reserved: the adjoint always recomputes the forward's lists */
+    int store_lists; /* 1: walk once per call into stored interaction lists (two walks:
+                        count, then write), evaluate from them, and let the adjoint reuse
+                        the forward's lists when called with the same active set;
+                        0: every evaluation walks the tree itself.  Ignored (0) with
+                        precision = 1 and while the stream is captured into a CUDA graph
+                        (sizing the lists synchronizes the stream once). */
     /* Optional device allocator (stream-ordered).  NULL alloc => cudaMallocAsync. */
     void *(*alloc)(size_t bytes, void *stream, void *ctx);
     void (*free)(void *ptr, void *stream, void *ctx);
@@ -93,7 +98,7 @@ typedef struct sfg_stats {
 } sfg_stats;
 
 /* Fill *p with the defaults: G = 1, theta = 0.5, leaf_size = 16, group_size = 32,
- * quadrupole = 1, precision = 0, list_depth = 0, store_lists = 0, no allocator. */
+ * quadrupole = 1, precision = 0, list_depth = 0, store_lists = 1, no allocator. */
 void sfg_default_params(sfg_params *p);
 
 /* Build the tree of n particles (Sec. 2.2: the oct-tree over every gas cell and

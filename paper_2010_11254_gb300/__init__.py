@@ -115,7 +115,7 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         if v is None:
             continue
-        if k == "quadrupole":
+        if k in ("quadrupole", "store_lists"):
             v = int(bool(v))
         setattr(p, k, v)
     return p
@@ -142,9 +142,12 @@ class Tree:
     """A built tree over one cloud (``sfg_build``); owns its device memory."""
 
     def __init__(self, pos, mass, soft, is_sink=None, *, G: float = 1.0, theta: float = 0.5, leaf_size: int = 16,
-                 group_size: int = 32, quadrupole: bool = True, precision: int = 0, offsets=None):
+                 group_size: int = 32, quadrupole: bool = True, precision: int = 0, store_lists: bool = True,
+                 offsets=None):
         """offsets (host sequence of n_clouds + 1 ints) builds one forest over an
-        ensemble of independent clouds (sfg_build_batch)."""
+        ensemble of independent clouds (sfg_build_batch).  store_lists: evaluate
+        from interaction lists stored by one walk (the adjoint reuses the
+        forward's for the same active set) instead of walking per evaluation."""
         lib = _load()
         pos = _dev(pos, torch.float64, "pos")
         mass = _dev(mass, torch.float64, "mass")
@@ -161,7 +164,7 @@ class Tree:
         self.device = pos.device
         self.n = n
         self.params = default_params(G=G, theta=theta, leaf_size=leaf_size, group_size=group_size,
-                                     quadrupole=quadrupole, precision=precision)
+                                     quadrupole=quadrupole, precision=precision, store_lists=store_lists)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             if offsets is None:

@@ -86,7 +86,7 @@ void sfg_default_params(sfg_params *p)
     p->list_depth = 0;
     p->quadrupole = 1;
     p->precision = 0;
-    p->store_lists = 0;
+    p->store_lists = 1;
 }
 
 const char *sfg_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }

@@ -93,6 +93,18 @@ struct Tree {
     bool ev_used[5] = {false, false, false, false, false};
     unsigned long long *d_ctime = nullptr; // [2][C + 1] per-cloud completion stamps (timing on)
     bool ctime_used[2] = {false, false};
+    // stored interaction lists (store_lists): P2M node ids and P2P particle
+    // ranges of every group of the active set they were walked for, kept for
+    // the adjoint; the group table and list sizes stay in the workspace
+    int *lm = nullptr;
+    int2 *lr = nullptr;
+    long long lm_cap = 0, lr_cap = 0;
+    int64_t *la = nullptr; // copy of that active index array
+    int64_t la_cap = 0, la_n = -1;
+    bool la_all = false;   // it was NULL (every particle)
+    bool lists_ok = false;
+    int *d_flag = nullptr;       // device scratch word
+    long long *d_lscan = nullptr; // list-offset scan scratch + totals
     std::unordered_set<void *> live; // every device allocation still held
 };
 

@@ -37,7 +37,10 @@ constexpr int WALK_WARPS = 4;  // warps per block
 constexpr int WALK_MINB = 6;   // resident blocks per SM the register budget must allow
 constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
 constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
-constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4;
+constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4, MODE_LIST = 5;
+// list sizes per group written by the counting walk: P2M nodes, softened P2P
+// ranges and particles, Newtonian P2P ranges and particles
+constexpr int NCNT = 5;
 
 struct WarpSmem {
     int2 stack[STK];
@@ -64,6 +67,7 @@ struct WalkParams {
     const uint8_t *sink_s;
     const double *nM, *ncom, *nQ;
     const Frame *frames;   // [C] per-cloud frames
+    int npart;             // particles
     const int32_t *pcloud; // sorted rank -> cloud (NULL: one cloud)
     int nclouds;
     // with timing on: [C] latest item end per cloud, [C] = earliest warp start (ns)
@@ -93,6 +97,11 @@ struct WalkParams {
     int *dbg_counts;
     const long long *dbg_off;
     int *dbg_m, *dbg_p;
+    // stored lists: sizes (NCNT per group), first entries, P2M node ids, P2P ranges
+    const int *lcnt;
+    const long long *lmo, *lro;
+    int *lm;
+    int2 *lr;
     // adjoint
     const float4 *cot; // per distinct target: (cot_a, cot_phi)
     double *gpart;     // [n][4] sorted: d_pos, d_mass
@@ -185,8 +194,8 @@ __device__ __forceinline__ void pair_supports(const Tgt &T, const float4 &hh, fl
 }
 
 // ------------------------------------------------------- forward tiles ----
-template <bool QUAD>
-__device__ __forceinline__ void fwd_p2m(const WarpSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+template <bool QUAD, class SM>
+__device__ __forceinline__ void fwd_p2m(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
                                         double &phi)
 {
     float pt = 0.f;
@@ -223,7 +232,8 @@ __device__ __forceinline__ void fwd_p2m(const WarpSmem &S, int cnt, const Tgt &T
     phi += (double)pt;
 }
 
-__device__ __forceinline__ void fwd_p2p(const WarpSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+template <class SM>
+__device__ __forceinline__ void fwd_p2p(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
                                         double &phi)
 {
     float pt = 0.f;
@@ -268,8 +278,8 @@ __device__ __forceinline__ void fwd_p2p(const WarpSmem &S, int cnt, const Tgt &T
 // accumulator to lane t - 1 after each step; after T' steps lane t holds the
 // complete sum (over the group's targets) for source t of the block and adds
 // it to that source's gradient.
-template <bool QUAD>
-__device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
+template <bool QUAD, class SM>
+__device__ __forceinline__ void vjp_p2m(const WalkParams &P, const SM &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
     const int tp = T.tp, base = T.slice * tp;
@@ -332,7 +342,7 @@ __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, 
         for (int q = 0; q < (QUAD ? 10 : 4); q++) acc[q] = __shfl_sync(FULL, acc[q], nxt, tp);
     }
     const int k = base + T.tl;
-    if (k < cnt) {
+    if (k < cnt && S.tN[k] >= 0) {
         double *dst = P.gnode + 10 * (size_t)S.tN[k];
 #pragma unroll
         for (int q = 0; q < (QUAD ? 10 : 4); q++)
@@ -340,7 +350,8 @@ __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const WarpSmem &S, 
     }
 }
 
-__device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, int cnt, const Tgt &T, float c0,
+template <class SM>
+__device__ __forceinline__ void vjp_p2p(const WalkParams &P, const SM &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
     const int tp = T.tp, base = T.slice * tp;
@@ -396,7 +407,7 @@ __device__ __forceinline__ void vjp_p2p(const WalkParams &P, const WarpSmem &S, 
         am = __shfl_sync(FULL, am, nxt, tp);
     }
     const int k = base + T.tl;
-    if (k < cnt) {
+    if (k < cnt && __float_as_int(S.tA[k].z) >= 0) {
         double *dst = P.gpart + 4 * (size_t)__float_as_int(S.tA[k].z);
         if (a0 != 0.f) atomicAdd(dst, (double)a0);
         if (a1 != 0.f) atomicAdd(dst + 1, (double)a1);
@@ -533,28 +544,39 @@ __device__ __forceinline__ void fwd_p2p64(const WarpSmem &S, int cnt, const Tgt 
 }
 
 // --------------------------------------------------------- tile staging ----
-template <bool QUAD, bool NODEID>
-__device__ __forceinline__ void stage_p2m(const WalkParams &P, WarpSmem &S, const int *list, int cnt, const Tgt &T,
+template <bool QUAD, bool NODEID, class SM>
+__device__ __forceinline__ void stage_p2m(const WalkParams &P, SM &S, const int *list, int cnt, const Tgt &T,
                                           int lane)
 {
     if (lane < cnt) {
         int id = list[lane];
-        float4 e0 = P.E0[id];
-        float4 e2 = P.E2[id];
-        float px = fmaf((float)(__float_as_int(e2.y) - T.cg[0]), T.s22, e0.x);
-        float py = fmaf((float)(__float_as_int(e2.z) - T.cg[1]), T.s22, e0.y);
-        float pz = fmaf((float)(__float_as_int(e2.w) - T.cg[2]), T.s22, e0.z);
-        S.tP[lane] = make_float4(px, py, pz, e0.w);
-        if (QUAD) {
-            S.tA[lane] = P.E1[id];
-            S.tB[lane] = e2.x;
+        if ((unsigned)id < (unsigned)P.nn) {
+            float4 e0 = P.E0[id];
+            float4 e2 = P.E2[id];
+            float px = fmaf((float)(__float_as_int(e2.y) - T.cg[0]), T.s22, e0.x);
+            float py = fmaf((float)(__float_as_int(e2.z) - T.cg[1]), T.s22, e0.y);
+            float pz = fmaf((float)(__float_as_int(e2.w) - T.cg[2]), T.s22, e0.z);
+            S.tP[lane] = make_float4(px, py, pz, e0.w);
+            if (QUAD) {
+                S.tA[lane] = P.E1[id];
+                S.tB[lane] = e2.x;
+            }
+        } else { // not a node (a corrupt list): massless and far, no gradient
+            atomicOr(P.status, ST_ETIMEOUT);
+            id = -1;
+            S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f);
+            if (QUAD) {
+                S.tA[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                S.tB[lane] = 0.f;
+            }
         }
         if (NODEID) S.tN[lane] = id;
     }
     __syncwarp();
 }
 
-__device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int cnt, int &qh, int &qoff, const Tgt &T,
+template <class SM>
+__device__ __forceinline__ void stage_p2p(const WalkParams &P, SM &S, int cnt, int &qh, int &qoff, const Tgt &T,
                                           int lane)
 {
     int j = -1, filled = 0;
@@ -576,16 +598,22 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int 
         if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
         if (lane >= filled) j = -1;
     }
-    if (lane < cnt && j >= 0) {
-        float4 a = P.pw[j];
-        int4 b = P.pc[j];
-        float px = fmaf((float)(b.x - T.cg[0]), T.s22, a.x);
-        float py = fmaf((float)(b.y - T.cg[1]), T.s22, a.y);
-        float pz = fmaf((float)(b.z - T.cg[2]), T.s22, a.z);
-        S.tP[lane] = make_float4(px, py, pz, a.w);
-        float h = __int_as_float(b.w); // negative for a sink
-        float ha = fabsf(h);
-        S.tA[lane] = make_float4(ha, 1.f / ha, __int_as_float(j), h < 0.f ? 1.f : 0.f);
+    if (lane < cnt) {
+        if (j >= 0 && j < P.npart) {
+            float4 a = P.pw[j];
+            int4 b = P.pc[j];
+            float px = fmaf((float)(b.x - T.cg[0]), T.s22, a.x);
+            float py = fmaf((float)(b.y - T.cg[1]), T.s22, a.y);
+            float pz = fmaf((float)(b.z - T.cg[2]), T.s22, a.z);
+            S.tP[lane] = make_float4(px, py, pz, a.w);
+            float h = __int_as_float(b.w); // negative for a sink
+            float ha = fabsf(h);
+            S.tA[lane] = make_float4(ha, 1.f / ha, __int_as_float(j), h < 0.f ? 1.f : 0.f);
+        } else { // the ring ran dry or a corrupt range: massless and far, no gradient
+            atomicOr(P.status, ST_ETIMEOUT);
+            S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f);
+            S.tA[lane] = make_float4(1.f, 1.f, __int_as_float(-1), 0.f);
+        }
     }
     __syncwarp();
 }
@@ -597,9 +625,10 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, WarpSmem &S, int 
 // leaves would all be opened); op = open (push its children).  link/cnt:
 // child range (op) or particle range (lf).
 __device__ __forceinline__ void test_node(const WalkParams &P, int node, const int glo[3], const int ghi[3],
-                                          unsigned long long hq, bool &acc, bool &lf, bool &op, int &link, int &cnt)
+                                          unsigned long long hq, bool &acc, bool &lf, bool &op, bool &nw, int &link,
+                                          int &cnt)
 {
-    acc = lf = op = false;
+    acc = lf = op = nw = false;
     link = cnt = 0;
     if (node < 0) return;
     int4 w0 = P.W0[node], w1 = P.W1[node], w2 = P.W2[node];
@@ -620,6 +649,9 @@ __device__ __forceinline__ void test_node(const WalkParams &P, int node, const i
     acc = sc >= P.T[level] && sb >= need;
     lf = !acc && leaf;
     op = !acc && !leaf;
+    // an opened leaf that passes clause (ii): every pair it contributes is
+    // beyond both softening supports (Newtonian)
+    nw = lf && sb >= need;
     link = w1.w;
     cnt = w2.w;
     if (op) {
@@ -643,7 +675,9 @@ __device__ __forceinline__ void test_node(const WalkParams &P, int node, const i
 // Walk state of one warp for one group.
 struct WalkState {
     int sp, nm, qh, qt, qoff, qn, tile;
-    int tot_m, tot_p, tot_leaf;
+    int tot_m, tot_p, tot_leaf, tot_ln, tot_pn; // tot_ln / tot_pn: the Newtonian part of tot_leaf / tot_p
+    long long off_s, off_n;                     // stored-list cursors of the softened / Newtonian ranges
+    long long lim_m, lim_s, lim_n;              // ends of the group's stored-list regions
     float ax, ay, az;
     double phi;
     double dax, day, daz;
@@ -654,7 +688,7 @@ struct WalkState {
 // Append accepted nodes (acc) and P2P ranges (lf) of this round to the lists.
 template <int MODE>
 __device__ __forceinline__ void append_lists(const WalkParams &P, WarpSmem &S, WalkState &W, int node, bool acc,
-                                             bool lf, int link, int cnt, unsigned lt)
+                                             bool lf, bool nw, int link, int cnt, unsigned lt)
 {
     unsigned ba = __ballot_sync(FULL, acc);
     unsigned bl = __ballot_sync(FULL, lf);
@@ -662,13 +696,28 @@ __device__ __forceinline__ void append_lists(const WalkParams &P, WarpSmem &S, W
     W.tot_m += __popc(ba);
     W.tot_leaf += __popc(bl);
     W.tot_p += lc;
-    if (MODE == MODE_COUNT || MODE == MODE_DUMP) {
-        if (MODE == MODE_DUMP) {
-            if (acc) P.dbg_m[W.off_m + __popc(ba & lt)] = node;
-            if (lf) P.dbg_p[W.off_p + __popc(bl & lt)] = node;
+    if (MODE == MODE_COUNT || MODE == MODE_LIST) {
+        unsigned bn = __ballot_sync(FULL, nw);
+        W.tot_ln += __popc(bn);
+        W.tot_pn += __reduce_add_sync(FULL, nw ? cnt : 0);
+        if (MODE == MODE_LIST) {
+            // writes stay inside the group's regions sized by the counting walk
+            unsigned bs = bl & ~bn;
+            long long im = W.off_m + __popc(ba & lt), is = W.off_s + __popc(bs & lt), in = W.off_n + __popc(bn & lt);
+            if (acc && im < W.lim_m) P.lm[im] = node;
+            if (lf && !nw && is < W.lim_s) P.lr[is] = make_int2(link, cnt);
+            if (nw && in < W.lim_n) P.lr[in] = make_int2(link, cnt);
             W.off_m += __popc(ba);
-            W.off_p += __popc(bl);
+            W.off_s += __popc(bs);
+            W.off_n += __popc(bn);
         }
+        return;
+    }
+    if (MODE == MODE_DUMP) {
+        if (acc) P.dbg_m[W.off_m + __popc(ba & lt)] = node;
+        if (lf) P.dbg_p[W.off_p + __popc(bl & lt)] = node;
+        W.off_m += __popc(ba);
+        W.off_p += __popc(bl);
         return;
     }
     if (acc) S.p2m[W.nm + __popc(ba & lt)] = node;
@@ -680,7 +729,8 @@ __device__ __forceinline__ void append_lists(const WalkParams &P, WarpSmem &S, W
 }
 
 // Advance the P2P range queue by cnt particles without staging them.
-__device__ __forceinline__ void skip_p2p(const WarpSmem &S, int cnt, int &qh, int &qoff)
+template <class SM>
+__device__ __forceinline__ void skip_p2p(const SM &S, int cnt, int &qh, int &qoff)
 {
     int done = 0;
     for (int it = 0; done < cnt && it < 66; it++) {
@@ -702,7 +752,7 @@ template <bool QUAD, int MODE>
 __device__ __forceinline__ void flush_tiles(const WalkParams &P, WarpSmem &S, WalkState &W, const Tgt &T, int lane,
                                             bool final, int kk, int K)
 {
-    if (MODE == MODE_COUNT || MODE == MODE_DUMP) return;
+    if (MODE == MODE_COUNT || MODE == MODE_DUMP || MODE == MODE_LIST) return;
     const int lim = final ? 1 : 32;
     while (MODE == MODE_EVAL64 && W.nm >= lim) {
         int c = min(W.nm, 32);
@@ -772,15 +822,15 @@ __device__ __forceinline__ void walk_group(const WalkParams &P, WarpSmem &S, int
     if (P.ctime && lane == 0) atomicMax(&P.ctime[cloud], global_ns());
 }
 
-template <bool QUAD, int MODE, bool GSTACK>
-__device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item,
-                                int lane, int &cloud_out)
+// Targets of group g on the lanes (see Tgt), the group's integer box, its
+// largest hq and its cloud.
+template <bool F64>
+__device__ __forceinline__ void setup_group(const WalkParams &P, int g, int lane, Tgt &T, int glo[3], int ghi[3],
+                                            unsigned long long &hq, int &cloud, int &tfirst, int &tcount)
 {
-    const unsigned lt = (1u << lane) - 1u;
-    const int cap = GSTACK ? GSTK : STK;
     const int2 gt = P.gtab[g];
-    const int tfirst = gt.x, tcount = gt.y;
-    Tgt T;
+    tfirst = gt.x;
+    tcount = gt.y;
     T.tp = 1;
     while (T.tp < tcount) T.tp <<= 1;
     T.R = 32 / T.tp;
@@ -789,12 +839,11 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
     T.has = T.tl < tcount;
     T.r = T.has ? P.tgt[tfirst + T.tl] : -1;
     // the group's cloud: its frame, and its root (node id = cloud id)
-    const int cloud = P.pcloud ? P.pcloud[P.tgt[tfirst]] : 0;
-    cloud_out = cloud;
+    cloud = P.pcloud ? P.pcloud[P.tgt[tfirst]] : 0;
     const Frame fr = P.frames[cloud];
     T.s22 = (float)fr.half_cell;
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
-    unsigned long long hq = 0;
+    hq = 0;
     double xd[3] = {0, 0, 0};
     T.h = 1.f;
     T.sink = false;
@@ -810,12 +859,11 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
         T.sink = P.sink_s[T.r] != 0;
     }
     T.hinv = 1.f / T.h;
-    if (MODE == MODE_EVAL64) {
+    if (F64) {
         for (int a = 0; a < 3; a++) T.x64[a] = xd[a];
         T.h64 = T.has ? P.soft_s[T.r] : 1.0;
         T.hinv64 = 1.0 / T.h64;
     }
-    int glo[3], ghi[3];
     for (int a = 0; a < 3; a++) {
         glo[a] = (int)__reduce_min_sync(FULL, lo[a]);
         ghi[a] = (int)__reduce_max_sync(FULL, hi[a]);
@@ -825,116 +873,24 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
         unsigned long long t = __shfl_xor_sync(FULL, hq, o);
         hq = t > hq ? t : hq;
     }
-    {
-        double c0 = fr.x0[0] + (double)T.cg[0] * fr.half_cell;
-        double c1 = fr.x0[1] + (double)T.cg[1] * fr.half_cell;
-        double c2 = fr.x0[2] + (double)T.cg[2] * fr.half_cell;
-        T.ox = (float)(xd[0] - c0);
-        T.oy = (float)(xd[1] - c1);
-        T.oz = (float)(xd[2] - c2);
-    }
-    WalkState W;
-    W.sp = W.nm = W.qh = W.qt = W.qoff = W.qn = W.tile = 0;
-    W.tot_m = W.tot_p = W.tot_leaf = 0;
-    W.ax = W.ay = W.az = 0.f;
-    W.phi = 0.0;
-    W.dax = W.day = W.daz = 0.0;
-    W.c0 = W.c1 = W.c2 = W.cf = 0.f;
-    W.off_m = W.off_p = 0;
-    if (MODE == MODE_VJP && T.has) {
-        float4 cv = P.cot[tfirst + T.tl];
-        W.c0 = cv.x;
-        W.c1 = cv.y;
-        W.c2 = cv.z;
-        W.cf = cv.w;
-    }
-    if (MODE == MODE_DUMP) {
-        W.off_m = P.dbg_off[2 * g];
-        W.off_p = P.dbg_off[2 * g + 1];
-    }
+    double c0 = fr.x0[0] + (double)T.cg[0] * fr.half_cell;
+    double c1 = fr.x0[1] + (double)T.cg[1] * fr.half_cell;
+    double c2 = fr.x0[2] + (double)T.cg[2] * fr.half_cell;
+    T.ox = (float)(xd[0] - c0);
+    T.oy = (float)(xd[1] - c1);
+    T.oz = (float)(xd[2] - c2);
+}
 
-    if (lane == 0) stack[0] = make_int2(cloud, 1);
-    W.sp = 1;
-    __syncwarp();
-
-    bool overflow = false;
-    // every node is visited at most once per group, so nn + 1 rounds bound the walk
-    int rounds = 0;
-    const int max_rounds = P.nn + 1;
-    while (W.sp > 0) {
-        if (++rounds > max_rounds) {
-            if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
-            break;
-        }
-        int node = -1;
-        int taken = 0;
-        while (taken < 32 && W.sp > 0) {
-            int2 top = stack[W.sp - 1];
-            int take = min(32 - taken, top.y);
-            if (lane >= taken && lane < taken + take) node = top.x + (top.y - take) + (lane - taken);
-            taken += take;
-            __syncwarp();
-            if (take == top.y) W.sp--;
-            else if (lane == 0) stack[W.sp - 1].y = top.y - take;
-            __syncwarp();
-        }
-        bool acc, lf, op;
-        int link, cnt;
-        test_node(P, node, glo, ghi, hq, acc, lf, op, link, cnt);
-        unsigned bo = __ballot_sync(FULL, op);
-        int npush = __popc(bo);
-        if (W.sp + npush > cap) {
-            overflow = true;
-            break;
-        }
-        if (op) stack[W.sp + __popc(bo & lt)] = make_int2(link, cnt);
-        W.sp += npush;
-        append_lists<MODE>(P, S, W, node, acc, lf, link, cnt, lt);
-        flush_tiles<QUAD, MODE>(P, S, W, T, lane, false, kk, K);
-    }
-    if (overflow) {
-        if (GSTACK) {
-            if (lane == 0) atomicOr(P.status, ST_EOVERFLOW);
-        } else if (lane == 0) {
-            unsigned long long idx = atomicAdd(&P.counters[2], 1ull);
-            P.ovf_list[idx] = item;
-        }
-        __syncwarp();
-        return;
-    }
-    if (MODE == MODE_COUNT) {
-        if (lane == 0) {
-            P.dbg_counts[3 * g] = W.tot_m;
-            P.dbg_counts[3 * g + 1] = W.tot_leaf;
-            P.dbg_counts[3 * g + 2] = W.tot_p;
-        }
-        return;
-    }
-    if (MODE == MODE_DUMP) return;
-    flush_tiles<QUAD, MODE>(P, S, W, T, lane, true, kk, K);
-    if (MODE == MODE_EVAL64) {
-        double dax = W.dax, day = W.day, daz = W.daz, dph = W.phi;
-        for (int o = T.tp; o < 32; o <<= 1) {
-            dax += __shfl_xor_sync(FULL, dax, o);
-            day += __shfl_xor_sync(FULL, day, o);
-            daz += __shfl_xor_sync(FULL, daz, o);
-            dph += __shfl_xor_sync(FULL, dph, o);
-        }
-        if (T.has && T.slice == 0) {
-            double *dst = P.res64 + 4 * (size_t)(tfirst + T.tl);
-            atomicAdd(dst, dax);
-            atomicAdd(dst + 1, day);
-            atomicAdd(dst + 2, daz);
-            atomicAdd(dst + 3, dph);
-        }
-        if (lane == 0 && kk == 0) {
-            atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(W.tot_p - 1));
-            atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)W.tot_m);
-        }
-        return;
-    }
-    float ax = W.ax, ay = W.ay, az = W.az;
-    double phi = W.phi;
+// Per-target results of one work item (item kk of K of group g): the
+// forward field (whole, or a partial sum that the group's last item adds up
+// in item order) or the target side of the adjoint; the interaction counts
+// once per group.  n_src_p: P2P particles of the group's list (its own
+// target included), n_src_m: P2M nodes.
+template <int MODE>
+__device__ __forceinline__ void finish_targets(const WalkParams &P, const Tgt &T, int g, int kk, int K, int tfirst,
+                                               int tcount, float ax, float ay, float az, double phi, int n_src_p,
+                                               int n_src_m, int lane)
+{
     for (int o = T.tp; o < 32; o <<= 1) {
         ax += __shfl_xor_sync(FULL, ax, o);
         ay += __shfl_xor_sync(FULL, ay, o);
@@ -986,10 +942,501 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
         }
     }
     if (lane == 0 && kk == 0) {
-        // every item walks the whole list: count it once (self pairs excluded)
-        atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(W.tot_p - 1));
-        atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)W.tot_m);
+        // count the group's list once (self pairs excluded)
+        atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(n_src_p - 1));
+        atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)n_src_m);
     }
+}
+
+template <bool QUAD, int MODE, bool GSTACK>
+__device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item,
+                                int lane, int &cloud_out)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const int cap = GSTACK ? GSTK : STK;
+    Tgt T;
+    int glo[3], ghi[3], cloud, tfirst, tcount;
+    unsigned long long hq;
+    setup_group<MODE == MODE_EVAL64>(P, g, lane, T, glo, ghi, hq, cloud, tfirst, tcount);
+    cloud_out = cloud;
+    WalkState W;
+    W.sp = W.nm = W.qh = W.qt = W.qoff = W.qn = W.tile = 0;
+    W.tot_m = W.tot_p = W.tot_leaf = W.tot_ln = W.tot_pn = 0;
+    W.off_s = W.off_n = 0;
+    W.ax = W.ay = W.az = 0.f;
+    W.phi = 0.0;
+    W.dax = W.day = W.daz = 0.0;
+    W.c0 = W.c1 = W.c2 = W.cf = 0.f;
+    W.off_m = W.off_p = 0;
+    if (MODE == MODE_VJP && T.has) {
+        float4 cv = P.cot[tfirst + T.tl];
+        W.c0 = cv.x;
+        W.c1 = cv.y;
+        W.c2 = cv.z;
+        W.cf = cv.w;
+    }
+    if (MODE == MODE_DUMP) {
+        W.off_m = P.dbg_off[2 * g];
+        W.off_p = P.dbg_off[2 * g + 1];
+    }
+    W.lim_m = W.lim_s = W.lim_n = 0;
+    if (MODE == MODE_LIST) {
+        const int *c = P.lcnt + NCNT * (size_t)g;
+        W.off_m = P.lmo[g];
+        W.off_s = P.lro[g];
+        W.off_n = P.lro[g] + c[1];
+        W.lim_m = W.off_m + c[0];
+        W.lim_s = W.off_n;
+        W.lim_n = W.off_n + c[3];
+    }
+
+    if (lane == 0) stack[0] = make_int2(cloud, 1);
+    W.sp = 1;
+    __syncwarp();
+
+    bool overflow = false;
+    // every node is visited at most once per group, so nn + 1 rounds bound the walk
+    int rounds = 0;
+    const int max_rounds = P.nn + 1;
+    while (W.sp > 0) {
+        if (++rounds > max_rounds) {
+            if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
+            break;
+        }
+        int node = -1;
+        int taken = 0;
+        while (taken < 32 && W.sp > 0) {
+            int2 top = stack[W.sp - 1];
+            int take = min(32 - taken, top.y);
+            if (lane >= taken && lane < taken + take) node = top.x + (top.y - take) + (lane - taken);
+            taken += take;
+            __syncwarp();
+            if (take == top.y) W.sp--;
+            else if (lane == 0) stack[W.sp - 1].y = top.y - take;
+            __syncwarp();
+        }
+        bool acc, lf, op, nw;
+        int link, cnt;
+        test_node(P, node, glo, ghi, hq, acc, lf, op, nw, link, cnt);
+        unsigned bo = __ballot_sync(FULL, op);
+        int npush = __popc(bo);
+        if (W.sp + npush > cap) {
+            overflow = true;
+            break;
+        }
+        if (op) stack[W.sp + __popc(bo & lt)] = make_int2(link, cnt);
+        W.sp += npush;
+        append_lists<MODE>(P, S, W, node, acc, lf, nw, link, cnt, lt);
+        flush_tiles<QUAD, MODE>(P, S, W, T, lane, false, kk, K);
+    }
+    if (overflow) {
+        if (GSTACK) {
+            if (lane == 0) atomicOr(P.status, ST_EOVERFLOW);
+        } else if (lane == 0) {
+            unsigned long long idx = atomicAdd(&P.counters[2], 1ull);
+            P.ovf_list[idx] = item;
+        }
+        __syncwarp();
+        return;
+    }
+    if (MODE == MODE_COUNT) {
+        if (lane == 0) {
+            int *c = P.dbg_counts + NCNT * (size_t)g;
+            c[0] = W.tot_m;
+            c[1] = W.tot_leaf - W.tot_ln;
+            c[2] = W.tot_p - W.tot_pn;
+            c[3] = W.tot_ln;
+            c[4] = W.tot_pn;
+        }
+        return;
+    }
+    if (MODE == MODE_DUMP || MODE == MODE_LIST) return;
+    flush_tiles<QUAD, MODE>(P, S, W, T, lane, true, kk, K);
+    if (MODE == MODE_EVAL64) {
+        double dax = W.dax, day = W.day, daz = W.daz, dph = W.phi;
+        for (int o = T.tp; o < 32; o <<= 1) {
+            dax += __shfl_xor_sync(FULL, dax, o);
+            day += __shfl_xor_sync(FULL, day, o);
+            daz += __shfl_xor_sync(FULL, daz, o);
+            dph += __shfl_xor_sync(FULL, dph, o);
+        }
+        if (T.has && T.slice == 0) {
+            double *dst = P.res64 + 4 * (size_t)(tfirst + T.tl);
+            atomicAdd(dst, dax);
+            atomicAdd(dst + 1, day);
+            atomicAdd(dst + 2, daz);
+            atomicAdd(dst + 3, dph);
+        }
+        if (lane == 0 && kk == 0) {
+            atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(W.tot_p - 1));
+            atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)W.tot_m);
+        }
+        return;
+    }
+    finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, W.ax, W.ay, W.az, W.phi, W.tot_p, W.tot_m, lane);
+}
+
+// ------------------------------------------------ stored-list evaluation ----
+// The forward and the adjoint evaluate groups from the lists of a prior
+// walk (MODE_LIST): P2M node ids, softened P2P particle ranges, Newtonian
+// P2P ranges (opened leaves that pass clause (ii), so none of their pairs
+// is inside either softening support and none is a self pair).  Item kk of
+// K takes a contiguous share of each list's tiles.
+struct EvalSmem {
+    int2 leafq[64]; // ring of P2P ranges being staged
+    float4 tP[32];
+    float4 tA[32];
+    float tB[32];
+    int tN[32];
+};
+
+constexpr int EVAL_WARPS = 4;
+constexpr int EVAL_MINB = 6;
+
+// Particle of this lane in the next cnt particles of the range ring (-1 if
+// the ring runs dry, which the callers rule out).
+template <class SM>
+__device__ __forceinline__ int ring_take(const WalkParams &P, const SM &S, int cnt, int &qh, int &qoff, int lane)
+{
+    int j = -1, filled = 0;
+    for (int it = 0; filled < cnt && it < 66; it++) {
+        int2 hr = S.leafq[qh & 63];
+        int take = min(hr.y - qoff, cnt - filled);
+        if (take < 0) take = 0;
+        if (lane >= filled && lane < filled + take) j = hr.x + qoff + (lane - filled);
+        filled += take;
+        qoff += take;
+        if (qoff >= hr.y) {
+            qh++;
+            qoff = 0;
+        }
+    }
+    if (filled < cnt) {
+        if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
+        if (lane >= filled) j = -1;
+    }
+    return j;
+}
+
+// Newtonian tile: positions and masses only (and the particle id for the adjoint).
+template <class SM>
+__device__ __forceinline__ void stage_p2p_newt(const WalkParams &P, SM &S, int cnt, int &qh, int &qoff, const Tgt &T,
+                                               int lane)
+{
+    int j = ring_take(P, S, cnt, qh, qoff, lane);
+    if (lane < cnt && (j < 0 || j >= P.npart)) { // a corrupt range: skipped, status set
+        atomicOr(P.status, ST_ETIMEOUT);
+        j = -1;
+    }
+    if (lane < cnt) {
+        if (j >= 0) {
+            float4 a = P.pw[j];
+            int4 b = P.pc[j];
+            float px = fmaf((float)(b.x - T.cg[0]), T.s22, a.x);
+            float py = fmaf((float)(b.y - T.cg[1]), T.s22, a.y);
+            float pz = fmaf((float)(b.z - T.cg[2]), T.s22, a.z);
+            S.tP[lane] = make_float4(px, py, pz, a.w);
+            S.tN[lane] = j;
+        } else {
+            S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f); // massless and far: no contribution
+            S.tN[lane] = -1;
+        }
+    }
+    __syncwarp();
+}
+
+template <class SM>
+__device__ __forceinline__ void fwd_p2p_newt(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+                                             double &phi)
+{
+    float pt = 0.f;
+#pragma unroll 2
+    for (int k = T.slice; k < cnt; k += T.R) {
+        float4 p = S.tP[k];
+        float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float rinv = rsqrtf(r2);
+        float mr = p.w * rinv;
+        float mr3 = mr * (rinv * rinv);
+        ax = fmaf(mr3, dx, ax);
+        ay = fmaf(mr3, dy, ay);
+        az = fmaf(mr3, dz, az);
+        pt -= mr;
+    }
+    phi += (double)pt;
+}
+
+// Adjoint of a Newtonian tile: the systolic source-side sums of vjp_p2p with
+// the Newtonian kernel only.
+template <class SM>
+__device__ __forceinline__ void vjp_p2p_newt(const WalkParams &P, const SM &S, int cnt, const Tgt &T, float c0,
+                                             float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
+{
+    const int tp = T.tp, base = T.slice * tp;
+    const int nxt = (T.tl + 1) & (tp - 1);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, am = 0.f;
+    for (int jj = 0; jj < tp; jj++) {
+        const int k = base + ((T.tl + jj) & (tp - 1));
+        if (T.has && k < cnt) {
+            float4 p = S.tP[k];
+            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float rinv = rsqrtf(r2);
+            float ri2 = rinv * rinv;
+            float K = ri2 * rinv;
+            float R = -3.f * K * ri2;
+            float m = p.w;
+            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
+            float mK = m * K;
+            float sv = m * fmaf(R, cd, cf * K);
+            float l0 = fmaf(mK, c0, sv * dx);
+            float l1 = fmaf(mK, c1, sv * dy);
+            float l2 = fmaf(mK, c2, sv * dz);
+            a0 += l0;
+            a1 += l1;
+            a2 += l2;
+            am += fmaf(K, cd, -rinv * cf);
+            gx -= l0;
+            gy -= l1;
+            gz -= l2;
+        }
+        a0 = __shfl_sync(FULL, a0, nxt, tp);
+        a1 = __shfl_sync(FULL, a1, nxt, tp);
+        a2 = __shfl_sync(FULL, a2, nxt, tp);
+        am = __shfl_sync(FULL, am, nxt, tp);
+    }
+    const int k = base + T.tl;
+    if (k < cnt && S.tN[k] >= 0) {
+        double *dst = P.gpart + 4 * (size_t)S.tN[k];
+        if (a0 != 0.f) atomicAdd(dst, (double)a0);
+        if (a1 != 0.f) atomicAdd(dst + 1, (double)a1);
+        if (a2 != 0.f) atomicAdd(dst + 2, (double)a2);
+        if (am != 0.f) atomicAdd(dst + 3, (double)am);
+    }
+}
+
+// This item's share of one P2P list: nr ranges holding np particles.
+template <int MODE, bool NEWT>
+__device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, const Tgt &T, const int2 *rr, int nr,
+                                              int np, int kk, int K, float c0, float c1, float c2, float cf,
+                                              float &ax, float &ay, float &az, double &phi, int lane)
+{
+    const int nt = (np + 31) >> 5;
+    const int t0 = (int)((long long)nt * kk / K), t1 = (int)((long long)nt * (kk + 1) / K);
+    if (t0 >= t1) return;
+    const int pb = t0 * 32, pe = min(np, t1 * 32);
+    // find the range holding particle pb: 32 ranges at a time, warp prefix sums of their sizes
+    int r = -1, qoff = 0, before = 0;
+    for (int base = 0; base < nr; base += 32) {
+        const int idx = base + lane;
+        const int c = idx < nr ? rr[idx].y : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        unsigned hit = __ballot_sync(FULL, idx < nr && before + incl > pb);
+        if (hit) {
+            const int L = __ffs(hit) - 1;
+            r = base + L;
+            qoff = pb - (before + __shfl_sync(FULL, incl - c, L));
+            break;
+        }
+        before += __shfl_sync(FULL, incl, 31);
+    }
+    if (r < 0) { // the stored sizes disagree with the ranges
+        if (lane == 0) atomicOr(P.status, ST_ETIMEOUT);
+        return;
+    }
+    int qh = 0, qt = 0, rn = r;
+    for (int b = pb; b < pe; b += 32) {
+        const int c = min(32, pe - b);
+        // keep >= 32 ranges (or all that are left) queued: a tile spans at most 32
+        if (qt - qh < 32 && rn < nr) {
+            const int k = min(32, nr - rn);
+            if (lane < k) S.leafq[(qt + lane) & 63] = rr[rn + lane];
+            qt += k;
+            rn += k;
+            __syncwarp();
+        }
+        if (NEWT) {
+            stage_p2p_newt(P, S, c, qh, qoff, T, lane);
+            if (MODE == MODE_VJP) vjp_p2p_newt(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2p_newt(S, c, T, ax, ay, az, phi);
+        } else {
+            stage_p2p(P, S, c, qh, qoff, T, lane);
+            if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2p(S, c, T, ax, ay, az, phi);
+        }
+        __syncwarp();
+    }
+}
+
+template <bool QUAD, int MODE>
+__device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g, int kk, int K, int lane)
+{
+    Tgt T;
+    int glo[3], ghi[3], cloud, tfirst, tcount;
+    unsigned long long hq;
+    setup_group<false>(P, g, lane, T, glo, ghi, hq, cloud, tfirst, tcount);
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, cf = 0.f;
+    if (MODE == MODE_VJP && T.has) {
+        float4 cv = P.cot[tfirst + T.tl];
+        c0 = cv.x;
+        c1 = cv.y;
+        c2 = cv.z;
+        cf = cv.w;
+    }
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    double phi = 0.0;
+    const int *cn = P.lcnt + NCNT * (size_t)g;
+    const int nm = cn[0], nls = cn[1], nps = cn[2], nln = cn[3], npn = cn[4];
+    {
+        const int *lm = P.lm + P.lmo[g];
+        const int nt = (nm + 31) >> 5;
+        const int t0 = (int)((long long)nt * kk / K), t1 = (int)((long long)nt * (kk + 1) / K);
+        for (int tt = t0; tt < t1; tt++) {
+            const int b = tt * 32, c = min(32, nm - b);
+            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, lm + b, c, T, lane);
+            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (T.has) fwd_p2m<QUAD>(S, c, T, ax, ay, az, phi);
+            __syncwarp();
+        }
+    }
+    const int2 *lr = P.lr + P.lro[g];
+    eval_p2p_list<MODE, false>(P, S, T, lr, nls, nps, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
+    eval_p2p_list<MODE, true>(P, S, T, lr + nls, nln, npn, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
+    finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, ax, ay, az, phi, nps + npn, nm, lane);
+    return cloud;
+}
+
+// Persistent warps take work items (longest first) from an atomic counter.
+template <bool QUAD, int MODE>
+__global__ void __launch_bounds__(EVAL_WARPS * 32, EVAL_MINB) k_eval(WalkParams P)
+{
+    __shared__ EvalSmem sm[EVAL_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    EvalSmem &S = sm[w];
+    const int nwork = P.ioff[*P.d_ngroups];
+    if (P.ctime && lane == 0) atomicMin(&P.ctime[P.nclouds], global_ns());
+    while (true) {
+        int w_i = 0;
+        if (lane == 0) w_i = (int)atomicAdd(&P.counters[3], 1ull);
+        w_i = __shfl_sync(FULL, w_i, 0);
+        if (w_i >= nwork) break;
+        const int2 it = P.items[w_i];
+        const int cloud = eval_item<QUAD, MODE>(P, S, it.x, it.y, P.kcnt[it.x], lane);
+        if (P.ctime && lane == 0) atomicMax(&P.ctime[cloud], global_ns());
+    }
+}
+
+// Exclusive scans over the groups of the stored-list sizes: lmo (P2M
+// entries) and lro (P2P ranges), 64-bit; totals in lmo[ng], lro[ng] and tot[2].
+constexpr int LS_NB = 512;
+
+__device__ __forceinline__ long long block_sum64(long long v, long long *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int k = 0; k < nw; k++) t += sh[k];
+    return t;
+}
+
+__global__ void k_lscan_reduce(const int *cnt, const int *d_ng, long long *bsum)
+{
+    __shared__ long long sh[32];
+    const int ng = *d_ng;
+    const int chunk = (ng + LS_NB - 1) / LS_NB;
+    const int b0 = min(ng, (int)blockIdx.x * chunk), b1 = min(ng, b0 + chunk);
+    long long sm = 0, sr = 0;
+    for (int g = b0 + threadIdx.x; g < b1; g += blockDim.x) {
+        const int *c = cnt + NCNT * (size_t)g;
+        sm += c[0];
+        sr += c[1] + c[3];
+    }
+    sm = block_sum64(sm, sh);
+    sr = block_sum64(sr, sh);
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = sm;
+        bsum[LS_NB + blockIdx.x] = sr;
+    }
+}
+
+__global__ void k_lscan_top(long long *bsum, const int *d_ng, long long *lmo, long long *lro, long long *tot)
+{
+    if (threadIdx.x != 0) return;
+    long long rm = 0, rr = 0;
+    for (int b = 0; b < LS_NB; b++) {
+        long long m = bsum[b], r = bsum[LS_NB + b];
+        bsum[b] = rm;
+        bsum[LS_NB + b] = rr;
+        rm += m;
+        rr += r;
+    }
+    const int ng = *d_ng;
+    lmo[ng] = rm;
+    lro[ng] = rr;
+    tot[0] = rm;
+    tot[1] = rr;
+}
+
+__global__ void k_lscan_down(const int *cnt, const int *d_ng, const long long *bsum, long long *lmo, long long *lro)
+{
+    __shared__ long long shm[32], shr[32];
+    const int ng = *d_ng;
+    const int chunk = (ng + LS_NB - 1) / LS_NB;
+    const int b0 = min(ng, (int)blockIdx.x * chunk), b1 = min(ng, b0 + chunk);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long cm = bsum[blockIdx.x], cr = bsum[LS_NB + blockIdx.x];
+    for (int base = b0; base < b1; base += blockDim.x) {
+        const int g = base + threadIdx.x;
+        long long vm = 0, vr = 0;
+        if (g < b1) {
+            const int *c = cnt + NCNT * (size_t)g;
+            vm = c[0];
+            vr = c[1] + c[3];
+        }
+        long long im = vm, ir = vr;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long tm = __shfl_up_sync(FULL, im, o), tr = __shfl_up_sync(FULL, ir, o);
+            if (lane >= o) {
+                im += tm;
+                ir += tr;
+            }
+        }
+        __syncthreads();
+        if (lane == 31) {
+            shm[w] = im;
+            shr[w] = ir;
+        }
+        __syncthreads();
+        long long pm = 0, pr = 0, tm = 0, tr = 0;
+        for (int k = 0; k < nw; k++) {
+            if (k < w) {
+                pm += shm[k];
+                pr += shr[k];
+            }
+            tm += shm[k];
+            tr += shr[k];
+        }
+        if (g < b1) {
+            lmo[g] = cm + pm + im - vm;
+            lro[g] = cr + pr + ir - vr;
+        }
+        cm += tm;
+        cr += tr;
+    }
+}
+
+// flag = 1 if a[0..n) != b[0..n)
+__global__ void k_cmp_idx(const int64_t *a, const int64_t *b, int64_t n, int *flag)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (a[k] != b[k]) *flag = 1;
 }
 
 template <bool QUAD, int MODE, bool GSTACK>
@@ -1027,21 +1474,22 @@ constexpr int SPLIT_ITERS = 4096;
 constexpr int KMAX = 32;
 constexpr int PSLOTS = 65536;
 
-__device__ inline long long group_iters(const int *cnt3, int tc, int g)
+__device__ inline long long group_iters(const int *cnt, int tc, int g)
 {
     int tp = 1;
     while (tp < tc) tp <<= 1;
-    long long src = (long long)cnt3[3 * g] + cnt3[3 * g + 2];
-    return src * tp / 32 + ((long long)cnt3[3 * g] + cnt3[3 * g + 1]) / 4 + 32;
+    const int *c = cnt + NCNT * (size_t)g;
+    long long src = (long long)c[0] + c[2] + c[4];
+    return src * tp / 32 + ((long long)c[0] + c[1] + c[3]) / 4 + 32;
 }
 
 // Total estimated cost of all groups (one 64-bit atomic per warp).
-__global__ void k_item_total(const int *cnt3, const int2 *gtab, const int *d_ngroups, unsigned long long *total)
+__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, unsigned long long *total)
 {
     int ng = *d_ngroups;
     unsigned long long acc = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        acc += (unsigned long long)group_iters(cnt3, gtab[g].y, g);
+        acc += (unsigned long long)group_iters(cnt, gtab[g].y, g);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
 }
@@ -1050,14 +1498,14 @@ __global__ void k_item_total(const int *cnt3, const int2 *gtab, const int *d_ngr
 // warp's share of the total, so the split groups need at most ~6 slots per
 // resident warp (the slot pool holds PSLOTS) and every item stays small next
 // to a warp's share (longest-first scheduling then balances the rest).
-__global__ void k_item_counts(const int *cnt3, const int2 *gtab, const int *d_ngroups,
+__global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngroups,
                               const unsigned long long *total, long long warps, int *kcnt, int *is_split)
 {
     int ng = *d_ngroups;
     long long C = (long long)(*total / (unsigned long long)(3 * warps));
     if (C < SPLIT_ITERS) C = SPLIT_ITERS;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        long long iters = group_iters(cnt3, gtab[g].y, g);
+        long long iters = group_iters(cnt, gtab[g].y, g);
         long long k = (iters + C - 1) / C;
         int K = (int)(k < 1 ? 1 : (k > KMAX ? KMAX : k));
         kcnt[g] = K;
@@ -1067,18 +1515,18 @@ __global__ void k_item_counts(const int *cnt3, const int2 *gtab, const int *d_ng
 
 // Longest first: items are bucketed by log2 of their estimated cost and the
 // buckets are issued from the most to the least expensive.
-__device__ inline int cost_bucket(const int *cnt3, const int2 *gtab, const int *kcnt, int g)
+__device__ inline int cost_bucket(const int *cnt, const int2 *gtab, const int *kcnt, int g)
 {
-    long long c = group_iters(cnt3, gtab[g].y, g) / kcnt[g];
+    long long c = group_iters(cnt, gtab[g].y, g) / kcnt[g];
     int b = 63 - __clzll(c > 1 ? c : 1);
     return 31 - min(b, 31);
 }
 
-__global__ void k_item_hist(const int *cnt3, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *hist)
+__global__ void k_item_hist(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *hist)
 {
     int ng = *d_ngroups;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        atomicAdd(&hist[cost_bucket(cnt3, gtab, kcnt, g)], kcnt[g]);
+        atomicAdd(&hist[cost_bucket(cnt, gtab, kcnt, g)], kcnt[g]);
 }
 
 __global__ void k_item_scan(int *hist)
@@ -1093,13 +1541,13 @@ __global__ void k_item_scan(int *hist)
     }
 }
 
-__global__ void k_item_fill(const int *cnt3, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *cursor,
+__global__ void k_item_fill(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *cursor,
                             int2 *items)
 {
     int ng = *d_ngroups;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         int K = kcnt[g];
-        int base = atomicAdd(&cursor[cost_bucket(cnt3, gtab, kcnt, g)], K);
+        int base = atomicAdd(&cursor[cost_bucket(cnt, gtab, kcnt, g)], K);
         for (int k = 0; k < K; k++) items[base + k] = make_int2(g, k);
     }
 }
@@ -1233,7 +1681,8 @@ struct Work {
     float4 *res_a;
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
-    int *cnt3, *kcnt, *is_split, *soff, *ioff, *gdone, *hist;
+    int *cnt, *kcnt, *is_split, *soff, *ioff, *gdone, *hist; // cnt: NCNT list sizes per group
+    long long *lmo, *lro; // stored lists: first P2M entry / first P2P range of every group (exclusive scans)
     int2 *items;
     float4 *part_a;
     double *part_phi;
@@ -1245,14 +1694,16 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
 {
     const size_t n = (size_t)t->n;
     const int retry_warps = num_sms() * WALK_WARPS;
-    const size_t NB = 22;
+    const size_t NB = 24;
     size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, (n + PSLOTS) * 4, scan_scratch_bytes(),
                      n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8,
-                     n * 12, n * 4, n * 4, (n + 1) * 4, (n + 1) * 4, n * 4,
-                     (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8, 64 * 4, (n + PSLOTS) * 8};
+                     n * 4 * NCNT, n * 4, n * 4, (n + 1) * 4, (n + 1) * 4, n * 4,
+                     (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8, 64 * 4, (n + PSLOTS) * 8,
+                     (n + 1) * 8, (n + 1) * 8};
     size_t total = 0;
     for (size_t b : sz) total += align_up(b);
     if (t->ws_bytes < total) {
+        t->lists_ok = false; // the list sizes lived in the old workspace
         if (t->ws) dev_free(t, t->ws, s);
         t->ws = dev_alloc(t, total, s);
         if (!t->ws) {
@@ -1279,7 +1730,7 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     w.gstack = (int2 *)ptr[9];
     w.res_a = (float4 *)ptr[10];
     w.res_phi = (double *)ptr[11];
-    w.cnt3 = (int *)ptr[12];
+    w.cnt = (int *)ptr[12];
     w.kcnt = (int *)ptr[13];
     w.is_split = (int *)ptr[14];
     w.soff = (int *)ptr[15];
@@ -1289,6 +1740,8 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     w.part_phi = (double *)ptr[19];
     w.hist = (int *)ptr[20];
     w.items = (int2 *)ptr[21];
+    w.lmo = (long long *)ptr[22];
+    w.lro = (long long *)ptr[23];
     return SFG_OK;
 }
 
@@ -1347,6 +1800,7 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.nclouds = t->nclouds;
     P.ctime = nullptr;
     P.nn = t->nn;
+    P.npart = (int)t->n;
     const double th = t->prm.theta;
     for (int l = 0; l <= SFG_LMAX; l++) {
         double v = ldexp(1.0, 2 * (SFG_LMAX - l)) / (th * th);
@@ -1367,6 +1821,11 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.cot = nullptr;
     P.gpart = nullptr;
     P.gnode = nullptr;
+    P.lcnt = w.cnt;
+    P.lmo = w.lmo;
+    P.lro = w.lro;
+    P.lm = t->lm;
+    P.lr = t->lr;
 }
 
 template <int MODE>
@@ -1434,28 +1893,144 @@ static int cloud_timer_begin(Tree *t, int which, cudaStream_t s, WalkParams &P)
 template <int MODE>
 static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s);
 
-static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+// List sizes of every group (a walk without evaluation).
+static void count_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+{
+    // a group whose walk gives up (status set) keeps empty lists
+    cudaMemsetAsync(w.cnt, 0, sizeof(int) * NCNT * (size_t)t->n, s);
+    P.dbg_counts = w.cnt;
+    launch_walk<MODE_COUNT>(t, P, s);
+    P.dbg_counts = nullptr;
+}
+
+// Cut the heavy groups into work items, from the list sizes.
+static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
 {
     const int n = (int)t->n, BT = 256;
     const int *d_ng = P.d_ngroups;
-    P.dbg_counts = w.cnt3;
-    launch_walk<MODE_COUNT>(t, P, s);
     cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s);
     unsigned long long *total = t->d_counters + 7;
     cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
-    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, d_ng, total);
+    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, total);
     const long long warps = (long long)num_sms() * WALK_MINB * WALK_WARPS;
-    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, d_ng, total, warps, w.kcnt, w.is_split);
+    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, total, warps, w.kcnt, w.is_split);
     scan_exclusive(w.is_split, w.soff, d_ng, n, nullptr, nullptr, w.scr, s);
     k_item_cap<<<grid_for(n, BT), BT, 0, s>>>(w.soff, d_ng, w.kcnt);
     scan_exclusive(w.kcnt, w.ioff, d_ng, n, nullptr, nullptr, w.scr, s);
     cudaMemsetAsync(w.gdone, 0, sizeof(int) * (size_t)n, s);
     cudaMemsetAsync(w.hist, 0, 32 * sizeof(int), s);
-    k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, w.kcnt, d_ng, w.hist);
+    k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, w.hist);
     k_item_scan<<<1, 32, 0, s>>>(w.hist);
-    k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt3, w.gtab, w.kcnt, d_ng, w.hist, w.items);
-    t->n_launch += 2 + 1 + 3 + 3 + 3;
-    P.dbg_counts = nullptr;
+    k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, w.hist, w.items);
+    t->n_launch += 1 + 3 + 3 + 3;
+}
+
+static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+{
+    count_lists(t, w, P, s);
+    items_from_counts(t, w, P, s);
+}
+
+// Stored lists are used unless disabled, in the all-FP64 mode, or while the
+// stream is captured into a CUDA graph (sizing them synchronizes).
+static bool use_lists(const Tree *t, cudaStream_t s)
+{
+    return t->prm.store_lists != 0 && t->prm.precision == 0 && !capturing(s);
+}
+
+static int grow_buffer(Tree *t, void **buf, long long *cap, long long need, size_t elem, cudaStream_t s)
+{
+    if (*buf && need <= *cap) return SFG_OK;
+    if (*buf) dev_free(t, *buf, s);
+    const long long c = need + need / 4 > 1024 ? need + need / 4 : 1024;
+    *buf = dev_alloc(t, elem * (size_t)c, s);
+    if (!*buf) {
+        *cap = 0;
+        return SFG_ENOMEM;
+    }
+    *cap = c;
+    return SFG_OK;
+}
+
+// Walk every group twice: count its lists, then write them (P2M node ids,
+// softened and Newtonian P2P ranges) into the tree's grow-only buffers,
+// sized from the counts after one synchronization.
+static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+{
+    t->lists_ok = false;
+    count_lists(t, w, P, s);
+    if (!t->d_lscan) {
+        t->d_lscan = (long long *)dev_alloc(t, sizeof(long long) * (2 * LS_NB + 2), s);
+        if (!t->d_lscan) return SFG_ENOMEM;
+    }
+    long long *tot_d = t->d_lscan + 2 * LS_NB;
+    k_lscan_reduce<<<LS_NB, 256, 0, s>>>(w.cnt, P.d_ngroups, t->d_lscan);
+    k_lscan_top<<<1, 32, 0, s>>>(t->d_lscan, P.d_ngroups, w.lmo, w.lro, tot_d);
+    k_lscan_down<<<LS_NB, 256, 0, s>>>(w.cnt, P.d_ngroups, t->d_lscan, w.lmo, w.lro);
+    t->n_launch += 3;
+    long long tot[2] = {0, 0};
+    SFG_CUDA_OK(cudaMemcpyAsync(tot, tot_d, sizeof(tot), cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
+    int rc = grow_buffer(t, (void **)&t->lm, &t->lm_cap, tot[0], sizeof(int), s);
+    if (rc) return rc;
+    rc = grow_buffer(t, (void **)&t->lr, &t->lr_cap, tot[1], sizeof(int2), s);
+    if (rc) return rc;
+    P.lm = t->lm;
+    P.lr = t->lr;
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
+    launch_walk<MODE_LIST>(t, P, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+// Record the active set the stored lists belong to.
+static int remember_active(Tree *t, const int64_t *active, int64_t n_active, cudaStream_t s)
+{
+    t->la_all = active == nullptr;
+    t->la_n = n_active;
+    if (active) {
+        if (n_active > t->la_cap) {
+            if (t->la) dev_free(t, t->la, s);
+            t->la = (int64_t *)dev_alloc(t, sizeof(int64_t) * (size_t)n_active, s);
+            t->la_cap = t->la ? n_active : 0;
+            if (!t->la) return SFG_ENOMEM;
+        }
+        SFG_CUDA_OK(cudaMemcpyAsync(t->la, active, sizeof(int64_t) * (size_t)n_active, cudaMemcpyDeviceToDevice, s));
+    }
+    t->lists_ok = true;
+    return SFG_OK;
+}
+
+// Do the stored lists belong to this active set?  (one synchronization)
+static int lists_match(Tree *t, const int64_t *active, int64_t n_active, cudaStream_t s, bool &match)
+{
+    match = false;
+    if (!t->lists_ok || t->la_n != n_active || t->la_all != (active == nullptr)) return SFG_OK;
+    if (!active) {
+        match = true;
+        return SFG_OK;
+    }
+    if (!t->d_flag) {
+        t->d_flag = (int *)dev_alloc(t, sizeof(int), s);
+        if (!t->d_flag) return SFG_ENOMEM;
+    }
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_flag, 0, sizeof(int), s));
+    k_cmp_idx<<<grid_for(n_active, 256), 256, 0, s>>>(active, t->la, n_active, t->d_flag);
+    t->n_launch += 1;
+    int f = 1;
+    SFG_CUDA_OK(cudaMemcpyAsync(&f, t->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaStreamSynchronize(s));
+    match = f == 0;
+    return SFG_OK;
+}
+
+template <int MODE>
+static void launch_eval(Tree *t, WalkParams &P, cudaStream_t s)
+{
+    const int blocks = num_sms() * EVAL_MINB;
+    if (t->prm.quadrupole) k_eval<true, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
+    else k_eval<false, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
+    t->n_launch += 1;
 }
 
 int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double *phi, cudaStream_t s)
@@ -1474,13 +2049,24 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
         SFG_CUDA_OK(cudaMemsetAsync(res64, 0, 32 * (size_t)t->n, s));
         P.res64 = res64;
     }
-    make_items(t, w, P, s);
+    const bool lists = !f64 && use_lists(t, s);
+    if (lists) {
+        rc = build_lists(t, w, P, s);
+        if (rc) return rc;
+        rc = remember_active(t, active, n_active, s);
+        if (rc) return rc;
+        items_from_counts(t, w, P, s);
+    } else {
+        t->lists_ok = false; // the counting walk below overwrites their sizes
+        make_items(t, w, P, s);
+    }
     if (t->timing) {
         int rc2 = cloud_timer_begin(t, 0, s, P);
         if (rc2) return rc2;
     }
     ph_begin(t, PH_FWD_WALK, s);
     if (f64) launch_walk<MODE_EVAL64>(t, P, s);
+    else if (lists) launch_eval<MODE_EVAL>(t, P, s);
     else launch_walk<MODE_EVAL>(t, P, s);
     ph_end(t, PH_FWD_WALK, s);
     if (f64) {
@@ -1639,13 +2225,30 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         P.cot = cot;
         P.gpart = gpart;
         P.gnode = gnode;
-        make_items(t, w, P, s);
+        const bool lists = use_lists(t, s);
+        if (lists) {
+            // the forward's lists when it was called with the same active set
+            bool match = false;
+            rc = lists_match(t, active, n_active, s, match);
+            if (rc) return rc;
+            if (!match) {
+                rc = build_lists(t, w, P, s);
+                if (rc) return rc;
+                rc = remember_active(t, active, n_active, s);
+                if (rc) return rc;
+            }
+            items_from_counts(t, w, P, s);
+        } else {
+            t->lists_ok = false;
+            make_items(t, w, P, s);
+        }
         if (t->timing) {
             int rc2 = cloud_timer_begin(t, 1, s, P);
             if (rc2) return rc2;
         }
         ph_begin(t, PH_VJP_WALK, s);
-        launch_walk<MODE_VJP>(t, P, s);
+        if (lists) launch_eval<MODE_VJP>(t, P, s);
+        else launch_walk<MODE_VJP>(t, P, s);
         ph_end(t, PH_VJP_WALK, s);
         k_gnode_unit<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nM, nn);
         t->n_launch += 4;
@@ -1676,22 +2279,22 @@ int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_gro
     int ng = 0;
     SFG_CUDA_OK(cudaMemcpyAsync(&ng, t->d_counters + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
-    int *cnt = (int *)dev_alloc(t, sizeof(int) * 3 * (size_t)(ng > 0 ? ng : 1), s);
+    int *cnt = (int *)dev_alloc(t, sizeof(int) * NCNT * (size_t)(ng > 0 ? ng : 1), s);
     if (!cnt) return SFG_ENOMEM;
     P.dbg_counts = cnt;
     launch_walk<MODE_COUNT>(t, P, s);
     int2 *gt_h = (int2 *)malloc(sizeof(int2) * (size_t)(ng > 0 ? ng : 1));
-    int *cnt_h = (int *)malloc(sizeof(int) * 3 * (size_t)(ng > 0 ? ng : 1));
+    int *cnt_h = (int *)malloc(sizeof(int) * NCNT * (size_t)(ng > 0 ? ng : 1));
     SFG_CUDA_OK(cudaMemcpyAsync(gt_h, w.gtab, sizeof(int2) * (size_t)ng, cudaMemcpyDeviceToHost, s));
-    SFG_CUDA_OK(cudaMemcpyAsync(cnt_h, cnt, sizeof(int) * 3 * (size_t)ng, cudaMemcpyDeviceToHost, s));
+    SFG_CUDA_OK(cudaMemcpyAsync(cnt_h, cnt, sizeof(int) * NCNT * (size_t)ng, cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
     long long tm = 0, tp = 0;
     long long *off_h = (long long *)malloc(sizeof(long long) * 2 * (size_t)(ng > 0 ? ng : 1));
     for (int g = 0; g < ng; g++) {
         off_h[2 * g] = tm;
         off_h[2 * g + 1] = tp;
-        tm += cnt_h[3 * g];
-        tp += cnt_h[3 * g + 1];
+        tm += cnt_h[NCNT * g];
+        tp += cnt_h[NCNT * g + 1] + cnt_h[NCNT * g + 3];
     }
     *n_groups = ng;
     *n_p2m_total = tm;
@@ -1700,8 +2303,8 @@ int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_gro
         for (int g = 0; g < ng; g++) {
             groups[4 * g] = gt_h[g].x;
             groups[4 * g + 1] = gt_h[g].y;
-            groups[4 * g + 2] = cnt_h[3 * g];
-            groups[4 * g + 3] = cnt_h[3 * g + 1];
+            groups[4 * g + 2] = cnt_h[NCNT * g];
+            groups[4 * g + 3] = cnt_h[NCNT * g + 1] + cnt_h[NCNT * g + 3];
         }
         long long *off_d = (long long *)dev_alloc(t, sizeof(long long) * 2 * (size_t)(ng > 0 ? ng : 1), s);
         int *dm = (int *)dev_alloc(t, sizeof(int) * (size_t)(tm > 0 ? tm : 1), s);
