@@ -375,7 +375,8 @@ def run_ensemble(args, rank, world, dist, dev):
                      "achieved": round(ach, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                      "frac": round(ach / fp32_peak, 4), "traffic": None,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"},
-        "interactions": {"p2p": int(st["n_p2p"]), "p2m": int(st["n_p2m"]), "groups": int(st["n_groups"])},
+        "interactions": {"p2p": int(st["n_p2p"]), "p2m": int(st["n_p2m"]),
+                         "p2p_newtonian_list": int(st["n_p2p_newton"]), "groups": int(st["n_groups"])},
         "particles_per_s": n * world / (ms * 1e-3),
         "e2e": {"value": e2e_val, "unit": "clouds/s",
                 "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in h_in),
@@ -484,7 +485,7 @@ def main():
     torch.cuda.synchronize(dev)
     sampler.start()
     times, walk_ms, vjp_walk_ms, fwd_ms, vjp_ms, build_ms = [], [], [], [], [], []
-    p2p = p2m = launches = n_ovf = 0
+    p2p = p2m = p2p_newt = launches = n_ovf = 0
     for _ in range(args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -500,7 +501,7 @@ def main():
         fwd_ms.append(st["fwd_ms"])
         vjp_ms.append(st["vjp_ms"])
         build_ms.append(st["build_ms"])
-        p2p, p2m = st["n_p2p"], st["n_p2m"]
+        p2p, p2m, p2p_newt = st["n_p2p"], st["n_p2m"], st["n_p2p_newton"]
         n_ovf = st["n_overflow"]
         launches += st["n_launches"]
         tree.check()
@@ -582,7 +583,7 @@ def main():
                       "fwd_walk": round(wk, 4), "vjp": round(statistics.mean(vjp_ms), 4),
                       "vjp_walk": round(statistics.mean(vjp_walk_ms), 4)},
         "adjoint_over_forward": round(statistics.mean(vjp_ms) / statistics.mean(fwd_ms), 3),
-        "interactions": {"p2p": int(p2p), "p2m": int(p2m),
+        "interactions": {"p2p": int(p2p), "p2m": int(p2m), "p2p_newtonian_list": int(p2p_newt),
                          "per_active": round((p2p + p2m) / act.size, 1), "overflowed_groups": int(n_ovf),
                          "fwd_per_s": round((p2p + p2m) / (statistics.mean(fwd_ms) * 1e-3), 1)},
         "build_hbm": {"algorithmic_GBps": round(BUILD_BYTES_PER_PARTICLE * c.n / (statistics.mean(build_ms) * 1e-3)

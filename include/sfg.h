@@ -92,9 +92,12 @@ typedef struct sfg_stats {
      * from CUDA events on the call's stream (0 when off) */
     float build_ms;       /* whole sfg_build */
     float fwd_ms;         /* whole sfg_accel */
-    float fwd_walk_ms;    /* its walk + evaluation launches (after the list-counting pass) */
+    float fwd_walk_ms;    /* its evaluation launch (k_eval from stored lists, or the walking
+                             evaluation when lists are off), after the list passes */
     float vjp_ms;         /* whole sfg_accel_vjp */
-    float vjp_walk_ms;    /* its walk + adjoint launches (after the list-counting pass) */
+    float vjp_walk_ms;    /* its adjoint evaluation launch, likewise */
+    int64_t n_p2p_newton; /* of n_p2p: pairs from stored Newtonian range lists (opened leaves wholly
+                             outside both softening supports; 0 without stored lists) */
 } sfg_stats;
 
 /* Fill *p with the defaults: G = 1, theta = 0.5, leaf_size = 16, group_size = 32,

@@ -194,7 +194,7 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
 {
     if (!tree || !out) return SFG_EINVAL;
     Tree *t = &tree->t;
-    unsigned long long c[8];
+    unsigned long long c[NCOUNTERS];
     SFG_CUDA_OK(cudaMemcpyAsync(c, t->d_counters, sizeof(c), cudaMemcpyDeviceToHost, t->stream));
     SFG_CUDA_OK(cudaStreamSynchronize(t->stream));
     sfg_stats s;
@@ -207,6 +207,7 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
     s.L0 = t->frame_h.L0;
     s.n_p2p = (int64_t)c[0];
     s.n_p2m = (int64_t)c[1];
+    s.n_p2p_newton = (int64_t)c[8];
     s.n_overflow = (int64_t)c[2];
     s.n_clouds = t->nclouds;
     s.n_groups = (int64_t)(*(int *)&c[5]);

@@ -677,12 +677,12 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->d_off, int64_t, C + 1);
     ALLOC(t->d_minmax, unsigned long long, 6 * (size_t)C);
     ALLOC(t->d_lvl, int, SFG_LMAX + 3);
-    ALLOC(t->d_counters, unsigned long long, 8);
+    ALLOC(t->d_counters, unsigned long long, NCOUNTERS);
     ALLOC(t->d_n, int, 1);
     SFG_CUDA_OK(cudaMemcpyAsync(t->d_off, t->off_h.data(), sizeof(int64_t) * (C + 1), cudaMemcpyHostToDevice, s));
     k_set_int<<<1, 1, 0, s>>>(t->d_n, n);
     SFG_CUDA_OK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
-    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, 8 * sizeof(unsigned long long), s));
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, NCOUNTERS * sizeof(unsigned long long), s));
 
     const dim3 cg = cloud_grid(t, BT);
     t->n_launch += 2 + 3; // k_set_int, k_minmax_init, k_validate_minmax, k_frame, k_keys

@@ -46,6 +46,8 @@ struct Frame {
     double half_cell; // L0 / 2^22 (exact)
 };
 
+constexpr int NCOUNTERS = 10;
+
 struct Tree {
     sfg_params prm;
     int64_t n = 0;
@@ -84,7 +86,8 @@ struct Tree {
     void *ws = nullptr, *ws2 = nullptr;
     size_t ws_bytes = 0, ws2_bytes = 0;
     sfg_stats last{};
-    // [0] p2p, [1] p2m, [2] overflowed groups, [3] work, [4] retry work, [5] groups, [6] distinct targets
+    // [0] p2p, [1] p2m, [2] overflowed groups, [3] work, [4] retry work, [5] groups, [6] distinct targets,
+    // [7] item cost total, [8] Newtonian-list P2P interactions
     unsigned long long *d_counters = nullptr;
     int *d_n = nullptr; // device copy of n
     long long n_launch = 0;

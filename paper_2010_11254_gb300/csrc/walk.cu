@@ -609,10 +609,12 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, SM &S, int cnt, i
             float h = __int_as_float(b.w); // negative for a sink
             float ha = fabsf(h);
             S.tA[lane] = make_float4(ha, 1.f / ha, __int_as_float(j), h < 0.f ? 1.f : 0.f);
+            S.tB[lane] = ha * ha;
         } else { // the ring ran dry or a corrupt range: massless and far, no gradient
             atomicOr(P.status, ST_ETIMEOUT);
             S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f);
             S.tA[lane] = make_float4(1.f, 1.f, __int_as_float(-1), 0.f);
+            S.tB[lane] = 0.f;
         }
     }
     __syncwarp();
@@ -889,7 +891,7 @@ __device__ __forceinline__ void setup_group(const WalkParams &P, int g, int lane
 template <int MODE>
 __device__ __forceinline__ void finish_targets(const WalkParams &P, const Tgt &T, int g, int kk, int K, int tfirst,
                                                int tcount, float ax, float ay, float az, double phi, int n_src_p,
-                                               int n_src_m, int lane)
+                                               int n_src_m, int n_src_pn, int lane)
 {
     for (int o = T.tp; o < 32; o <<= 1) {
         ax += __shfl_xor_sync(FULL, ax, o);
@@ -945,6 +947,7 @@ __device__ __forceinline__ void finish_targets(const WalkParams &P, const Tgt &T
         // count the group's list once (self pairs excluded)
         atomicAdd(&P.counters[0], (unsigned long long)tcount * (unsigned long long)(n_src_p - 1));
         atomicAdd(&P.counters[1], (unsigned long long)tcount * (unsigned long long)n_src_m);
+        if (n_src_pn) atomicAdd(&P.counters[8], (unsigned long long)tcount * (unsigned long long)n_src_pn);
     }
 }
 
@@ -1073,7 +1076,7 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
         }
         return;
     }
-    finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, W.ax, W.ay, W.az, W.phi, W.tot_p, W.tot_m, lane);
+    finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, W.ax, W.ay, W.az, W.phi, W.tot_p, W.tot_m, 0, lane);
 }
 
 // ------------------------------------------------ stored-list evaluation ----
@@ -1086,8 +1089,13 @@ struct EvalSmem {
     int2 leafq[64]; // ring of P2P ranges being staged
     float4 tP[32];
     float4 tA[32];
-    float tB[32];
+    float tB[32];   // P2M: Qyz; P2P: h^2
     int tN[32];
+    // the group's targets, for pairs evaluated off their own lane
+    float4 gT[32];  // (ox, oy, oz, h)
+    float4 gU[32];  // (1/h, sink flag, target rank bits, h^2)
+    float4 sAcc[32]; // per-target sums of the softened pairs: (a, phi)
+    unsigned short sq[1024]; // softened pairs of a tile: target | source << 5
 };
 
 constexpr int EVAL_WARPS = 4;
@@ -1215,6 +1223,105 @@ __device__ __forceinline__ void vjp_p2p_newt(const WalkParams &P, const SM &S, i
     }
 }
 
+
+// Forward of a softened-list tile.  Every pair first takes the Newtonian
+// kernel; a pair inside max(h_i, h_j) (the self pair included) is left out
+// and flagged in the lane's 32-bit mask instead.  The flagged pairs of the
+// whole warp are then compacted into a queue and evaluated with the full
+// pair rule 32 at a time, their sums collected per target in shared memory.
+template <class SM>
+__device__ __forceinline__ void fwd_step_defer(const SM &S, int k, const Tgt &T, float ht2, float &ax, float &ay,
+                                               float &az, float &pt, unsigned &mask)
+{
+    float4 p = S.tP[k];
+    float hj2 = S.tB[k];
+    float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    bool sft = r2 < fmaxf(ht2, hj2);
+    if (sft) mask |= 1u << k;
+    float rinv = rsqrtf(sft ? 1.f : r2);
+    float mr = sft ? 0.f : p.w * rinv;
+    float mr3 = mr * (rinv * rinv);
+    ax = fmaf(mr3, dx, ax);
+    ay = fmaf(mr3, dy, ay);
+    az = fmaf(mr3, dz, az);
+    pt -= mr;
+}
+
+// Exclusive warp prefix of n and the warp total.
+__device__ __forceinline__ int warp_excl(int n, int lane, int &total)
+{
+    int v = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    total = __shfl_sync(FULL, v, 31);
+    return v - n;
+}
+
+__device__ __forceinline__ void fwd_p2p_defer(EvalSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+                                              double &phi, int lane)
+{
+    float pt = 0.f;
+    unsigned mask = 0u;
+    const float ht2 = T.h * T.h;
+    if (T.has) {
+        if (T.R == 1 && cnt == 32) {
+#pragma unroll
+            for (int k = 0; k < 32; k++) fwd_step_defer(S, k, T, ht2, ax, ay, az, pt, mask);
+        } else {
+#pragma unroll 2
+            for (int k = T.slice; k < cnt; k += T.R) fwd_step_defer(S, k, T, ht2, ax, ay, az, pt, mask);
+        }
+    }
+    phi += (double)pt;
+    int total;
+    int at = warp_excl(__popc(mask), lane, total);
+    if (total == 0) return;
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        S.sq[at++] = (unsigned short)(T.tl | (k << 5));
+    }
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+        if (b + lane < total) {
+            const unsigned e = S.sq[b + lane];
+            const int t = e & 31, k = e >> 5;
+            const float4 tg = S.gT[t], tu = S.gU[t];
+            const float4 p = S.tP[k], hh = S.tA[k];
+            if (__float_as_int(hh.z) != __float_as_int(tu.z)) { // not the self pair
+                float dx = p.x - tg.x, dy = p.y - tg.y, dz = p.z - tg.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                // pair rule (Sec. 2.2.1): gas-gas averages the kernels of both
+                // supports, any sink uses one kernel of the larger support
+                bool sink = tu.y != 0.f || hh.w != 0.f;
+                bool tbig = tg.w >= hh.x;
+                float ha = tbig ? tg.w : hh.x, hainv = tbig ? tu.x : hh.y;
+                float hb = sink ? ha : (tbig ? hh.x : tg.w), hbinv = sink ? hainv : (tbig ? hh.y : tu.x);
+                float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                float r = r2 * rinv;
+                float K1, P1, K2, P2;
+                soft_KP(r, rinv, ha, hainv, K1, P1);
+                soft_KP(r, rinv, hb, hbinv, K2, P2);
+                float mK = p.w * 0.5f * (K1 + K2);
+                atomicAdd(&S.sAcc[t].x, mK * dx);
+                atomicAdd(&S.sAcc[t].y, mK * dy);
+                atomicAdd(&S.sAcc[t].z, mK * dz);
+                atomicAdd(&S.sAcc[t].w, p.w * 0.5f * (P1 + P2));
+            }
+        }
+    }
+    __syncwarp();
+    // potentials: FP32 within the tile, FP64 across tiles (like the lane sums)
+    if (T.has && T.slice == 0) {
+        phi += (double)S.sAcc[T.tl].w;
+        S.sAcc[T.tl].w = 0.f;
+    }
+    __syncwarp();
+}
+
 // This item's share of one P2P list: nr ranges holding np particles.
 template <int MODE, bool NEWT>
 __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, const Tgt &T, const int2 *rr, int nr,
@@ -1266,11 +1373,12 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
         } else {
             stage_p2p(P, S, c, qh, qoff, T, lane);
             if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (T.has) fwd_p2p(S, c, T, ax, ay, az, phi);
+            else fwd_p2p_defer(S, c, T, ax, ay, az, phi, lane);
         }
         __syncwarp();
     }
 }
+
 
 template <bool QUAD, int MODE>
 __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g, int kk, int K, int lane)
@@ -1289,6 +1397,12 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     }
     float ax = 0.f, ay = 0.f, az = 0.f;
     double phi = 0.0;
+    if (T.slice == 0) {
+        S.gT[T.tl] = make_float4(T.ox, T.oy, T.oz, T.h);
+        S.gU[T.tl] = make_float4(T.hinv, T.sink ? 1.f : 0.f, __int_as_float(T.r), T.h * T.h);
+    }
+    S.sAcc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
     const int *cn = P.lcnt + NCNT * (size_t)g;
     const int nm = cn[0], nls = cn[1], nps = cn[2], nln = cn[3], npn = cn[4];
     {
@@ -1306,7 +1420,14 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     const int2 *lr = P.lr + P.lro[g];
     eval_p2p_list<MODE, false>(P, S, T, lr, nls, nps, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
     eval_p2p_list<MODE, true>(P, S, T, lr + nls, nln, npn, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
-    finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, ax, ay, az, phi, nps + npn, nm, lane);
+    if (MODE == MODE_EVAL && T.has && T.slice == 0) {
+        const float4 v = S.sAcc[T.tl];
+        ax += v.x;
+        ay += v.y;
+        az += v.z;
+    }
+    __syncwarp();
+    finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, ax, ay, az, phi, nps + npn, nm, npn, lane);
     return cloud;
 }
 
@@ -1848,7 +1969,7 @@ static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, Wa
 {
     int rc = get_work(t, s, w);
     if (rc) return rc;
-    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, 8 * sizeof(unsigned long long), s));
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, NCOUNTERS * sizeof(unsigned long long), s));
     const int *dng;
     rc = form_groups(t, active, n_active, w, &dng, s);
     if (rc) return rc;
