@@ -73,13 +73,36 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def make_inputs(wl: dict, rank: int, frac: float | None):
+def make_cloud(wl: dict, rank: int):
+    """The workload's cloud; with SFG_CLOUD_CACHE=<dir> the generated arrays are
+    kept there (npz) for later runs of the same workload and rank."""
     import gen
     seed = gen.CONFIG_SEED[wl["seed_id"]] + 1000 * rank
+    cache = os.environ.get("SFG_CLOUD_CACHE")
+    path = None
+    if cache:
+        path = os.path.join(cache, f"cloud_{wl['n_gas']}_{wl['n_clumps']}_{wl['n_sink']}_{seed}.npz")
+        if os.path.exists(path):
+            z = np.load(path)
+            return gen.Cloud(z["pos"], z["mass"], z["soft"], z["is_sink"], seed, "clumpy (cached)"), seed
     c = gen.clumpy_cloud(wl["n_gas"], n_clumps=wl["n_clumps"], n_sink=wl["n_sink"], seed=seed)
-    f = wl["active"] if frac is None else frac
-    act = gen.active_subset(c.n, f, seed=seed)
+    if path:
+        os.makedirs(cache, exist_ok=True)
+        np.savez(path, pos=c.pos, mass=c.mass, soft=c.soft, is_sink=c.is_sink)
+    return c, seed
+
+
+def make_active(c, frac: float, seed: int):
+    import gen
+    act = gen.active_subset(c.n, frac, seed=seed)
     ca, cp = gen.cotangents(act.size, seed=seed + 7)
+    return act, ca, cp
+
+
+def make_inputs(wl: dict, rank: int, frac: float | None):
+    c, seed = make_cloud(wl, rank)
+    f = wl["active"] if frac is None else frac
+    act, ca, cp = make_active(c, f, seed)
     return c, act, ca, cp, f
 
 
@@ -412,49 +435,10 @@ def run_reference_ensemble(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS) + ["ensemble-256"])
-    ap.add_argument("--active-frac", type=float, default=None)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--leaf-size", type=int, default=16)
-    ap.add_argument("--group-size", type=int, default=32)
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
-                    help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
-    args = ap.parse_args()
-    wl = WORKLOADS.get(args.workload)
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        if wl is None:
-            run_reference_ensemble(args, rank)
-        else:
-            run_reference(args, wl, rank, world)
-        return
-
+def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
+    """One bench line: warm-up and timed steps, e2e loop, rooflines, error."""
     import torch
     import paper_2010_11254_gb300 as sfg
-
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    os.environ.setdefault("SFG_TIMING", "1")
-    if args.workload == "ensemble-256":
-        run_ensemble(args, rank, world, dist, dev)
-        if dist is not None:
-            dist.destroy_process_group()
-        return
-
-    c, act, ca, cp, frac = make_inputs(wl, rank, args.active_frac)
     d_pos = torch.from_numpy(c.pos).to(dev)
     d_mass = torch.from_numpy(c.mass).to(dev)
     d_soft = torch.from_numpy(c.soft).to(dev)
@@ -465,7 +449,9 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     kw = dict(theta=wl["theta"], leaf_size=args.leaf_size, group_size=args.group_size, quadrupole=True,
-              precision=args.precision)
+              precision=args.precision, store_lists=bool(args.store_lists))
+    lists = bool(args.store_lists) and args.precision == 0
+    kname = "k_eval" if lists else "k_walk"
 
     def one_step():
         tree = sfg.Tree(d_pos, d_mass, d_soft, d_sink, **kw)
@@ -559,10 +545,10 @@ def main():
 
     wk = statistics.mean(walk_ms)
     vk = statistics.mean(vjp_walk_ms)
-    r_fwd = roof("k_walk<QUAD, MODE_EVAL> (forward walk + FP32 evaluation)",
+    r_fwd = roof(f"{kname}<QUAD, MODE_EVAL> (forward FP32 evaluation{' from stored lists' if lists else ''})",
                  p2p * FLOP_P2P + p2m * FLOP_P2M_QUAD, wk, "fwd",
                  f"P2P {FLOP_P2P}, P2M quadrupole {FLOP_P2M_QUAD} FP32 flops per interaction")
-    r_vjp = roof("k_walk<QUAD, MODE_VJP> (adjoint walk + FP32 tidal-tensor products)",
+    r_vjp = roof(f"{kname}<QUAD, MODE_VJP> (adjoint FP32 tidal-tensor products{' from stored lists' if lists else ''})",
                  p2p * FLOP_VJP_P2P + p2m * FLOP_VJP_P2M_QUAD, vk, "vjp",
                  f"P2P {FLOP_VJP_P2P}, P2M quadrupole {FLOP_VJP_P2M_QUAD} FP32 flops per interaction")
     dominant, other = (r_vjp, r_fwd) if vk >= wk else (r_fwd, r_vjp)
@@ -574,7 +560,7 @@ def main():
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
                    "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"],
                    "leaf_size": args.leaf_size, "group_size": args.group_size, "quadrupole": True,
-                   "precision": args.precision,
+                   "precision": args.precision, "store_lists": bool(args.store_lists),
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"independent clouds x{world}"},
         "roofline": dominant,
@@ -595,11 +581,67 @@ def main():
         "clocks": clocks,
     }
     if rank == 0:
-        line["force_error"] = force_error(c, act, acc_h, phi_h)
+        line["force_error"] = force_error(c, act, acc_h, phi_h, sample=args.error_sample)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, c, act, ca, cp)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS) + ["ensemble-256"])
+    ap.add_argument("--active-frac", type=float, default=None)
+    ap.add_argument("--active-fracs", default=None,
+                    help="comma-separated active fractions: one line each on the same cloud")
+    ap.add_argument("--error-sample", type=int, default=1000,
+                    help="active rows checked against the FP64 direct sum")
+    ap.add_argument("--store-lists", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf-size", type=int, default=16)
+    ap.add_argument("--group-size", type=int, default=32)
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
+    args = ap.parse_args()
+    wl = WORKLOADS.get(args.workload)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if wl is None:
+            run_reference_ensemble(args, rank)
+        else:
+            run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    import paper_2010_11254_gb300 as sfg
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    os.environ.setdefault("SFG_TIMING", "1")
+    if args.workload == "ensemble-256":
+        run_ensemble(args, rank, world, dist, dev)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    c, seed = make_cloud(wl, rank)
+    fracs = ([float(x) for x in args.active_fracs.split(",")] if args.active_fracs
+             else [wl["active"] if args.active_frac is None else args.active_frac])
+    for frac in fracs:
+        act, ca, cp = make_active(c, frac, seed)
+        line = run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
