@@ -151,6 +151,7 @@ typedef struct {
     uint32_t cq[3];        /* grid cell of the centre of mass */
     uint64_t hq;           /* ceil((hmax / cell)^2), capped at 2^62 */
     double M, com[3], Q[6]; /* Q: xx yy zz xy xz yz, traceless, about com */
+    double S[6];            /* second moment sum m d d^T about com (xx yy zz xy xz yz) */
     double hmax, flo[3], fhi[3]; /* max softening; FP64 tight box */
 } onode;
 
@@ -256,59 +257,80 @@ static void node_centre(const sfgo_tree *t, const onode *nd, double c[3])
         c[a] = t->x0[a] + (double)(2u * nd->corner[a] + (1u << (LMAX - nd->level))) * half_cell;
 }
 
-/* Moments of every node from (pos, mass) in sorted order: leaves sum their
- * members in sorted order; internal nodes combine children in octant order
- * (parallel-axis theorem for Q).  Fixed operation order. */
+/* Moments of every node (Sec. 2.2: mass, centre of mass, and the traceless
+ * quadrupole Q = sum m (3 d d^T - |d|^2 I) about the centre of mass, d =
+ * x - com).  Every node first sums about its own cell centre c: the mass M,
+ * the first moment s = sum m (x - c) and the second moment S' = sum m (x - c)
+ * (x - c)^T -- over its members in sorted order for a leaf, over its
+ * children in octant order for an internal node, each child entering with its
+ * mass at its centre of mass plus its own second moment about it.  Then the
+ * parallel-axis theorem moves S' to the centre of mass: com = c + s/M and
+ * S = S' - s (s/M)^T, and Q = 3 S - tr(S) I.  A massless node keeps com = c.
+ * Fixed operation order; the products added into S' and the shift use an
+ * explicit fused multiply-add (one rounding, C99 fma), everything else is
+ * plain IEEE add/mul/div without contraction. */
 static void compute_moments(sfgo_tree *t, const double *pos, const double *mass)
 {
     for (int64_t i = t->nn - 1; i >= 0; i--) {
         onode *nd = &t->nodes[i];
-        double M = 0.0, s[3] = {0.0, 0.0, 0.0}, Q[6] = {0, 0, 0, 0, 0, 0}, com[3];
-        if (nd->nchild == 0) {
-            for (int64_t k = nd->first; k < nd->first + nd->count; k++) M = M + mass[k];
-            for (int64_t k = nd->first; k < nd->first + nd->count; k++)
-                for (int a = 0; a < 3; a++) s[a] = s[a] + mass[k] * pos[3 * k + a];
-        } else {
-            for (int c = 0; c < nd->nchild; c++) M = M + t->nodes[nd->child_first + c].M;
-            for (int c = 0; c < nd->nchild; c++) {
-                const onode *ch = &t->nodes[nd->child_first + c];
-                for (int a = 0; a < 3; a++) s[a] = s[a] + ch->M * ch->com[a];
-            }
-        }
-        if (M > 0.0) {
-            for (int a = 0; a < 3; a++) com[a] = s[a] / M;
-        } else {
-            node_centre(t, nd, com);
-        }
+        double c[3];
+        node_centre(t, nd, c);
+        double M = 0.0, s[3] = {0.0, 0.0, 0.0}, S[6] = {0, 0, 0, 0, 0, 0};
         if (nd->nchild == 0) {
             for (int64_t k = nd->first; k < nd->first + nd->count; k++) {
                 double m = mass[k];
-                double d0 = pos[3 * k] - com[0], d1 = pos[3 * k + 1] - com[1], d2 = pos[3 * k + 2] - com[2];
-                double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                Q[0] = Q[0] + m * (3.0 * d0 * d0 - r2);
-                Q[1] = Q[1] + m * (3.0 * d1 * d1 - r2);
-                Q[2] = Q[2] + m * (3.0 * d2 * d2 - r2);
-                Q[3] = Q[3] + m * (3.0 * d0 * d1);
-                Q[4] = Q[4] + m * (3.0 * d0 * d2);
-                Q[5] = Q[5] + m * (3.0 * d1 * d2);
+                double d[3], md[3];
+                for (int a = 0; a < 3; a++) d[a] = pos[3 * k + a] - c[a];
+                M = M + m;
+                for (int a = 0; a < 3; a++) md[a] = m * d[a];
+                for (int a = 0; a < 3; a++) s[a] = s[a] + md[a];
+                S[0] = fma(md[0], d[0], S[0]);
+                S[1] = fma(md[1], d[1], S[1]);
+                S[2] = fma(md[2], d[2], S[2]);
+                S[3] = fma(md[0], d[1], S[3]);
+                S[4] = fma(md[0], d[2], S[4]);
+                S[5] = fma(md[1], d[2], S[5]);
             }
         } else {
-            for (int c = 0; c < nd->nchild; c++) {
-                const onode *ch = &t->nodes[nd->child_first + c];
-                double Mc = ch->M;
-                double d0 = ch->com[0] - com[0], d1 = ch->com[1] - com[1], d2 = ch->com[2] - com[2];
-                double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                Q[0] = Q[0] + (ch->Q[0] + Mc * (3.0 * d0 * d0 - r2));
-                Q[1] = Q[1] + (ch->Q[1] + Mc * (3.0 * d1 * d1 - r2));
-                Q[2] = Q[2] + (ch->Q[2] + Mc * (3.0 * d2 * d2 - r2));
-                Q[3] = Q[3] + (ch->Q[3] + Mc * (3.0 * d0 * d1));
-                Q[4] = Q[4] + (ch->Q[4] + Mc * (3.0 * d0 * d2));
-                Q[5] = Q[5] + (ch->Q[5] + Mc * (3.0 * d1 * d2));
+            for (int q = 0; q < nd->nchild; q++) {
+                const onode *ch = &t->nodes[nd->child_first + q];
+                double d[3], md[3];
+                for (int a = 0; a < 3; a++) d[a] = ch->com[a] - c[a];
+                M = M + ch->M;
+                for (int a = 0; a < 3; a++) md[a] = ch->M * d[a];
+                for (int a = 0; a < 3; a++) s[a] = s[a] + md[a];
+                S[0] = S[0] + fma(md[0], d[0], ch->S[0]);
+                S[1] = S[1] + fma(md[1], d[1], ch->S[1]);
+                S[2] = S[2] + fma(md[2], d[2], ch->S[2]);
+                S[3] = S[3] + fma(md[0], d[1], ch->S[3]);
+                S[4] = S[4] + fma(md[0], d[2], ch->S[4]);
+                S[5] = S[5] + fma(md[1], d[2], ch->S[5]);
             }
         }
+        if (M > 0.0) {
+            double dl[3];
+            for (int a = 0; a < 3; a++) {
+                dl[a] = s[a] / M;
+                nd->com[a] = c[a] + dl[a];
+            }
+            S[0] = fma(-s[0], dl[0], S[0]);
+            S[1] = fma(-s[1], dl[1], S[1]);
+            S[2] = fma(-s[2], dl[2], S[2]);
+            S[3] = fma(-s[0], dl[1], S[3]);
+            S[4] = fma(-s[0], dl[2], S[4]);
+            S[5] = fma(-s[1], dl[2], S[5]);
+        } else {
+            for (int a = 0; a < 3; a++) nd->com[a] = c[a];
+        }
+        double tr = S[0] + S[1] + S[2];
         nd->M = M;
-        for (int a = 0; a < 3; a++) nd->com[a] = com[a];
-        for (int c = 0; c < 6; c++) nd->Q[c] = Q[c];
+        for (int q = 0; q < 6; q++) nd->S[q] = S[q];
+        nd->Q[0] = 3.0 * S[0] - tr;
+        nd->Q[1] = 3.0 * S[1] - tr;
+        nd->Q[2] = 3.0 * S[2] - tr;
+        nd->Q[3] = 3.0 * S[3];
+        nd->Q[4] = 3.0 * S[4];
+        nd->Q[5] = 3.0 * S[5];
     }
 }
 

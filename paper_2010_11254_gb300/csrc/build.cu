@@ -454,6 +454,7 @@ struct MomArgs {
     unsigned long long *Whq;
     float4 *E0, *E1, *E2;
     double *nM, *ncom, *nQ, *nhmax;
+    double *nS; // [nn][6] second moment about the centre of mass (scratch of the reduction)
     float4 *pw;
     int4 *pc;
     const int *leaves;
@@ -472,8 +473,8 @@ __device__ inline void node_centre(const Frame &fr, const uint32_t lo[3], int le
 
 __device__ inline void write_records(const MomArgs &A, const Frame &fr, int node, int level, bool leaf, int link,
                                      int cnt, const uint32_t lo[3], const uint32_t hi[3], double M,
-                                     const double com[3], const double Q[6], double hmax, const double c[3],
-                                     const int ci[3])
+                                     const double com[3], const double Q[6], const double S[6], double hmax,
+                                     const double c[3], const int ci[3])
 {
     uint32_t cq[3];
     for (int a = 0; a < 3; a++) cq[a] = cell_of(com[a], fr.x0[a], fr.scale);
@@ -487,18 +488,70 @@ __device__ inline void write_records(const MomArgs &A, const Frame &fr, int node
     A.nM[node] = M;
     for (int a = 0; a < 3; a++) A.ncom[3 * (size_t)node + a] = com[a];
     for (int k = 0; k < 6; k++) A.nQ[6 * (size_t)node + k] = Q[k];
+    for (int k = 0; k < 6; k++) A.nS[6 * (size_t)node + k] = S[k];
     A.nhmax[node] = hmax;
+}
+
+// Moments about the node's cell centre c, then moved to the centre of mass
+// (parallel-axis theorem): M, s = sum m (x - c), S' = sum m (x - c)(x - c)^T
+// in one pass; com = c + s/M, S = S' - s (s/M)^T, Q = 3 S - tr(S) I.  The
+// operation order is fixed (members in sorted order, children in octant
+// order; the products added into S' and the shift are explicit fused
+// multiply-adds, everything else is uncontracted), so the values are
+// reproducible bit for bit.
+__device__ inline void moments_finish(double M, const double s[3], double S[6], const double cen[3], double com[3],
+                                      double Q[6])
+{
+    if (M > 0.0) {
+        double dl[3];
+        for (int a = 0; a < 3; a++) {
+            dl[a] = s[a] / M;
+            com[a] = cen[a] + dl[a];
+        }
+        S[0] = __fma_rn(-s[0], dl[0], S[0]);
+        S[1] = __fma_rn(-s[1], dl[1], S[1]);
+        S[2] = __fma_rn(-s[2], dl[2], S[2]);
+        S[3] = __fma_rn(-s[0], dl[1], S[3]);
+        S[4] = __fma_rn(-s[0], dl[2], S[4]);
+        S[5] = __fma_rn(-s[1], dl[2], S[5]);
+    } else {
+        for (int a = 0; a < 3; a++) com[a] = cen[a];
+    }
+    double tr = S[0] + S[1] + S[2];
+    Q[0] = 3.0 * S[0] - tr;
+    Q[1] = 3.0 * S[1] - tr;
+    Q[2] = 3.0 * S[2] - tr;
+    Q[3] = 3.0 * S[3];
+    Q[4] = 3.0 * S[4];
+    Q[5] = 3.0 * S[5];
 }
 
 __device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
 {
     const int f = A.nfirst[node], c = A.ncount[node], level = A.nlevel[node];
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
-    double M = 0.0, s[3] = {0.0, 0.0, 0.0}, hmax = 0.0;
-    for (int k = f; k < f + c; k++) M = M + A.mass[k];
+    int ci[3];
+    double cen[3];
+    {
+        // every member shares the cell prefix: the first one gives the centre
+        uint64_t key = A.key[f];
+        uint32_t q[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
+        node_centre(fr, q, level, ci, cen);
+    }
+    double M = 0.0, s[3] = {0.0, 0.0, 0.0}, S[6] = {0, 0, 0, 0, 0, 0}, hmax = 0.0;
     for (int k = f; k < f + c; k++) {
         double m = A.mass[k];
-        for (int a = 0; a < 3; a++) s[a] = s[a] + m * A.pos[3 * (size_t)k + a];
+        double d[3], md[3];
+        for (int a = 0; a < 3; a++) d[a] = A.pos[3 * (size_t)k + a] - cen[a];
+        M = M + m;
+        for (int a = 0; a < 3; a++) md[a] = m * d[a];
+        for (int a = 0; a < 3; a++) s[a] = s[a] + md[a];
+        S[0] = __fma_rn(md[0], d[0], S[0]);
+        S[1] = __fma_rn(md[1], d[1], S[1]);
+        S[2] = __fma_rn(md[2], d[2], S[2]);
+        S[3] = __fma_rn(md[0], d[1], S[3]);
+        S[4] = __fma_rn(md[0], d[2], S[4]);
+        S[5] = __fma_rn(md[1], d[2], S[5]);
         uint64_t key = A.key[k];
         uint32_t q[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
         for (int a = 0; a < 3; a++) {
@@ -507,46 +560,24 @@ __device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
         }
         double h = A.soft[k];
         if (h > hmax) hmax = h;
-    }
-    int ci[3];
-    double cen[3], com[3];
-    node_centre(fr, lo, level, ci, cen);
-    if (M > 0.0) {
-        for (int a = 0; a < 3; a++) com[a] = s[a] / M;
-    } else {
-        for (int a = 0; a < 3; a++) com[a] = cen[a];
-    }
-    double Q[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = f; k < f + c; k++) {
-        double m = A.mass[k];
-        double x0 = A.pos[3 * (size_t)k], x1 = A.pos[3 * (size_t)k + 1], x2 = A.pos[3 * (size_t)k + 2];
-        double d0 = x0 - com[0], d1 = x1 - com[1], d2 = x2 - com[2];
-        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-        Q[0] = Q[0] + m * (3.0 * d0 * d0 - r2);
-        Q[1] = Q[1] + m * (3.0 * d1 * d1 - r2);
-        Q[2] = Q[2] + m * (3.0 * d2 * d2 - r2);
-        Q[3] = Q[3] + m * (3.0 * d0 * d1);
-        Q[4] = Q[4] + m * (3.0 * d0 * d2);
-        Q[5] = Q[5] + m * (3.0 * d1 * d2);
         // particle record of the walk: FP32 offset from the leaf centre
-        float hs = (float)A.soft[k];
+        float hs = (float)h;
         if (A.sink[k]) hs = -hs;
-        A.pw[k] = make_float4((float)(x0 - cen[0]), (float)(x1 - cen[1]), (float)(x2 - cen[2]), (float)m);
+        A.pw[k] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)m);
         A.pc[k] = make_int4(ci[0], ci[1], ci[2], __float_as_int(hs));
     }
-    write_records(A, fr, node, level, true, f, c, lo, hi, M, com, Q, hmax, cen, ci);
+    double com[3], Q[6];
+    moments_finish(M, s, S, cen, com, Q);
+    write_records(A, fr, node, level, true, f, c, lo, hi, M, com, Q, S, hmax, cen, ci);
 }
 
 __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
 {
     const int cf = A.nchild_first[node], nc = A.nnchild[node], level = A.nlevel[node];
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
-    double M = 0.0, s[3] = {0.0, 0.0, 0.0}, hmax = 0.0;
-    for (int k = 0; k < nc; k++) M = M + __ldcg(&A.nM[cf + k]);
+    double hmax = 0.0;
     for (int k = 0; k < nc; k++) {
         int ch = cf + k;
-        double Mc = __ldcg(&A.nM[ch]);
-        for (int a = 0; a < 3; a++) s[a] = s[a] + Mc * __ldcg(&A.ncom[3 * (size_t)ch + a]);
         int4 w0 = __ldcg(&A.W0[ch]), w1 = __ldcg(&A.W1[ch]);
         uint32_t l3[3] = {(uint32_t)w0.x, (uint32_t)w0.y, (uint32_t)w0.z};
         uint32_t h3[3] = {(uint32_t)w1.x, (uint32_t)w1.y, (uint32_t)w1.z};
@@ -558,30 +589,28 @@ __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
         if (h > hmax) hmax = h;
     }
     int ci[3];
-    double cen[3], com[3];
+    double cen[3];
     node_centre(fr, lo, level, ci, cen);
-    if (M > 0.0) {
-        for (int a = 0; a < 3; a++) com[a] = s[a] / M;
-    } else {
-        for (int a = 0; a < 3; a++) com[a] = cen[a];
-    }
-    double Q[6] = {0, 0, 0, 0, 0, 0};
+    double M = 0.0, s[3] = {0.0, 0.0, 0.0}, S[6] = {0, 0, 0, 0, 0, 0};
     for (int k = 0; k < nc; k++) {
         int ch = cf + k;
         double Mc = __ldcg(&A.nM[ch]);
-        double d0 = __ldcg(&A.ncom[3 * (size_t)ch]) - com[0];
-        double d1 = __ldcg(&A.ncom[3 * (size_t)ch + 1]) - com[1];
-        double d2 = __ldcg(&A.ncom[3 * (size_t)ch + 2]) - com[2];
-        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-        const double *Qc = A.nQ + 6 * (size_t)ch;
-        Q[0] = Q[0] + (__ldcg(&Qc[0]) + Mc * (3.0 * d0 * d0 - r2));
-        Q[1] = Q[1] + (__ldcg(&Qc[1]) + Mc * (3.0 * d1 * d1 - r2));
-        Q[2] = Q[2] + (__ldcg(&Qc[2]) + Mc * (3.0 * d2 * d2 - r2));
-        Q[3] = Q[3] + (__ldcg(&Qc[3]) + Mc * (3.0 * d0 * d1));
-        Q[4] = Q[4] + (__ldcg(&Qc[4]) + Mc * (3.0 * d0 * d2));
-        Q[5] = Q[5] + (__ldcg(&Qc[5]) + Mc * (3.0 * d1 * d2));
+        double d[3], md[3];
+        for (int a = 0; a < 3; a++) d[a] = __ldcg(&A.ncom[3 * (size_t)ch + a]) - cen[a];
+        M = M + Mc;
+        for (int a = 0; a < 3; a++) md[a] = Mc * d[a];
+        for (int a = 0; a < 3; a++) s[a] = s[a] + md[a];
+        const double *Sc = A.nS + 6 * (size_t)ch;
+        S[0] = S[0] + __fma_rn(md[0], d[0], __ldcg(&Sc[0]));
+        S[1] = S[1] + __fma_rn(md[1], d[1], __ldcg(&Sc[1]));
+        S[2] = S[2] + __fma_rn(md[2], d[2], __ldcg(&Sc[2]));
+        S[3] = S[3] + __fma_rn(md[0], d[1], __ldcg(&Sc[3]));
+        S[4] = S[4] + __fma_rn(md[0], d[2], __ldcg(&Sc[4]));
+        S[5] = S[5] + __fma_rn(md[1], d[2], __ldcg(&Sc[5]));
     }
-    write_records(A, fr, node, level, false, cf, nc, lo, hi, M, com, Q, hmax, cen, ci);
+    double com[3], Q[6];
+    moments_finish(M, s, S, cen, com, Q);
+    write_records(A, fr, node, level, false, cf, nc, lo, hi, M, com, Q, S, hmax, cen, ci);
 }
 
 // Leaves of every level (one thread per leaf), then internal nodes one level
@@ -802,6 +831,8 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->nQ, double, 6 * (size_t)nn);
     ALLOC(t->nhmax, double, nn);
     int *lflag, *lpre, *leaves, *d_nn;
+    double *nS;
+    ALLOC(nS, double, 6 * (size_t)nn);
     ALLOC(lflag, int, nn);
     ALLOC(lpre, int, nn + 1);
     ALLOC(leaves, int, nn);
@@ -836,6 +867,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.ncom = t->ncom;
     A.nQ = t->nQ;
     A.nhmax = t->nhmax;
+    A.nS = nS;
     A.pw = t->pw;
     A.pc = t->pc;
     A.leaves = leaves;
@@ -847,6 +879,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         k_internal_moments<<<grid_for(e - b, 128), 128, 0, s>>>(A, b, e);
         t->n_launch += 1;
     }
+    dev_free(t, nS, s);
     dev_free(t, lflag, s);
     dev_free(t, lpre, s);
     dev_free(t, leaves, s);

@@ -88,8 +88,14 @@ def test_moments_against_flat_sums(small):
         np.testing.assert_allclose(mf[i, 1:4], com, rtol=0, atol=1e-13)
         Qo = mf[i, 4:10]
         Qf = np.array([Q[0, 0], Q[1, 1], Q[2, 2], Q[0, 1], Q[0, 2], Q[1, 2]])
-        np.testing.assert_allclose(Qo, Qf, rtol=0, atol=1e-11 * max((m[sl] * s2).sum(), 1e-300))
-        assert abs(Qo[0] + Qo[1] + Qo[2]) <= 1e-11 * max((m[sl] * s2).sum(), 1e-300)
+        # Q is summed about the cell centre c and moved to the centre of mass
+        # (parallel-axis theorem): the shift cancels down from the second
+        # moment about c, so rounding is bounded by a few ulps of
+        # sum m |x - c|^2 <= M (sqrt(3)/2 L)^2, L the cell side.
+        L = t.L0 * 2.0 ** -int(nd[i, 0])
+        tol = 1e-11 * (m[sl] * s2).sum() + 1e-14 * M * L * L
+        np.testing.assert_allclose(Qo, Qf, rtol=0, atol=max(tol, 1e-300))
+        assert abs(Qo[0] + Qo[1] + Qo[2]) <= max(tol, 1e-300)
         assert mf[i, 10] == h[sl].max()
         np.testing.assert_array_equal(nd[i, 9:12], q[sl].min(0))
         np.testing.assert_array_equal(nd[i, 12:15], q[sl].max(0))
