@@ -789,12 +789,14 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         k_oct_root<<<(C + 127) / 128, 128, 0, s>>>(t->d_off, C, t->nfirst, t->ncount, t->nparent, t->nlevel,
                                                    t->ncloud, t->d_lvl);
         t->n_launch += 1 + (SFG_LMAX + 1) * 5;
+        // grid-stride over a level (its size is only known on the device)
+        const int og = std::min(grid_for(cap, BT), num_sms() * 4);
         for (int level = 0; level <= SFG_LMAX; level++) {
-            k_oct_count<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+            k_oct_count<<<og, BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, tmp, t->d_status);
             scan_range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
                        t->d_lvl + level + 1, scr, s);
-            k_oct_write<<<grid_for(cap, BT), BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+            k_oct_write<<<og, BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, t->nparent, t->nchild_first, t->nnchild,
                                                          t->nlevel, t->ncloud, tmpo, t->d_status);
         }

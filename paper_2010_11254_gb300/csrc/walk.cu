@@ -1094,7 +1094,9 @@ struct EvalSmem {
     // the group's targets, for pairs evaluated off their own lane
     float4 gT[32];  // (ox, oy, oz, h)
     float4 gU[32];  // (1/h, sink flag, target rank bits, h^2)
-    float4 sAcc[32]; // per-target sums of the softened pairs: (a, phi)
+    float4 sAcc[32]; // per-target sums of the softened pairs: forward (a, phi), adjoint (-dL/dx_i, -)
+    float4 gC[32];   // adjoint: the targets' cotangents (cot_a, cot_phi)
+    float4 sS[32];   // adjoint: per-source sums of the softened pairs of a tile (dL/dx_j, dL/dm_j)
     unsigned short sq[1024]; // softened pairs of a tile: target | source << 5
 };
 
@@ -1322,6 +1324,121 @@ __device__ __forceinline__ void fwd_p2p_defer(EvalSmem &S, int cnt, const Tgt &T
     __syncwarp();
 }
 
+// Adjoint of a softened-list tile: the systolic loop of vjp_p2p_newt with
+// the Newtonian kernel for every pair; a pair inside max(h_i, h_j) (the self
+// pair included) contributes nothing there and is flagged instead.  The
+// flagged pairs of the warp are then evaluated 32 at a time with the full
+// pair rule and its tidal tensor, their target-side terms summed per target
+// and their source-side terms per source in shared memory; each lane adds
+// its source's sums to the systolic ones before the FP64 atomics.
+__device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, int cnt, const Tgt &T, float c0,
+                                              float c1, float c2, float cf, float &gx, float &gy, float &gz,
+                                              int lane)
+{
+    const int tp = T.tp, base = T.slice * tp;
+    const int nxt = (T.tl + 1) & (tp - 1);
+    const float ht2 = T.h * T.h;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, am = 0.f;
+    unsigned mask = 0u;
+    for (int jj = 0; jj < tp; jj++) {
+        const int k = base + ((T.tl + jj) & (tp - 1));
+        if (T.has && k < cnt) {
+            float4 p = S.tP[k];
+            float hj2 = S.tB[k];
+            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool sft = r2 < fmaxf(ht2, hj2);
+            if (sft) mask |= 1u << k;
+            float rinv = rsqrtf(sft ? 1.f : r2);
+            float ri2 = rinv * rinv;
+            float K = ri2 * rinv;
+            float R = -3.f * K * ri2;
+            float m = sft ? 0.f : p.w;
+            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
+            float mK = m * K;
+            float sv = m * fmaf(R, cd, cf * K);
+            float l0 = fmaf(mK, c0, sv * dx);
+            float l1 = fmaf(mK, c1, sv * dy);
+            float l2 = fmaf(mK, c2, sv * dz);
+            a0 += l0;
+            a1 += l1;
+            a2 += l2;
+            am += sft ? 0.f : fmaf(K, cd, -rinv * cf);
+            gx -= l0;
+            gy -= l1;
+            gz -= l2;
+        }
+        a0 = __shfl_sync(FULL, a0, nxt, tp);
+        a1 = __shfl_sync(FULL, a1, nxt, tp);
+        a2 = __shfl_sync(FULL, a2, nxt, tp);
+        am = __shfl_sync(FULL, am, nxt, tp);
+    }
+    int total;
+    int at = warp_excl(__popc(mask), lane, total);
+    const int ks = base + T.tl; // the source whose sums this lane holds
+    if (total > 0) {
+        S.sS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        while (mask) {
+            const int k = __ffs(mask) - 1;
+            mask &= mask - 1;
+            S.sq[at++] = (unsigned short)(T.tl | (k << 5));
+        }
+        __syncwarp();
+        for (int b = 0; b < total; b += 32) {
+            if (b + lane < total) {
+                const unsigned e = S.sq[b + lane];
+                const int t = e & 31, k = e >> 5;
+                const float4 tg = S.gT[t], tu = S.gU[t], tc = S.gC[t];
+                const float4 p = S.tP[k], hh = S.tA[k];
+                if (__float_as_int(hh.z) != __float_as_int(tu.z)) { // not the self pair
+                    float dx = p.x - tg.x, dy = p.y - tg.y, dz = p.z - tg.z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    // pair rule (Sec. 2.2.1), as in the forward
+                    bool sink = tu.y != 0.f || hh.w != 0.f;
+                    bool tbig = tg.w >= hh.x;
+                    float ha = tbig ? tg.w : hh.x, hainv = tbig ? tu.x : hh.y;
+                    float hb = sink ? ha : (tbig ? hh.x : tg.w), hbinv = sink ? hainv : (tbig ? hh.y : tu.x);
+                    float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                    float r = r2 * rinv;
+                    float K1, P1, R1, K2, P2, R2;
+                    soft_KPR(r, rinv, ha, hainv, K1, P1, R1);
+                    soft_KPR(r, rinv, hb, hbinv, K2, P2, R2);
+                    float K = 0.5f * (K1 + K2), Pp = 0.5f * (P1 + P2), R = 0.5f * (R1 + R2);
+                    float m = p.w;
+                    float cd = fmaf(tc.x, dx, fmaf(tc.y, dy, tc.z * dz));
+                    float mK = m * K;
+                    float sv = m * fmaf(R, cd, tc.w * K);
+                    float l0 = fmaf(mK, tc.x, sv * dx);
+                    float l1 = fmaf(mK, tc.y, sv * dy);
+                    float l2 = fmaf(mK, tc.z, sv * dz);
+                    atomicAdd(&S.sS[k].x, l0);
+                    atomicAdd(&S.sS[k].y, l1);
+                    atomicAdd(&S.sS[k].z, l2);
+                    atomicAdd(&S.sS[k].w, fmaf(K, cd, Pp * tc.w));
+                    atomicAdd(&S.sAcc[t].x, -l0);
+                    atomicAdd(&S.sAcc[t].y, -l1);
+                    atomicAdd(&S.sAcc[t].z, -l2);
+                }
+            }
+        }
+        __syncwarp();
+        if (ks < cnt) { // padded lanes carry source sums too
+            const float4 v = S.sS[ks];
+            a0 += v.x;
+            a1 += v.y;
+            a2 += v.z;
+            am += v.w;
+        }
+    }
+    if (ks < cnt && __float_as_int(S.tA[ks].z) >= 0) {
+        double *dst = P.gpart + 4 * (size_t)__float_as_int(S.tA[ks].z);
+        if (a0 != 0.f) atomicAdd(dst, (double)a0);
+        if (a1 != 0.f) atomicAdd(dst + 1, (double)a1);
+        if (a2 != 0.f) atomicAdd(dst + 2, (double)a2);
+        if (am != 0.f) atomicAdd(dst + 3, (double)am);
+    }
+}
+
 // This item's share of one P2P list: nr ranges holding np particles.
 template <int MODE, bool NEWT>
 __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, const Tgt &T, const int2 *rr, int nr,
@@ -1372,7 +1489,7 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
             else if (T.has) fwd_p2p_newt(S, c, T, ax, ay, az, phi);
         } else {
             stage_p2p(P, S, c, qh, qoff, T, lane);
-            if (MODE == MODE_VJP) vjp_p2p(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            if (MODE == MODE_VJP) vjp_p2p_defer(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
             else fwd_p2p_defer(S, c, T, ax, ay, az, phi, lane);
         }
         __syncwarp();
@@ -1400,6 +1517,7 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     if (T.slice == 0) {
         S.gT[T.tl] = make_float4(T.ox, T.oy, T.oz, T.h);
         S.gU[T.tl] = make_float4(T.hinv, T.sink ? 1.f : 0.f, __int_as_float(T.r), T.h * T.h);
+        if (MODE == MODE_VJP) S.gC[T.tl] = make_float4(c0, c1, c2, cf);
     }
     S.sAcc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
@@ -1420,7 +1538,7 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     const int2 *lr = P.lr + P.lro[g];
     eval_p2p_list<MODE, false>(P, S, T, lr, nls, nps, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
     eval_p2p_list<MODE, true>(P, S, T, lr + nls, nln, npn, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
-    if (MODE == MODE_EVAL && T.has && T.slice == 0) {
+    if (T.has && T.slice == 0) { // the deferred softened pairs' target-side sums
         const float4 v = S.sAcc[T.tl];
         ax += v.x;
         ay += v.y;
@@ -1589,44 +1707,49 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams 
 }
 
 // Work items from the counted list sizes: the sliced iteration count of a
-// group (P2M + P2P sources x T'/32) plus a walk term; groups above SPLIT_ITERS
-// are cut into up to KMAX items, while the partial-sum slot pool lasts.
-constexpr int SPLIT_ITERS = 4096;
+// group (P2M, softened P2P and Newtonian P2P sources x T'/32, each weighted
+// by its relative cost in quarters: wt = (P2M, softened, Newtonian, walk
+// term)) plus a walk term; groups above the split size are cut into up to
+// KMAX items, while the partial-sum slot pool lasts.
+constexpr int SPLIT_ITERS = 1024;
+constexpr int SPLIT_PER_WARP = 8; // items per resident warp's share, at least
 constexpr int KMAX = 32;
 constexpr int PSLOTS = 65536;
 
-__device__ inline long long group_iters(const int *cnt, int tc, int g)
+__device__ inline long long group_iters(const int *cnt, int tc, int g, int4 wt)
 {
     int tp = 1;
     while (tp < tc) tp <<= 1;
     const int *c = cnt + NCNT * (size_t)g;
-    long long src = (long long)c[0] + c[2] + c[4];
-    return src * tp / 32 + ((long long)c[0] + c[1] + c[3]) / 4 + 32;
+    long long src = (long long)wt.x * c[0] + (long long)wt.y * c[2] + (long long)wt.z * c[4];
+    return src * tp / 128 + ((long long)c[0] + c[1] + c[3]) * wt.w / 16 + 32;
 }
 
 // Total estimated cost of all groups (one 64-bit atomic per warp).
-__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, unsigned long long *total)
+__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
+                             unsigned long long *total)
 {
     int ng = *d_ngroups;
     unsigned long long acc = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        acc += (unsigned long long)group_iters(cnt, gtab[g].y, g);
+        acc += (unsigned long long)group_iters(cnt, gtab[g].y, g, wt);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
 }
 
-// Split size: at least SPLIT_ITERS, and at least a third of one resident
-// warp's share of the total, so the split groups need at most ~6 slots per
-// resident warp (the slot pool holds PSLOTS) and every item stays small next
-// to a warp's share (longest-first scheduling then balances the rest).
-__global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngroups,
+// Split size: at least SPLIT_ITERS, and at least 1/SPLIT_PER_WARP of one
+// resident warp's share of the total, so the split groups need at most ~2
+// SPLIT_PER_WARP slots per resident warp (the slot pool holds PSLOTS) and
+// every item stays small next to a warp's share (longest-first scheduling
+// then balances the rest).
+__global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
                               const unsigned long long *total, long long warps, int *kcnt, int *is_split)
 {
     int ng = *d_ngroups;
-    long long C = (long long)(*total / (unsigned long long)(3 * warps));
+    long long C = (long long)(*total / (unsigned long long)(SPLIT_PER_WARP * warps));
     if (C < SPLIT_ITERS) C = SPLIT_ITERS;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        long long iters = group_iters(cnt, gtab[g].y, g);
+        long long iters = group_iters(cnt, gtab[g].y, g, wt);
         long long k = (iters + C - 1) / C;
         int K = (int)(k < 1 ? 1 : (k > KMAX ? KMAX : k));
         kcnt[g] = K;
@@ -1636,18 +1759,19 @@ __global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngr
 
 // Longest first: items are bucketed by log2 of their estimated cost and the
 // buckets are issued from the most to the least expensive.
-__device__ inline int cost_bucket(const int *cnt, const int2 *gtab, const int *kcnt, int g)
+__device__ inline int cost_bucket(const int *cnt, const int2 *gtab, const int *kcnt, int g, int4 wt)
 {
-    long long c = group_iters(cnt, gtab[g].y, g) / kcnt[g];
+    long long c = group_iters(cnt, gtab[g].y, g, wt) / kcnt[g];
     int b = 63 - __clzll(c > 1 ? c : 1);
     return 31 - min(b, 31);
 }
 
-__global__ void k_item_hist(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *hist)
+__global__ void k_item_hist(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int4 wt,
+                            int *hist)
 {
     int ng = *d_ngroups;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        atomicAdd(&hist[cost_bucket(cnt, gtab, kcnt, g)], kcnt[g]);
+        atomicAdd(&hist[cost_bucket(cnt, gtab, kcnt, g, wt)], kcnt[g]);
 }
 
 __global__ void k_item_scan(int *hist)
@@ -1662,13 +1786,13 @@ __global__ void k_item_scan(int *hist)
     }
 }
 
-__global__ void k_item_fill(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int *cursor,
-                            int2 *items)
+__global__ void k_item_fill(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int4 wt,
+                            int *cursor, int2 *items)
 {
     int ng = *d_ngroups;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         int K = kcnt[g];
-        int base = atomicAdd(&cursor[cost_bucket(cnt, gtab, kcnt, g)], K);
+        int base = atomicAdd(&cursor[cost_bucket(cnt, gtab, kcnt, g, wt)], K);
         for (int k = 0; k < K; k++) items[base + k] = make_int2(g, k);
     }
 }
@@ -2024,32 +2148,40 @@ static void count_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
     P.dbg_counts = nullptr;
 }
 
+// Relative costs (in quarters) of a P2M, softened P2P and Newtonian P2P
+// source per target lane, and of the walk term: evaluation from stored lists
+// (forward, adjoint; measured per interaction on a clumpy cloud) and the
+// walking evaluation (unit weights).
+constexpr int4 WT_EVAL = {7, 8, 4, 1};
+constexpr int4 WT_VJP = {20, 6, 4, 1};
+constexpr int4 WT_WALK = {4, 4, 4, 4};
+
 // Cut the heavy groups into work items, from the list sizes.
-static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int4 wt)
 {
     const int n = (int)t->n, BT = 256;
     const int *d_ng = P.d_ngroups;
     cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s);
     unsigned long long *total = t->d_counters + 7;
     cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
-    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, total);
+    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total);
     const long long warps = (long long)num_sms() * WALK_MINB * WALK_WARPS;
-    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, total, warps, w.kcnt, w.is_split);
+    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total, warps, w.kcnt, w.is_split);
     scan_exclusive(w.is_split, w.soff, d_ng, n, nullptr, nullptr, w.scr, s);
     k_item_cap<<<grid_for(n, BT), BT, 0, s>>>(w.soff, d_ng, w.kcnt);
     scan_exclusive(w.kcnt, w.ioff, d_ng, n, nullptr, nullptr, w.scr, s);
     cudaMemsetAsync(w.gdone, 0, sizeof(int) * (size_t)n, s);
     cudaMemsetAsync(w.hist, 0, 32 * sizeof(int), s);
-    k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, w.hist);
+    k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, wt, w.hist);
     k_item_scan<<<1, 32, 0, s>>>(w.hist);
-    k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, w.hist, w.items);
+    k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, wt, w.hist, w.items);
     t->n_launch += 1 + 3 + 3 + 3;
 }
 
 static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
 {
     count_lists(t, w, P, s);
-    items_from_counts(t, w, P, s);
+    items_from_counts(t, w, P, s, WT_WALK);
 }
 
 // Stored lists are used unless disabled, in the all-FP64 mode, or while the
@@ -2176,7 +2308,7 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
         if (rc) return rc;
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
-        items_from_counts(t, w, P, s);
+        items_from_counts(t, w, P, s, WT_EVAL);
     } else {
         t->lists_ok = false; // the counting walk below overwrites their sizes
         make_items(t, w, P, s);
@@ -2358,7 +2490,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
                 rc = remember_active(t, active, n_active, s);
                 if (rc) return rc;
             }
-            items_from_counts(t, w, P, s);
+            items_from_counts(t, w, P, s, WT_VJP);
         } else {
             t->lists_ok = false;
             make_items(t, w, P, s);
