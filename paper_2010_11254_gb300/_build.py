@@ -2,7 +2,11 @@
 
 build.cu (frame, keys, sort, octree, FP64 moments) is compiled without FMA
 contraction so that its FP64 results are reproducible operation by operation;
-the walk/eval file may contract FP32 multiply-adds.
+the walk/eval file may contract FP32 multiply-adds, and its FP32 arithmetic
+flushes denormals and uses the hardware reciprocal square root and
+approximate division (the FP32 pair terms never come near the denormal
+range: positions are offsets of at most 2^22 half-cells and separations of
+coincident points are handled before any division).
 
 Environment: SFG_NVCC_EXTRA adds nvcc flags (e.g. -D defines) and
 SFG_LIB_NAME names the output library (default libsfg.so), so that builds
@@ -26,7 +30,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", INCLUDE]
 SOURCES = {
     "build.cu": ["-fmad=false"],
-    "walk.cu": [],
+    "walk.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "api.cu": [],
 }
 
