@@ -352,16 +352,32 @@ __global__ void k_pack(const double *pos, const double *mass, const double *soft
 }
 
 // --------------------------------------------------------------- octree ----
-// First index k in [lo, hi) with child digit(key[k]) >= d (digits are
-// non-decreasing inside one node's range).
-__device__ inline int lower_digit(const uint64_t *key, int lo, int hi, int cshift, uint32_t d)
+// Child boundaries of the node [f, e) at child shift cshift: s[d] = first
+// index whose child digit is >= d (s[0] = f, s[8] = e).  The seven binary
+// searches run in lockstep, so their loads overlap instead of chaining.
+__device__ inline void digit_bounds(const uint64_t *key, int f, int e, int cshift, int s[9])
 {
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (((key[mid] >> cshift) & 7u) < d) lo = mid + 1;
-        else hi = mid;
+    int lo[7], hi[7];
+#pragma unroll
+    for (int d = 0; d < 7; d++) {
+        lo[d] = f;
+        hi[d] = e;
     }
-    return lo;
+    const int n = e - f;
+    for (int it = 0; it < 32 && (1 << it) <= n; it++) {
+#pragma unroll
+        for (int d = 0; d < 7; d++) {
+            if (lo[d] < hi[d]) {
+                int mid = (lo[d] + hi[d]) >> 1;
+                if (((key[mid] >> cshift) & 7u) < (uint32_t)(d + 1)) lo[d] = mid + 1;
+                else hi[d] = mid;
+            }
+        }
+    }
+    s[0] = f;
+#pragma unroll
+    for (int d = 0; d < 7; d++) s[d + 1] = lo[d];
+    s[8] = e;
 }
 
 // One root per cloud: node c covers cloud c's sorted range.
@@ -393,13 +409,10 @@ __global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int 
         int f = nfirst[node], c = ncount[node];
         int nch = 0;
         if (c > leaf_size && level < SFG_LMAX) {
-            int cshift = 3 * (SFG_LMAX - level - 1);
-            int prev = f;
-            for (uint32_t d = 1; d <= 8; d++) {
-                int s = d < 8 ? lower_digit(key, prev, f + c, cshift, d) : f + c;
-                if (s > prev) nch++;
-                prev = s;
-            }
+            int sb[9];
+            digit_bounds(key, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
+#pragma unroll
+            for (int d = 0; d < 8; d++) nch += sb[d + 1] > sb[d];
         }
         tmp[node - b] = nch;
     }
@@ -418,25 +431,25 @@ __global__ void k_oct_write(const uint64_t *key, const int *lvl, int level, int 
             nnchild[node] = 0;
             continue;
         }
-        int cshift = 3 * (SFG_LMAX - level - 1);
         int cf = next + tmp_off[node - b];
-        int k = 0, prev = f;
-        for (uint32_t d = 1; d <= 8; d++) {
-            int s = d < 8 ? lower_digit(key, prev, f + c, cshift, d) : f + c;
-            if (s > prev) {
+        int sb[9];
+        digit_bounds(key, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
+        int k = 0;
+        const int cl = ncloud[node];
+        for (int d = 0; d < 8; d++) {
+            if (sb[d + 1] > sb[d]) {
                 int id = cf + k;
                 if (id < cap) {
-                    nfirst[id] = prev;
-                    ncount[id] = s - prev;
+                    nfirst[id] = sb[d];
+                    ncount[id] = sb[d + 1] - sb[d];
                     nparent[id] = node;
                     nlevel[id] = level + 1;
-                    ncloud[id] = ncloud[node];
+                    ncloud[id] = cl;
                 } else {
                     atomicOr(status, ST_NODECAP);
                 }
                 k++;
             }
-            prev = s;
         }
         nchild_first[node] = cf;
         nnchild[node] = k;

@@ -194,40 +194,51 @@ __device__ __forceinline__ void pair_supports(const Tgt &T, const float4 &hh, fl
 }
 
 // ------------------------------------------------------- forward tiles ----
+// One P2M interaction: monopole a = M d / r^3, phi = -M / r, plus the
+// quadrupole a_Q = -Q d / r^5 + 5/2 (d.Qd) d / r^7, phi_Q = -(d.Qd) / (2 r^5).
+template <bool QUAD, class SM>
+__device__ __forceinline__ void fwd_p2m_step(const SM &S, int k, const Tgt &T, float &ax, float &ay, float &az,
+                                             float &pt)
+{
+    float4 p = S.tP[k];
+    float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float rinv = rsqrtf(r2);
+    float ri2 = rinv * rinv;
+    float Mri3 = p.w * (ri2 * rinv);
+    if (QUAD) {
+        float4 q = S.tA[k];
+        float qyz = S.tB[k];
+        float qzz = -(q.x + q.y);
+        float Qd0 = fmaf(q.x, dx, fmaf(q.z, dy, q.w * dz));
+        float Qd1 = fmaf(q.z, dx, fmaf(q.y, dy, qyz * dz));
+        float Qd2 = fmaf(q.w, dx, fmaf(qyz, dy, qzz * dz));
+        float ri5 = rinv * ri2 * ri2;
+        float t = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2)) * ri5; // d.Qd / r^5
+        float c = fmaf(t, 2.5f * ri2, Mri3);
+        ax = fmaf(c, dx, fmaf(-ri5, Qd0, ax));
+        ay = fmaf(c, dy, fmaf(-ri5, Qd1, ay));
+        az = fmaf(c, dz, fmaf(-ri5, Qd2, az));
+        pt = fmaf(-p.w, rinv, fmaf(-0.5f, t, pt));
+    } else {
+        ax = fmaf(Mri3, dx, ax);
+        ay = fmaf(Mri3, dy, ay);
+        az = fmaf(Mri3, dz, az);
+        pt = fmaf(-p.w, rinv, pt);
+    }
+}
+
 template <bool QUAD, class SM>
 __device__ __forceinline__ void fwd_p2m(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
                                         double &phi)
 {
     float pt = 0.f;
+    if (T.R == 1 && cnt == 32) {
+#pragma unroll 4
+        for (int k = 0; k < 32; k++) fwd_p2m_step<QUAD>(S, k, T, ax, ay, az, pt);
+    } else {
 #pragma unroll 2
-    for (int k = T.slice; k < cnt; k += T.R) {
-        float4 p = S.tP[k];
-        float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float rinv = rsqrtf(r2);
-        float ri2 = rinv * rinv;
-        float ri3 = ri2 * rinv;
-        if (QUAD) {
-            float4 q = S.tA[k];
-            float qyz = S.tB[k];
-            float qzz = -(q.x + q.y);
-            float Qd0 = fmaf(q.x, dx, fmaf(q.z, dy, q.w * dz));
-            float Qd1 = fmaf(q.z, dx, fmaf(q.y, dy, qyz * dz));
-            float Qd2 = fmaf(q.w, dx, fmaf(qyz, dy, qzz * dz));
-            float dQd = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2));
-            float ri5 = ri3 * ri2;
-            float c = fmaf(2.5f * dQd * ri5, ri2, p.w * ri3);
-            ax = fmaf(c, dx, fmaf(-ri5, Qd0, ax));
-            ay = fmaf(c, dy, fmaf(-ri5, Qd1, ay));
-            az = fmaf(c, dz, fmaf(-ri5, Qd2, az));
-            pt = fmaf(-p.w, rinv, fmaf(-0.5f * dQd, ri5, pt));
-        } else {
-            float c = p.w * ri3;
-            ax = fmaf(c, dx, ax);
-            ay = fmaf(c, dy, ay);
-            az = fmaf(c, dz, az);
-            pt = fmaf(-p.w, rinv, pt);
-        }
+        for (int k = T.slice; k < cnt; k += T.R) fwd_p2m_step<QUAD>(S, k, T, ax, ay, az, pt);
     }
     phi += (double)pt;
 }
@@ -272,6 +283,95 @@ __device__ __forceinline__ void fwd_p2p(const SM &S, int cnt, const Tgt &T, floa
 
 // ------------------------------------------------------- adjoint tiles ----
 
+// One P2M tile of the adjoint for a fixed slice width TP.  With d = com - x_i,
+// q = d.Qd, cd = c.d (c, cf the target's cotangents), the derivative of
+// L = c.a + cf phi with respect to d is
+//   gd = (M/r^3 + 5/2 q/r^7) c - Q c / r^5 + (5 cd/r^7 - cf/r^5) Q d
+//      + [M/r^3 (cf - 3 cd/r^2) + (5 c.Qd + q (5/2 cf - 35/2 cd/r^2)) / r^7] d
+// (the source's centre of mass gets +gd, the target -gd); dL/dM = cd/r^3 -
+// cf/r; dL/dQ_ab = (w_a d_b + w_b d_a)/2 with w = (5/2 cd/r^7 - cf/(2 r^5)) d
+// - c/r^5 (the off-diagonal sums are kept doubled and halved once at the end).
+template <bool QUAD, class SM>
+__device__ __forceinline__ void vjp_p2m_tile(const WalkParams &P, const SM &S, int cnt, const Tgt &T, float c0,
+                                             float c1, float c2, float cf, float &gx, float &gy, float &gz)
+{
+    const int TP = T.tp, base = T.slice * TP;
+    const int nxt = (T.tl + 1) & (TP - 1);
+    const float ncf = -cf, cf25 = 2.5f * cf;
+    float acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; q++) acc[q] = 0.f;
+    for (int j = 0; j < TP; j++) {
+        const int k = base + ((T.tl + j) & (TP - 1));
+        if (T.has && k < cnt) {
+            float4 p = S.tP[k];
+            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float rinv = rsqrtf(r2);
+            float ri2 = rinv * rinv, ri3 = ri2 * rinv;
+            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
+            float Mri3 = p.w * ri3;
+            acc[0] = fmaf(cd, ri3, fmaf(ncf, rinv, acc[0]));
+            float gd0, gd1, gd2;
+            if (QUAD) {
+                float ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+                float4 qa = S.tA[k]; // Qxx Qyy Qxy Qxz
+                float qyz = S.tB[k];
+                float qzz = -(qa.x + qa.y);
+                float Qd0 = fmaf(qa.x, dx, fmaf(qa.z, dy, qa.w * dz));
+                float Qd1 = fmaf(qa.z, dx, fmaf(qa.y, dy, qyz * dz));
+                float Qd2 = fmaf(qa.w, dx, fmaf(qyz, dy, qzz * dz));
+                float Qc0 = fmaf(qa.x, c0, fmaf(qa.z, c1, qa.w * c2));
+                float Qc1 = fmaf(qa.z, c0, fmaf(qa.y, c1, qyz * c2));
+                float Qc2 = fmaf(qa.w, c0, fmaf(qyz, c1, qzz * c2));
+                float q = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2));
+                float cQd = fmaf(c0, Qd0, fmaf(c1, Qd1, c2 * Qd2));
+                float kc = fmaf(2.5f * q, ri7, Mri3);
+                float kq = fmaf(5.f * cd, ri7, ncf * ri5);
+                float kd = fmaf(ri7, fmaf(q, fmaf(-17.5f * cd, ri2, cf25), 5.f * cQd),
+                                Mri3 * fmaf(-3.f * cd, ri2, cf));
+                gd0 = fmaf(kc, c0, fmaf(-ri5, Qc0, fmaf(kq, Qd0, kd * dx)));
+                gd1 = fmaf(kc, c1, fmaf(-ri5, Qc1, fmaf(kq, Qd1, kd * dy)));
+                gd2 = fmaf(kc, c2, fmaf(-ri5, Qc2, fmaf(kq, Qd2, kd * dz)));
+                float sQ = 0.5f * kq;
+                float w0 = fmaf(sQ, dx, -ri5 * c0), w1 = fmaf(sQ, dy, -ri5 * c1), w2 = fmaf(sQ, dz, -ri5 * c2);
+                acc[4] = fmaf(w0, dx, acc[4]);
+                acc[5] = fmaf(w1, dy, acc[5]);
+                acc[6] = fmaf(w2, dz, acc[6]);
+                acc[7] = fmaf(w0, dy, fmaf(w1, dx, acc[7]));
+                acc[8] = fmaf(w0, dz, fmaf(w2, dx, acc[8]));
+                acc[9] = fmaf(w1, dz, fmaf(w2, dy, acc[9]));
+            } else {
+                // monopole: a = M d / r^3, phi = -M / r
+                float kd = Mri3 * fmaf(-3.f * cd, ri2, cf);
+                gd0 = fmaf(Mri3, c0, kd * dx);
+                gd1 = fmaf(Mri3, c1, kd * dy);
+                gd2 = fmaf(Mri3, c2, kd * dz);
+            }
+            acc[1] += gd0;
+            acc[2] += gd1;
+            acc[3] += gd2;
+            gx -= gd0;
+            gy -= gd1;
+            gz -= gd2;
+        }
+#pragma unroll
+        for (int q = 0; q < (QUAD ? 10 : 4); q++) acc[q] = __shfl_sync(FULL, acc[q], nxt, TP);
+    }
+    if (QUAD) {
+        acc[7] *= 0.5f;
+        acc[8] *= 0.5f;
+        acc[9] *= 0.5f;
+    }
+    const int k = base + T.tl;
+    if (k < cnt && S.tN[k] >= 0) {
+        double *dst = P.gnode + 10 * (size_t)S.tN[k];
+#pragma unroll
+        for (int q = 0; q < (QUAD ? 10 : 4); q++)
+            if (acc[q] != 0.f) atomicAdd(dst + q, (double)acc[q]);
+    }
+}
+
 // Target side accumulates -dL/dd in registers.  Source side: within each
 // slice of T' lanes, step j pairs lane t with source (t + j) mod T' of the
 // slice's block of T' sources, and every lane hands its running source
@@ -282,72 +382,7 @@ template <bool QUAD, class SM>
 __device__ __forceinline__ void vjp_p2m(const WalkParams &P, const SM &S, int cnt, const Tgt &T, float c0,
                                         float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
-    const int tp = T.tp, base = T.slice * tp;
-    const int nxt = (T.tl + 1) & (tp - 1);
-    float acc[10];
-#pragma unroll
-    for (int q = 0; q < 10; q++) acc[q] = 0.f;
-    for (int j = 0; j < tp; j++) {
-        const int k = base + ((T.tl + j) & (tp - 1));
-        if (T.has && k < cnt) {
-            float4 p = S.tP[k];
-            float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float rinv = rsqrtf(r2);
-            float ri2 = rinv * rinv, ri3 = ri2 * rinv, ri5 = ri3 * ri2;
-            float M = p.w;
-            float cd = fmaf(c0, dx, fmaf(c1, dy, c2 * dz));
-            // monopole: a = M d ri3, phi = -M ri
-            float s1 = M * ri3;                           // coefficient of c
-            float s2 = M * fmaf(-3.f * cd, ri5, cf * ri3); // coefficient of d
-            float gd0 = fmaf(s1, c0, s2 * dx), gd1 = fmaf(s1, c1, s2 * dy), gd2 = fmaf(s1, c2, s2 * dz);
-            acc[0] += fmaf(cd, ri3, -cf * rinv);
-            if (QUAD) {
-                float4 q = S.tA[k];
-                float qyz = S.tB[k];
-                float qzz = -(q.x + q.y);
-                float Qd0 = fmaf(q.x, dx, fmaf(q.z, dy, q.w * dz));
-                float Qd1 = fmaf(q.z, dx, fmaf(q.y, dy, qyz * dz));
-                float Qd2 = fmaf(q.w, dx, fmaf(qyz, dy, qzz * dz));
-                float Qc0 = fmaf(q.x, c0, fmaf(q.z, c1, q.w * c2));
-                float Qc1 = fmaf(q.z, c0, fmaf(q.y, c1, qyz * c2));
-                float Qc2 = fmaf(q.w, c0, fmaf(qyz, c1, qzz * c2));
-                float dQd = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2));
-                float cQd = fmaf(c0, Qd0, fmaf(c1, Qd1, c2 * Qd2));
-                float ri7 = ri5 * ri2, ri9 = ri7 * ri2;
-                // d/dd of c.(-Q d ri5 + 2.5 dQd d ri7) + cf (-0.5 dQd ri5)
-                float aQ = -ri5;                                                          // of Q c
-                float aQd = 5.f * cd * ri7 - cf * ri5;                                    // of Q d
-                float ad = 5.f * cQd * ri7 - 17.5f * dQd * cd * ri9 + 2.5f * cf * dQd * ri7; // of d
-                float ac = 2.5f * dQd * ri7;                                              // of c
-                gd0 += aQ * Qc0 + aQd * Qd0 + ad * dx + ac * c0;
-                gd1 += aQ * Qc1 + aQd * Qd1 + ad * dy + ac * c1;
-                gd2 += aQ * Qc2 + aQd * Qd2 + ad * dz + ac * c2;
-                float sQ = 2.5f * cd * ri7 - 0.5f * cf * ri5;
-                acc[4] += fmaf(-c0 * dx, ri5, sQ * dx * dx);
-                acc[5] += fmaf(-c1 * dy, ri5, sQ * dy * dy);
-                acc[6] += fmaf(-c2 * dz, ri5, sQ * dz * dz);
-                acc[7] += fmaf(-0.5f * (c0 * dy + dx * c1), ri5, sQ * dx * dy);
-                acc[8] += fmaf(-0.5f * (c0 * dz + dx * c2), ri5, sQ * dx * dz);
-                acc[9] += fmaf(-0.5f * (c1 * dz + dy * c2), ri5, sQ * dy * dz);
-            }
-            acc[1] += gd0;
-            acc[2] += gd1;
-            acc[3] += gd2;
-            gx -= gd0;
-            gy -= gd1;
-            gz -= gd2;
-        }
-#pragma unroll
-        for (int q = 0; q < (QUAD ? 10 : 4); q++) acc[q] = __shfl_sync(FULL, acc[q], nxt, tp);
-    }
-    const int k = base + T.tl;
-    if (k < cnt && S.tN[k] >= 0) {
-        double *dst = P.gnode + 10 * (size_t)S.tN[k];
-#pragma unroll
-        for (int q = 0; q < (QUAD ? 10 : 4); q++)
-            if (acc[q] != 0.f) atomicAdd(dst + q, (double)acc[q]);
-    }
+    vjp_p2m_tile<QUAD>(P, S, cnt, T, c0, c1, c2, cf, gx, gy, gz);
 }
 
 template <class SM>
@@ -1156,22 +1191,32 @@ __device__ __forceinline__ void stage_p2p_newt(const WalkParams &P, SM &S, int c
 }
 
 template <class SM>
+__device__ __forceinline__ void fwd_newt_step(const SM &S, int k, const Tgt &T, float &ax, float &ay, float &az,
+                                              float &pt)
+{
+    float4 p = S.tP[k];
+    float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float rinv = rsqrtf(r2);
+    float mr = p.w * rinv;
+    float mr3 = mr * (rinv * rinv);
+    ax = fmaf(mr3, dx, ax);
+    ay = fmaf(mr3, dy, ay);
+    az = fmaf(mr3, dz, az);
+    pt -= mr;
+}
+
+template <class SM>
 __device__ __forceinline__ void fwd_p2p_newt(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
                                              double &phi)
 {
     float pt = 0.f;
+    if (T.R == 1 && cnt == 32) {
+#pragma unroll 4
+        for (int k = 0; k < 32; k++) fwd_newt_step(S, k, T, ax, ay, az, pt);
+    } else {
 #pragma unroll 2
-    for (int k = T.slice; k < cnt; k += T.R) {
-        float4 p = S.tP[k];
-        float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float rinv = rsqrtf(r2);
-        float mr = p.w * rinv;
-        float mr3 = mr * (rinv * rinv);
-        ax = fmaf(mr3, dx, ax);
-        ay = fmaf(mr3, dy, ay);
-        az = fmaf(mr3, dz, az);
-        pt -= mr;
+        for (int k = T.slice; k < cnt; k += T.R) fwd_newt_step(S, k, T, ax, ay, az, pt);
     }
     phi += (double)pt;
 }
@@ -1182,11 +1227,11 @@ template <class SM>
 __device__ __forceinline__ void vjp_p2p_newt(const WalkParams &P, const SM &S, int cnt, const Tgt &T, float c0,
                                              float c1, float c2, float cf, float &gx, float &gy, float &gz, int lane)
 {
-    const int tp = T.tp, base = T.slice * tp;
-    const int nxt = (T.tl + 1) & (tp - 1);
+    const int TP = T.tp, base = T.slice * TP;
+    const int nxt = (T.tl + 1) & (TP - 1);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, am = 0.f;
-    for (int jj = 0; jj < tp; jj++) {
-        const int k = base + ((T.tl + jj) & (tp - 1));
+    for (int jj = 0; jj < TP; jj++) {
+        const int k = base + ((T.tl + jj) & (TP - 1));
         if (T.has && k < cnt) {
             float4 p = S.tP[k];
             float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
@@ -1210,10 +1255,10 @@ __device__ __forceinline__ void vjp_p2p_newt(const WalkParams &P, const SM &S, i
             gy -= l1;
             gz -= l2;
         }
-        a0 = __shfl_sync(FULL, a0, nxt, tp);
-        a1 = __shfl_sync(FULL, a1, nxt, tp);
-        a2 = __shfl_sync(FULL, a2, nxt, tp);
-        am = __shfl_sync(FULL, am, nxt, tp);
+        a0 = __shfl_sync(FULL, a0, nxt, TP);
+        a1 = __shfl_sync(FULL, a1, nxt, TP);
+        a2 = __shfl_sync(FULL, a2, nxt, TP);
+        am = __shfl_sync(FULL, am, nxt, TP);
     }
     const int k = base + T.tl;
     if (k < cnt && S.tN[k] >= 0) {
@@ -1224,6 +1269,7 @@ __device__ __forceinline__ void vjp_p2p_newt(const WalkParams &P, const SM &S, i
         if (am != 0.f) atomicAdd(dst + 3, (double)am);
     }
 }
+
 
 
 // Forward of a softened-list tile.  Every pair first takes the Newtonian
@@ -1335,13 +1381,13 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
                                               float c1, float c2, float cf, float &gx, float &gy, float &gz,
                                               int lane)
 {
-    const int tp = T.tp, base = T.slice * tp;
-    const int nxt = (T.tl + 1) & (tp - 1);
+    const int TP = T.tp, base = T.slice * TP;
+    const int nxt = (T.tl + 1) & (TP - 1);
     const float ht2 = T.h * T.h;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, am = 0.f;
     unsigned mask = 0u;
-    for (int jj = 0; jj < tp; jj++) {
-        const int k = base + ((T.tl + jj) & (tp - 1));
+    for (int jj = 0; jj < TP; jj++) {
+        const int k = base + ((T.tl + jj) & (TP - 1));
         if (T.has && k < cnt) {
             float4 p = S.tP[k];
             float hj2 = S.tB[k];
@@ -1368,10 +1414,10 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
             gy -= l1;
             gz -= l2;
         }
-        a0 = __shfl_sync(FULL, a0, nxt, tp);
-        a1 = __shfl_sync(FULL, a1, nxt, tp);
-        a2 = __shfl_sync(FULL, a2, nxt, tp);
-        am = __shfl_sync(FULL, am, nxt, tp);
+        a0 = __shfl_sync(FULL, a0, nxt, TP);
+        a1 = __shfl_sync(FULL, a1, nxt, TP);
+        a2 = __shfl_sync(FULL, a2, nxt, TP);
+        am = __shfl_sync(FULL, am, nxt, TP);
     }
     int total;
     int at = warp_excl(__popc(mask), lane, total);
@@ -1438,6 +1484,7 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
         if (am != 0.f) atomicAdd(dst + 3, (double)am);
     }
 }
+
 
 // This item's share of one P2P list: nr ranges holding np particles.
 template <int MODE, bool NEWT>
