@@ -94,6 +94,13 @@ def _load():
         lib.sfgo_vjp.restype = ctypes.c_int
         lib.sfgo_vjp.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _f64p, _f64p, _f64p,
                                  _f64p]
+        lib.sfgo_direct_tidal.restype = None
+        lib.sfgo_direct_tidal.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _u8p, ctypes.c_double,
+                                          ctypes.c_int64, _i64p, _f64p]
+        lib.sfgo_tidal_group.restype = ctypes.c_int
+        lib.sfgo_tidal_group.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _f64p]
+        lib.sfgo_tidal_dt.restype = None
+        lib.sfgo_tidal_dt.argtypes = [ctypes.c_int64, _f64p, ctypes.c_double, _f64p]
         lib.sfgo_num_threads.restype = ctypes.c_int
         lib.sfgo_num_threads.argtypes = []
         _lib = lib
@@ -154,6 +161,27 @@ def direct(pos, mass, soft, is_sink=None, targets=None, G: float = 1.0):
     _load().sfgo_direct(n, _p(pos, _f64p), _p(mass, _f64p), _p(soft, _f64p), _p(sink, _u8p), float(G), tg.size,
                         _p(tg, _i64p), _p(acc, _f64p), _p(phi, _f64p))
     return acc, phi
+
+
+def direct_tidal(pos, mass, soft, is_sink=None, targets=None, G: float = 1.0):
+    """FP64 direct-sum tidal tensor T = -grad grad Phi (Sec. 2.2) at the targets,
+    as [n][6] = xx yy zz xy xz yz."""
+    pos, mass, soft = _f64(pos), _f64(mass), _f64(soft)
+    n = pos.shape[0]
+    tg = _i64(np.arange(n) if targets is None else targets)
+    sink = _u8(np.zeros(n) if is_sink is None else is_sink)
+    T = np.zeros((tg.size, 6))
+    _load().sfgo_direct_tidal(n, _p(pos, _f64p), _p(mass, _f64p), _p(soft, _f64p), _p(sink, _u8p), float(G),
+                              tg.size, _p(tg, _i64p), _p(T, _f64p))
+    return T
+
+
+def tidal_dt(tidal, eta: float):
+    """Tidal timestep sqrt(eta) (|T|_F^2 / 6)^(-1/4) of Sec. 2.3 for T given as [n][6]."""
+    T = _f64(tidal).reshape(-1, 6)
+    dt = np.zeros(T.shape[0])
+    _load().sfgo_tidal_dt(T.shape[0], _p(T, _f64p), float(eta), _p(dt, _f64p))
+    return dt
 
 
 # ------------------------------------------------------------------ tree ----
@@ -244,6 +272,16 @@ class Tree:
         if rc != 0:
             raise ValueError("a requested row is not a walked target")
         return acc, phi
+
+    def tidal_group(self, idx, G: float = 1.0, quadrupole: bool = True):
+        """Group-form tidal tensor [n][6] (xx yy zz xy xz yz) on the last walk's lists."""
+        idx = _i64(idx)
+        T = np.zeros((idx.size, 6))
+        rc = self._lib.sfgo_tidal_group(self._h, float(G), int(quadrupole), _p(idx, _i64p), idx.size,
+                                        _p(T, _f64p))
+        if rc != 0:
+            raise ValueError("a requested row is not a walked target")
+        return T
 
     def eval_frozen(self, pos, mass, idx, G: float = 1.0, quadrupole: bool = True):
         pos, mass, idx = _f64(pos), _f64(mass), _i64(idx)

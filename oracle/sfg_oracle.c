@@ -139,6 +139,52 @@ void sfgo_direct(int64_t n, const double *pos, const double *mass, const double 
     }
 }
 
+/* One pair's tidal term (per unit G m_j): T += -[K I + (dK/dr / r) d d^T],
+ * d = x_j - x_i: the derivative of a = m K(r) d with respect to x_i (Sec. 2.2
+ * defines T = -grad grad Phi; Sec. 2.2.1 sums it with the same softened kernel
+ * and symmetrisation as g).  Components xx yy zz xy xz yz. */
+static void pair_tidal(double m, double K, double Kr, double dx, double dy, double dz, double T[6])
+{
+    T[0] -= m * (K + Kr * dx * dx);
+    T[1] -= m * (K + Kr * dy * dy);
+    T[2] -= m * (K + Kr * dz * dz);
+    T[3] -= m * Kr * dx * dy;
+    T[4] -= m * Kr * dx * dz;
+    T[5] -= m * Kr * dy * dz;
+}
+
+/* Direct-sum tidal tensor at the targets (all pairs j != i). */
+void sfgo_direct_tidal(int64_t n, const double *pos, const double *mass, const double *soft, const uint8_t *sink,
+                       double G, int64_t nt, const int64_t *targets, double *tidal)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets[t];
+        double T[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i)
+                continue;
+            double dx = pos[3 * j] - pos[3 * i], dy = pos[3 * j + 1] - pos[3 * i + 1], dz = pos[3 * j + 2] - pos[3 * i + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double K, P, Kr;
+            pair_law(r, soft[i], soft[j], sink ? sink[i] : 0, sink ? sink[j] : 0, &K, &P, &Kr);
+            pair_tidal(mass[j], K, Kr, dx, dy, dz, T);
+        }
+        for (int c = 0; c < 6; c++) tidal[6 * t + c] = G * T[c];
+    }
+}
+
+/* Tidal timestep of Sec. 2.3, Eq. for Delta t_tidal: sqrt(eta) (|T|^2 / 6)^(-1/4)
+ * with |T| the Frobenius norm (T given as xx yy zz xy xz yz); infinite when T = 0. */
+void sfgo_tidal_dt(int64_t n, const double *tidal, double eta, double *dt)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const double *T = tidal + 6 * i;
+        double f2 = T[0] * T[0] + T[1] * T[1] + T[2] * T[2] + 2.0 * (T[3] * T[3] + T[4] * T[4] + T[5] * T[5]);
+        dt[i] = f2 > 0.0 ? sqrt(eta) * pow(f2 / 6.0, -0.25) : HUGE_VAL;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Tree                                                                     */
 /* ------------------------------------------------------------------------ */
@@ -836,6 +882,69 @@ int sfgo_accel_group(const sfgo_tree *t, double G, int quad, const int64_t *idx,
         phi[k] = G * p;
     }
     free(Mn); free(comn); free(Qn);
+    return bad ? -1 : 0;
+}
+
+/* Tidal term of one node at x_i (per unit G): the derivative -d a / d d of its
+ * monopole (+ quadrupole) field, d = com - x_i, q = d.Qd:
+ *   monopole   -M I / r^3 + 3 M d d^T / r^5
+ *   quadrupole  Q / r^5 - 5 (Qd d^T + d Qd^T) / r^7 - 5/2 q I / r^7 + 35/2 q d d^T / r^9 */
+static void p2m_tidal(const double *com, double M, const double *Q, const double *x, int quad, double T[6])
+{
+    double d[3] = {com[0] - x[0], com[1] - x[1], com[2] - x[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double ir = 1.0 / sqrt(r2), ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+    static const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int c = 0; c < 6; c++) {
+        double dd = d[ia[c]] * d[ib[c]];
+        T[c] += 3.0 * M * dd * ir5 - (c < 3 ? M * ir3 : 0.0);
+    }
+    if (quad) {
+        double ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+        double Qd[3] = {Q[0] * d[0] + Q[3] * d[1] + Q[4] * d[2], Q[3] * d[0] + Q[1] * d[1] + Q[5] * d[2],
+                        Q[4] * d[0] + Q[5] * d[1] + Q[2] * d[2]};
+        double q = d[0] * Qd[0] + d[1] * Qd[1] + d[2] * Qd[2];
+        for (int c = 0; c < 6; c++) {
+            int a = ia[c], b = ib[c];
+            T[c] += Q[c] * ir5 - 5.0 * (Qd[a] * d[b] + d[a] * Qd[b]) * ir7 + 17.5 * q * d[a] * d[b] * ir9 -
+                    (c < 3 ? 2.5 * q * ir7 : 0.0);
+        }
+    }
+}
+
+/* Group-form tidal tensor at the listed original indices: the same lists as
+ * sfgo_accel_group, with pair and node terms differentiated once more
+ * (Sec. 2.2: T in the same pass and with the same opening criterion as g). */
+int sfgo_tidal_group(const sfgo_tree *t, double G, int quad, const int64_t *idx, int64_t n_idx, double *tidal)
+{
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n_idx; k++) {
+        int64_t r = t->rank[idx[k]];
+        if (t->tgroup[r] < 0 || !t->groups[t->tgroup[r]].walked) {
+            bad = 1;
+            continue;
+        }
+        const ogroup *g = &t->groups[t->tgroup[r]];
+        const double *x = t->pos + 3 * r;
+        double T[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t q = 0; q < g->n_p2m; q++) {
+            const onode *nd = &t->nodes[g->p2m[q]];
+            p2m_tidal(nd->com, nd->M, nd->Q, x, quad, T);
+        }
+        for (int64_t q = 0; q < g->n_p2p; q++) {
+            const onode *nd = &t->nodes[g->p2p[q]];
+            for (int64_t j = nd->first; j < nd->first + nd->count; j++) {
+                if (j == r) continue;
+                double dx = t->pos[3 * j] - x[0], dy = t->pos[3 * j + 1] - x[1], dz = t->pos[3 * j + 2] - x[2];
+                double rr = sqrt(dx * dx + dy * dy + dz * dz);
+                double K, P, Kr;
+                pair_law(rr, t->soft[r], t->soft[j], t->sink[r], t->sink[j], &K, &P, &Kr);
+                pair_tidal(t->mass[j], K, Kr, dx, dy, dz, T);
+            }
+        }
+        for (int c = 0; c < 6; c++) tidal[6 * k + c] = G * T[c];
+    }
     return bad ? -1 : 0;
 }
 
