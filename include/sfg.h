@@ -146,6 +146,36 @@ int sfg_build_batch(const double *pos, const double *mass, const double *soft, c
 int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
               void *stream);
 
+/* Field, potential and tidal tensor at the active particles (Sec. 2.2: the
+ * tidal tensor T = -grad grad Phi is summed in the same pass and with the same
+ * opening criterion as g; Sec. 2.2.1: pairs use spatial derivatives of the
+ * same softened kernel with the same symmetrisation).  accel and phi are as
+ * for sfg_accel; for row k
+ *   tidal[k][6] = (T_xx, T_yy, T_zz, T_xy, T_xz, T_yz) at x_{active_idx[k]}:
+ * each softened pair adds -G m_j [K I + (dK/dr / r) d d^T] (d = x_j - x_i,
+ * a = G m_j K d), each accepted node the derivative of its monopole (+
+ * quadrupole) field, so T is the derivative of accel with respect to the
+ * target's own position with the lists fixed.  Sums are FP32 per lane and
+ * per work item, written as float64.
+ *   tidal [n_active][6] float64, device, overwritten
+ * Always walks stored interaction lists (whatever store_lists says) and keeps
+ * them for a following sfg_accel_vjp of the same active set.  Errors as for
+ * sfg_accel, and SFG_EINVAL for a tree built with precision = 1 or while
+ * `stream` is being captured into a CUDA graph (sizing the lists
+ * synchronizes the stream). */
+int sfg_accel_tidal(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
+                    double *tidal, void *stream);
+
+/* Tidal timestep constraint of Sec. 2.3:
+ *   dt[k] = sqrt(eta) * (|T_k|^2 / 6)^(-1/4),
+ * |T| the Frobenius norm of the symmetric tensor given by its six components
+ * (as sfg_accel_tidal writes them); +infinity where T = 0.
+ *   tidal [n][6] float64, device;  dt [n] float64, device, overwritten;
+ *   eta > 0 the tolerance parameter.
+ * Errors: SFG_EINVAL (n < 0, NULL pointer with n > 0, eta <= 0 or not finite),
+ * SFG_ECUDA. */
+int sfg_tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, void *stream);
+
 /* Adjoint of sfg_accel with the interaction lists frozen (recomputed by the
  * same walk): with L = sum_k cot_a[k] . accel[k] + cot_phi[k] * phi[k],
  *   d_pos[n][3] = dL/dpos  and  d_mass[n] = dL/dmass

@@ -90,6 +90,10 @@ def _load():
         lib.sfg_accel.restype = i32
         lib.sfg_accel_vjp.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
         lib.sfg_accel_vjp.restype = i32
+        lib.sfg_accel_tidal.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+        lib.sfg_accel_tidal.restype = i32
+        lib.sfg_tidal_timestep.argtypes = [vp, i64, ctypes.c_double, vp, vp]
+        lib.sfg_tidal_timestep.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.sfg_get_stats.restype = i32
         lib.sfg_cloud_times.argtypes = [vp, vp, vp]
@@ -197,6 +201,18 @@ class Tree:
         _check(rc, "sfg_accel")
         return acc, phi
 
+    def accel_tidal(self, active=None):
+        """(accel [n][3], phi [n], tidal [n][6] = xx yy zz xy xz yz) at the active rows."""
+        a, na = self._active(active)
+        acc = torch.empty((na, 3), dtype=torch.float64, device=self.device)
+        phi = torch.empty(na, dtype=torch.float64, device=self.device)
+        tid = torch.empty((na, 6), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            rc = _load().sfg_accel_tidal(self._h, None if a is None else a.data_ptr(), na, acc.data_ptr(),
+                                         phi.data_ptr(), tid.data_ptr(), _stream(self.device))
+        _check(rc, "sfg_accel_tidal")
+        return acc, phi, tid
+
     def accel_vjp(self, active, cot_a, cot_phi=None):
         a, na = self._active(active)
         cot_a = _dev(cot_a, torch.float64, "cot_a")
@@ -289,6 +305,17 @@ class _Gravity(torch.autograd.Function):
         d_pos, d_mass = tree.accel_vjp(ctx.active, g_acc, g_phi)
         tree.close()
         return d_pos, d_mass, None, None, None, None
+
+
+def tidal_timestep(tidal: torch.Tensor, eta: float) -> torch.Tensor:
+    """Tidal timestep sqrt(eta) (|T|_F^2 / 6)^(-1/4) of every row of tidal [n][6]."""
+    tidal = _dev(tidal, torch.float64, "tidal")
+    n = tidal.numel() // 6
+    dt = torch.empty(n, dtype=torch.float64, device=tidal.device)
+    with torch.cuda.device(tidal.device):
+        rc = _load().sfg_tidal_timestep(tidal.data_ptr(), n, float(eta), dt.data_ptr(), _stream(tidal.device))
+    _check(rc, "sfg_tidal_timestep")
+    return dt
 
 
 def gravity(pos, mass, soft, is_sink=None, active=None, **kw):

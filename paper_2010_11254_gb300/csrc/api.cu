@@ -181,6 +181,22 @@ int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, doubl
     return sfg::accel(&tree->t, active_idx, n_active, accel, phi, (cudaStream_t)stream);
 }
 
+int sfg_accel_tidal(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
+                    double *tidal, void *stream)
+{
+    if (!tree || n_active < 0 || (n_active > 0 && (!accel || !tidal))) return SFG_EINVAL;
+    tree->t.stream = (cudaStream_t)stream;
+    cudaGetLastError();
+    return sfg::accel_tidal(&tree->t, active_idx, n_active, accel, phi, tidal, (cudaStream_t)stream);
+}
+
+int sfg_tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, void *stream)
+{
+    if (n < 0 || (n > 0 && (!tidal || !dt)) || !(eta > 0.0) || !std::isfinite(eta)) return SFG_EINVAL;
+    cudaGetLastError();
+    return sfg::tidal_timestep(tidal, n, eta, dt, (cudaStream_t)stream);
+}
+
 int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
                   const double *cot_phi, double *d_pos, double *d_mass, void *stream)
 {

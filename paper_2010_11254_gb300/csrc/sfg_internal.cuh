@@ -83,8 +83,8 @@ struct Tree {
     float4 *E0 = nullptr, *E1 = nullptr, *E2 = nullptr;
     double *nM = nullptr, *ncom = nullptr, *nQ = nullptr, *nhmax = nullptr;
     // per-call workspace (grow-only)
-    void *ws = nullptr, *ws2 = nullptr;
-    size_t ws_bytes = 0, ws2_bytes = 0;
+    void *ws = nullptr, *ws2 = nullptr, *ws3 = nullptr; // forward, adjoint, tidal sums
+    size_t ws_bytes = 0, ws2_bytes = 0, ws3_bytes = 0;
     sfg_stats last{};
     // [0] p2p, [1] p2m, [2] overflowed groups, [3] work, [4] retry work, [5] groups, [6] distinct targets,
     // [7] item cost total, [8] Newtonian-list P2P interactions
@@ -131,6 +131,9 @@ void scan_exclusive(const int *in, int *out, const int *d_n, int max_n, int *ext
 int accel(Tree *t, const int64_t *active, int64_t n_active, double *accel, double *phi, cudaStream_t s);
 int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *cot_a, const double *cot_phi,
               double *d_pos, double *d_mass, cudaStream_t s);
+int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *accel, double *phi, double *tidal,
+                cudaStream_t s);
+int tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, cudaStream_t s);
 int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
                 int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s);
 

@@ -37,7 +37,8 @@ constexpr int WALK_WARPS = 4;  // warps per block
 constexpr int WALK_MINB = 6;   // resident blocks per SM the register budget must allow
 constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
 constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
-constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4, MODE_LIST = 5;
+constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4, MODE_LIST = 5,
+              MODE_TIDAL = 6; // MODE_TIDAL: forward evaluation plus the tidal tensor (stored lists only)
 // list sizes per group written by the counting walk: P2M nodes, softened P2P
 // ranges and particles, Newtonian P2P ranges and particles
 constexpr int NCNT = 5;
@@ -80,6 +81,7 @@ struct WalkParams {
     float4 *res_a;
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
+    float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
     unsigned long long *counters; // [0] p2p [1] p2m [2] overflowed groups [3] work [4] retry work
     int *ovf_list;
     int *status;
@@ -233,13 +235,8 @@ __device__ __forceinline__ void fwd_p2m(const SM &S, int cnt, const Tgt &T, floa
                                         double &phi)
 {
     float pt = 0.f;
-    if (T.R == 1 && cnt == 32) {
-#pragma unroll 4
-        for (int k = 0; k < 32; k++) fwd_p2m_step<QUAD>(S, k, T, ax, ay, az, pt);
-    } else {
 #pragma unroll 2
-        for (int k = T.slice; k < cnt; k += T.R) fwd_p2m_step<QUAD>(S, k, T, ax, ay, az, pt);
-    }
+    for (int k = T.slice; k < cnt; k += T.R) fwd_p2m_step<QUAD>(S, k, T, ax, ay, az, pt);
     phi += (double)pt;
 }
 
@@ -934,7 +931,7 @@ __device__ __forceinline__ void finish_targets(const WalkParams &P, const Tgt &T
         az += __shfl_xor_sync(FULL, az, o);
         phi += __shfl_xor_sync(FULL, phi, o);
     }
-    if (MODE == MODE_EVAL) {
+    if (MODE == MODE_EVAL || MODE == MODE_TIDAL) {
         if (K == 1) {
             if (T.has && T.slice == 0) {
                 P.res_a[tfirst + T.tl] = make_float4(ax, ay, az, 0.f);
@@ -1132,6 +1129,7 @@ struct EvalSmem {
     float4 sAcc[32]; // per-target sums of the softened pairs: forward (a, phi), adjoint (-dL/dx_i, -)
     float4 gC[32];   // adjoint: the targets' cotangents (cot_a, cot_phi)
     float4 sS[32];   // adjoint: per-source sums of the softened pairs of a tile (dL/dx_j, dL/dm_j)
+    float sTid[32][8]; // tidal mode: per-target sums of the softened pairs (as res_T)
     unsigned short sq[1024]; // softened pairs of a tile: target | source << 5
 };
 
@@ -1211,13 +1209,8 @@ __device__ __forceinline__ void fwd_p2p_newt(const SM &S, int cnt, const Tgt &T,
                                              double &phi)
 {
     float pt = 0.f;
-    if (T.R == 1 && cnt == 32) {
-#pragma unroll 4
-        for (int k = 0; k < 32; k++) fwd_newt_step(S, k, T, ax, ay, az, pt);
-    } else {
 #pragma unroll 2
-        for (int k = T.slice; k < cnt; k += T.R) fwd_newt_step(S, k, T, ax, ay, az, pt);
-    }
+    for (int k = T.slice; k < cnt; k += T.R) fwd_newt_step(S, k, T, ax, ay, az, pt);
     phi += (double)pt;
 }
 
@@ -1296,6 +1289,109 @@ __device__ __forceinline__ void fwd_step_defer(const SM &S, int k, const Tgt &T,
     pt -= mr;
 }
 
+// ---------------------------------------------------------- tidal mode ----
+// T = -grad grad Phi (Sec. 2.2) summed on the same lists and with the same
+// softened kernel as g (Sec. 2.2.1).  A lane keeps T without its isotropic
+// part, t (xx yy zz xy xz yz), and that part's coefficient iso separately:
+// T = t - iso I.  A pair adds -m [K I + (dK/dr / r) d d^T] (d = x_j - x_i);
+// a node adds the derivative of its monopole (+ quadrupole) field.
+struct TidAcc {
+    float t[6];
+    float iso;
+};
+
+__device__ __forceinline__ void tid_add_dd(TidAcc &A, float c, float dx, float dy, float dz)
+{
+    const float cx = c * dx, cy = c * dy;
+    A.t[0] = fmaf(cx, dx, A.t[0]);
+    A.t[1] = fmaf(cy, dy, A.t[1]);
+    A.t[2] = fmaf(c * dz, dz, A.t[2]);
+    A.t[3] = fmaf(cx, dy, A.t[3]);
+    A.t[4] = fmaf(cx, dz, A.t[4]);
+    A.t[5] = fmaf(cy, dz, A.t[5]);
+}
+
+// P2M with its tidal term: monopole -M I / r^3 + 3 M d d^T / r^5; quadrupole
+// Q / r^5 - 5 (Qd d^T + d Qd^T) / r^7 - 5/2 q I / r^7 + 35/2 q d d^T / r^9.
+template <bool QUAD, class SM>
+__device__ __forceinline__ void tid_p2m_step(const SM &S, int k, const Tgt &T, float &ax, float &ay, float &az,
+                                             float &pt, TidAcc &A)
+{
+    float4 p = S.tP[k];
+    float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float rinv = rsqrtf(r2);
+    float ri2 = rinv * rinv;
+    float Mri3 = p.w * (ri2 * rinv);
+    if (QUAD) {
+        float4 q = S.tA[k];
+        float qyz = S.tB[k];
+        float qzz = -(q.x + q.y);
+        float Qd0 = fmaf(q.x, dx, fmaf(q.z, dy, q.w * dz));
+        float Qd1 = fmaf(q.z, dx, fmaf(q.y, dy, qyz * dz));
+        float Qd2 = fmaf(q.w, dx, fmaf(qyz, dy, qzz * dz));
+        float ri5 = rinv * ri2 * ri2;
+        float t = fmaf(dx, Qd0, fmaf(dy, Qd1, dz * Qd2)) * ri5; // q / r^5
+        float c = fmaf(t, 2.5f * ri2, Mri3);
+        ax = fmaf(c, dx, fmaf(-ri5, Qd0, ax));
+        ay = fmaf(c, dy, fmaf(-ri5, Qd1, ay));
+        az = fmaf(c, dz, fmaf(-ri5, Qd2, az));
+        pt = fmaf(-p.w, rinv, fmaf(-0.5f, t, pt));
+        A.iso += c; // M / r^3 + 5/2 q / r^7
+        tid_add_dd(A, fmaf(17.5f * t, ri2 * ri2, 3.f * Mri3 * ri2), dx, dy, dz);
+        const float b = -5.f * ri5 * ri2;
+        const float e0 = b * Qd0, e1 = b * Qd1, e2 = b * Qd2;
+        A.t[0] = fmaf(ri5, q.x, fmaf(2.f * e0, dx, A.t[0]));
+        A.t[1] = fmaf(ri5, q.y, fmaf(2.f * e1, dy, A.t[1]));
+        A.t[2] = fmaf(ri5, qzz, fmaf(2.f * e2, dz, A.t[2]));
+        A.t[3] = fmaf(ri5, q.z, fmaf(e0, dy, fmaf(e1, dx, A.t[3])));
+        A.t[4] = fmaf(ri5, q.w, fmaf(e0, dz, fmaf(e2, dx, A.t[4])));
+        A.t[5] = fmaf(ri5, qyz, fmaf(e1, dz, fmaf(e2, dy, A.t[5])));
+    } else {
+        ax = fmaf(Mri3, dx, ax);
+        ay = fmaf(Mri3, dy, ay);
+        az = fmaf(Mri3, dz, az);
+        pt = fmaf(-p.w, rinv, pt);
+        A.iso += Mri3;
+        tid_add_dd(A, 3.f * Mri3 * ri2, dx, dy, dz);
+    }
+}
+
+template <bool QUAD, class SM>
+__device__ __forceinline__ void tid_p2m(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+                                        double &phi, TidAcc &A)
+{
+    float pt = 0.f;
+    for (int k = T.slice; k < cnt; k += T.R) tid_p2m_step<QUAD>(S, k, T, ax, ay, az, pt, A);
+    phi += (double)pt;
+}
+
+// Newtonian pair (every pair of a Newtonian range; the pairs outside both
+// supports of a softened range, the others flagged in mask).
+template <bool SOFT, class SM>
+__device__ __forceinline__ void tid_p2p_step(const SM &S, int k, const Tgt &T, float ht2, float &ax, float &ay,
+                                             float &az, float &pt, unsigned &mask, TidAcc &A)
+{
+    float4 p = S.tP[k];
+    float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    bool sft = false;
+    if (SOFT) {
+        sft = r2 < fmaxf(ht2, S.tB[k]);
+        if (sft) mask |= 1u << k;
+    }
+    float rinv = rsqrtf(sft ? 1.f : r2);
+    float ri2 = rinv * rinv;
+    float mr = sft ? 0.f : p.w * rinv;
+    float mr3 = mr * ri2;
+    ax = fmaf(mr3, dx, ax);
+    ay = fmaf(mr3, dy, ay);
+    az = fmaf(mr3, dz, az);
+    pt -= mr;
+    A.iso += mr3;
+    tid_add_dd(A, 3.f * mr3 * ri2, dx, dy, dz);
+}
+
 // Exclusive warp prefix of n and the warp total.
 __device__ __forceinline__ int warp_excl(int n, int lane, int &total)
 {
@@ -1316,7 +1412,7 @@ __device__ __forceinline__ void fwd_p2p_defer(EvalSmem &S, int cnt, const Tgt &T
     const float ht2 = T.h * T.h;
     if (T.has) {
         if (T.R == 1 && cnt == 32) {
-#pragma unroll
+#pragma unroll 8
             for (int k = 0; k < 32; k++) fwd_step_defer(S, k, T, ht2, ax, ay, az, pt, mask);
         } else {
 #pragma unroll 2
@@ -1363,6 +1459,73 @@ __device__ __forceinline__ void fwd_p2p_defer(EvalSmem &S, int cnt, const Tgt &T
     }
     __syncwarp();
     // potentials: FP32 within the tile, FP64 across tiles (like the lane sums)
+    if (T.has && T.slice == 0) {
+        phi += (double)S.sAcc[T.tl].w;
+        S.sAcc[T.tl].w = 0.f;
+    }
+    __syncwarp();
+}
+
+// Tidal mode, one P2P tile: Newtonian pairs on the lanes; for a softened
+// range the pairs inside max(h_i, h_j) are deferred as in fwd_p2p_defer and
+// evaluated with K, P and dK/dr / r of the pair rule.
+template <bool SOFT>
+__device__ __forceinline__ void tid_p2p(EvalSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
+                                        double &phi, TidAcc &A, int lane)
+{
+    float pt = 0.f;
+    unsigned mask = 0u;
+    const float ht2 = T.h * T.h;
+    if (T.has) {
+        for (int k = T.slice; k < cnt; k += T.R) tid_p2p_step<SOFT>(S, k, T, ht2, ax, ay, az, pt, mask, A);
+    }
+    phi += (double)pt;
+    if (!SOFT) return;
+    int total;
+    int at = warp_excl(__popc(mask), lane, total);
+    if (total == 0) return;
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        S.sq[at++] = (unsigned short)(T.tl | (k << 5));
+    }
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+        if (b + lane < total) {
+            const unsigned e = S.sq[b + lane];
+            const int t = e & 31, k = e >> 5;
+            const float4 tg = S.gT[t], tu = S.gU[t];
+            const float4 p = S.tP[k], hh = S.tA[k];
+            if (__float_as_int(hh.z) != __float_as_int(tu.z)) { // not the self pair
+                float dx = p.x - tg.x, dy = p.y - tg.y, dz = p.z - tg.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bool sink = tu.y != 0.f || hh.w != 0.f;
+                bool tbig = tg.w >= hh.x;
+                float ha = tbig ? tg.w : hh.x, hainv = tbig ? tu.x : hh.y;
+                float hb = sink ? ha : (tbig ? hh.x : tg.w), hbinv = sink ? hainv : (tbig ? hh.y : tu.x);
+                float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                float r = r2 * rinv;
+                float K1, P1, R1, K2, P2, R2;
+                soft_KPR(r, rinv, ha, hainv, K1, P1, R1);
+                soft_KPR(r, rinv, hb, hbinv, K2, P2, R2);
+                const float m = p.w;
+                const float mK = m * 0.5f * (K1 + K2), mR = m * 0.5f * (R1 + R2);
+                atomicAdd(&S.sAcc[t].x, mK * dx);
+                atomicAdd(&S.sAcc[t].y, mK * dy);
+                atomicAdd(&S.sAcc[t].z, mK * dz);
+                atomicAdd(&S.sAcc[t].w, m * 0.5f * (P1 + P2));
+                // T += -m [K I + (dK/dr / r) d d^T]
+                atomicAdd(&S.sTid[t][0], -mR * dx * dx);
+                atomicAdd(&S.sTid[t][1], -mR * dy * dy);
+                atomicAdd(&S.sTid[t][2], -mR * dz * dz);
+                atomicAdd(&S.sTid[t][3], -mR * dx * dy);
+                atomicAdd(&S.sTid[t][4], -mR * dx * dz);
+                atomicAdd(&S.sTid[t][5], -mR * dy * dz);
+                atomicAdd(&S.sTid[t][6], mK);
+            }
+        }
+    }
+    __syncwarp();
     if (T.has && T.slice == 0) {
         phi += (double)S.sAcc[T.tl].w;
         S.sAcc[T.tl].w = 0.f;
@@ -1490,7 +1653,7 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
 template <int MODE, bool NEWT>
 __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, const Tgt &T, const int2 *rr, int nr,
                                               int np, int kk, int K, float c0, float c1, float c2, float cf,
-                                              float &ax, float &ay, float &az, double &phi, int lane)
+                                              float &ax, float &ay, float &az, double &phi, TidAcc &A, int lane)
 {
     const int nt = (np + 31) >> 5;
     const int t0 = (int)((long long)nt * kk / K), t1 = (int)((long long)nt * (kk + 1) / K);
@@ -1533,10 +1696,12 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
         if (NEWT) {
             stage_p2p_newt(P, S, c, qh, qoff, T, lane);
             if (MODE == MODE_VJP) vjp_p2p_newt(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (MODE == MODE_TIDAL) tid_p2p<false>(S, c, T, ax, ay, az, phi, A, lane);
             else if (T.has) fwd_p2p_newt(S, c, T, ax, ay, az, phi);
         } else {
             stage_p2p(P, S, c, qh, qoff, T, lane);
             if (MODE == MODE_VJP) vjp_p2p_defer(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            else if (MODE == MODE_TIDAL) tid_p2p<true>(S, c, T, ax, ay, az, phi, A, lane);
             else fwd_p2p_defer(S, c, T, ax, ay, az, phi, lane);
         }
         __syncwarp();
@@ -1567,6 +1732,11 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         if (MODE == MODE_VJP) S.gC[T.tl] = make_float4(c0, c1, c2, cf);
     }
     S.sAcc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    TidAcc A = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, 0.f};
+    if (MODE == MODE_TIDAL) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) S.sTid[lane][c] = 0.f;
+    }
     __syncwarp();
     const int *cn = P.lcnt + NCNT * (size_t)g;
     const int nm = cn[0], nls = cn[1], nps = cn[2], nln = cn[3], npn = cn[4];
@@ -1578,27 +1748,53 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
             const int b = tt * 32, c = min(32, nm - b);
             stage_p2m<QUAD, MODE == MODE_VJP>(P, S, lm + b, c, T, lane);
             if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (T.has) fwd_p2m<QUAD>(S, c, T, ax, ay, az, phi);
+            else if (MODE == MODE_TIDAL) {
+                if (T.has) tid_p2m<QUAD>(S, c, T, ax, ay, az, phi, A);
+            } else if (T.has) fwd_p2m<QUAD>(S, c, T, ax, ay, az, phi);
             __syncwarp();
         }
     }
     const int2 *lr = P.lr + P.lro[g];
-    eval_p2p_list<MODE, false>(P, S, T, lr, nls, nps, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
-    eval_p2p_list<MODE, true>(P, S, T, lr + nls, nln, npn, kk, K, c0, c1, c2, cf, ax, ay, az, phi, lane);
+    eval_p2p_list<MODE, false>(P, S, T, lr, nls, nps, kk, K, c0, c1, c2, cf, ax, ay, az, phi, A, lane);
+    eval_p2p_list<MODE, true>(P, S, T, lr + nls, nln, npn, kk, K, c0, c1, c2, cf, ax, ay, az, phi, A, lane);
     if (T.has && T.slice == 0) { // the deferred softened pairs' target-side sums
         const float4 v = S.sAcc[T.tl];
         ax += v.x;
         ay += v.y;
         az += v.z;
+        if (MODE == MODE_TIDAL) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) A.t[c] += S.sTid[T.tl][c];
+            A.iso += S.sTid[T.tl][6];
+        }
     }
     __syncwarp();
+    if (MODE == MODE_TIDAL) {
+        // slices -> one sum per target; items of a split group add theirs
+        for (int o = T.tp; o < 32; o <<= 1) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) A.t[c] += __shfl_xor_sync(FULL, A.t[c], o);
+            A.iso += __shfl_xor_sync(FULL, A.iso, o);
+        }
+        if (T.has && T.slice == 0) {
+            float *dst = P.res_T + 8 * (size_t)(tfirst + T.tl);
+#pragma unroll
+            for (int c = 0; c < 6; c++) atomicAdd(dst + c, A.t[c]);
+            atomicAdd(dst + 6, A.iso);
+        }
+    }
     finish_targets<MODE>(P, T, g, kk, K, tfirst, tcount, ax, ay, az, phi, nps + npn, nm, npn, lane);
     return cloud;
 }
 
 // Persistent warps take work items (longest first) from an atomic counter.
+// resident blocks per SM of the evaluation kernel (the tidal mode carries
+// seven more accumulators per lane)
+constexpr int TIDAL_MINB = 4;
+constexpr int eval_minb(int mode) { return mode == MODE_TIDAL ? TIDAL_MINB : EVAL_MINB; }
+
 template <bool QUAD, int MODE>
-__global__ void __launch_bounds__(EVAL_WARPS * 32, EVAL_MINB) k_eval(WalkParams P)
+__global__ void __launch_bounds__(EVAL_WARPS * 32, eval_minb(MODE)) k_eval(WalkParams P)
 {
     __shared__ EvalSmem sm[EVAL_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1941,6 +2137,30 @@ __global__ void k_rows_out(const int64_t *idx, int64_t n_active, int n, const in
     }
 }
 
+// Tidal rows in the caller's order: T = G (t - iso I), FP64.
+__global__ void k_rows_out_tidal(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
+                                 const float *res_T, double G, double *tidal)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) continue;
+        const float *r = res_T + 8 * (size_t)pre[rank[i]];
+        const double iso = (double)r[6];
+        for (int c = 0; c < 6; c++) tidal[6 * k + c] = G * ((double)r[c] - (c < 3 ? iso : 0.0));
+    }
+}
+
+// Tidal timestep sqrt(eta) (|T|_F^2 / 6)^(-1/4) (Sec. 2.3); +inf where T = 0.
+__global__ void k_tidal_dt(const double *tidal, int64_t n, double eta, double *dt)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double *T = tidal + 6 * k;
+        double f2 = T[0] * T[0] + T[1] * T[1] + T[2] * T[2] + 2.0 * (T[3] * T[3] + T[4] * T[4] + T[5] * T[5]);
+        dt[k] = f2 > 0.0 ? sqrt(eta) * rsqrt(sqrt(f2 / 6.0)) : __longlong_as_double(0x7ff0000000000000ll);
+    }
+}
+
 __global__ void k_rows_out64(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
                              const double *res64, double G, double *accel, double *phi)
 {
@@ -1973,6 +2193,7 @@ struct Work {
     float4 *res_a;
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
+    float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
     int *cnt, *kcnt, *is_split, *soff, *ioff, *gdone, *hist; // cnt: NCNT list sizes per group
     long long *lmo, *lro; // stored lists: first P2M entry / first P2P range of every group (exclusive scans)
     int2 *items;
@@ -2327,7 +2548,7 @@ static int lists_match(Tree *t, const int64_t *active, int64_t n_active, cudaStr
 template <int MODE>
 static void launch_eval(Tree *t, WalkParams &P, cudaStream_t s)
 {
-    const int blocks = num_sms() * EVAL_MINB;
+    const int blocks = num_sms() * eval_minb(MODE);
     if (t->prm.quadrupole) k_eval<true, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
     else k_eval<false, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
     t->n_launch += 1;
@@ -2379,6 +2600,65 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
     }
     t->n_launch += 1;
     ph_end(t, PH_FWD, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+// Field, potential and tidal tensor from stored lists (walked here unless the
+// lists of the same active set are kept).
+int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *acc, double *phi, double *tidal,
+                cudaStream_t s)
+{
+    if (n_active == 0) return SFG_OK;
+    if (t->prm.precision != 0 || capturing(s)) return SFG_EINVAL;
+    Work w;
+    WalkParams P;
+    ph_begin(t, PH_FWD, s);
+    int rc = prepare(t, active, n_active, w, P, s);
+    if (rc) return rc;
+    bool match = false;
+    rc = lists_match(t, active, n_active, s, match);
+    if (rc) return rc;
+    if (!match) {
+        rc = build_lists(t, w, P, s);
+        if (rc) return rc;
+        rc = remember_active(t, active, n_active, s);
+        if (rc) return rc;
+    }
+    items_from_counts(t, w, P, s, WT_EVAL);
+    const size_t need = 32 * (size_t)t->n;
+    if (t->ws3_bytes < need) {
+        if (t->ws3) dev_free(t, t->ws3, s);
+        t->ws3 = dev_alloc(t, need, s);
+        if (!t->ws3) {
+            t->ws3_bytes = 0;
+            return SFG_ENOMEM;
+        }
+        t->ws3_bytes = need;
+    }
+    P.res_T = (float *)t->ws3;
+    SFG_CUDA_OK(cudaMemsetAsync(P.res_T, 0, need, s));
+    if (t->timing) {
+        int rc2 = cloud_timer_begin(t, 0, s, P);
+        if (rc2) return rc2;
+    }
+    ph_begin(t, PH_FWD_WALK, s);
+    launch_eval<MODE_TIDAL>(t, P, s);
+    ph_end(t, PH_FWD_WALK, s);
+    k_rows_out<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, w.res_a,
+                                                       w.res_phi, t->prm.G, acc, phi);
+    k_rows_out_tidal<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, P.res_T,
+                                                             t->prm.G, tidal);
+    t->n_launch += 2;
+    ph_end(t, PH_FWD, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+int tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, cudaStream_t s)
+{
+    if (n <= 0) return SFG_OK;
+    k_tidal_dt<<<grid_for(n, 256), 256, 0, s>>>(tidal, n, eta, dt);
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
 }
