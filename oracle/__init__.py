@@ -101,6 +101,8 @@ def _load():
         lib.sfgo_tidal_group.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _f64p]
         lib.sfgo_tidal_dt.restype = None
         lib.sfgo_tidal_dt.argtypes = [ctypes.c_int64, _f64p, ctypes.c_double, _f64p]
+        lib.sfgo_set_relative.restype = None
+        lib.sfgo_set_relative.argtypes = [_vp, _f64p, ctypes.c_double, ctypes.c_double]
         lib.sfgo_num_threads.restype = ctypes.c_int
         lib.sfgo_num_threads.argtypes = []
         _lib = lib
@@ -272,6 +274,16 @@ class Tree:
         if rc != 0:
             raise ValueError("a requested row is not a walked target")
         return acc, phi
+
+    def set_relative(self, g_prev=None, alpha: float = 0.0, G: float = 1.0):
+        """Relative (acceleration-based) opening criterion of Sec. 2.2 for the
+        next walks: |g_prev| per particle (input order) and tolerance alpha;
+        None switches it off."""
+        if g_prev is None:
+            self._lib.sfgo_set_relative(self._h, None, 0.0, 0.0)
+            return
+        g = _f64(g_prev)
+        self._lib.sfgo_set_relative(self._h, _p(g, _f64p), float(alpha), float(G))
 
     def tidal_group(self, idx, G: float = 1.0, quadrupole: bool = True):
         """Group-form tidal tensor [n][6] (xx yy zz xy xz yz) on the last walk's lists."""

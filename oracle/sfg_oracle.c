@@ -205,6 +205,7 @@ typedef struct {
     int64_t node, tfirst, tcount; /* targets: tgt[tfirst .. tfirst+tcount) (sorted ranks) */
     uint32_t lo[3], hi[3];
     uint64_t hq;
+    double gmin; /* smallest |g_prev| of the targets (relative criterion) */
     int walked;
     int64_t n_p2m, n_p2p;
     int64_t *p2m, *p2p; /* accepted nodes; opened leaves */
@@ -228,6 +229,9 @@ typedef struct sfgo_tree {
     ogroup *groups;
     int64_t *tgt;       /* unique active sorted ranks, grouped */
     int64_t *tgroup;    /* sorted rank -> group id (-1) */
+    /* relative (acceleration-based) opening criterion, off when gprev == NULL */
+    double *gprev;      /* |g| of the previous step per sorted rank */
+    double alpha, Grel; /* error tolerance; G multiplying node masses */
 } sfgo_tree;
 
 /* Frame: per-axis min; root side L0 = smallest power of two >= largest extent. */
@@ -514,7 +518,7 @@ void sfgo_free(sfgo_tree *t)
 {
     if (!t) return;
     free_walk(t);
-    free(t->pos); free(t->mass); free(t->soft); free(t->sink);
+    free(t->pos); free(t->mass); free(t->soft); free(t->sink); free(t->gprev);
     free(t->order); free(t->rank); free(t->key); free(t->q); free(t->nodes);
     free(t);
 }
@@ -587,6 +591,23 @@ static uint64_t cell_gap(uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi)
     return g > 0 ? (uint64_t)g : 0u;
 }
 
+/* Relative criterion of Sec. 2.2 (the acceleration-based rule the paper takes
+ * from GADGET-2, applied together with the geometric one): accept only if the
+ * node's quadrupole-order error scale G M L^2 / r^4 is at most alpha |g_prev|.
+ * Group form, conservative for every target: r >= sqrt(sc) cells (sc = the
+ * squared whole-cell gap of the geometric clause) and |g_prev| >= gmin, so
+ * test G M L^2 <= alpha gmin (sc cell^2)^2, as exactly these IEEE products
+ * (each rounded once, in this order, no contraction). */
+static int accept_relative(const sfgo_tree *t, const ogroup *g, const onode *nd, uint64_t sc)
+{
+    double L = ldexp(t->L0, -nd->level);
+    double cell = ldexp(t->L0, -LMAX);
+    double lhs = (t->Grel * nd->M) * (L * L);
+    double r2 = (double)sc * (cell * cell);
+    double rhs = (t->alpha * g->gmin) * (r2 * r2);
+    return lhs <= rhs;
+}
+
 static int accept_group(const sfgo_tree *t, const ogroup *g, const onode *nd, const uint64_t *T)
 {
     uint64_t sc = 0, sb = 0;
@@ -597,8 +618,21 @@ static int accept_group(const sfgo_tree *t, const ogroup *g, const onode *nd, co
         sb += gb * gb;
     }
     uint64_t hneed = g->hq > nd->hq ? g->hq : nd->hq;
-    (void)t;
-    return sc >= T[nd->level] && sb >= hneed;
+    if (!(sc >= T[nd->level] && sb >= hneed)) return 0;
+    return t->gprev ? accept_relative(t, g, nd, sc) : 1;
+}
+
+/* Switch the relative criterion on (g_prev = |g| per particle in the input
+ * order, alpha > 0) or off (g_prev == NULL). */
+void sfgo_set_relative(sfgo_tree *t, const double *g_prev, double alpha, double G)
+{
+    free(t->gprev);
+    t->gprev = NULL;
+    if (!g_prev) return;
+    t->gprev = (double *)malloc(8 * t->n);
+    for (int64_t r = 0; r < t->n; r++) t->gprev[r] = g_prev[t->order[r]];
+    t->alpha = alpha;
+    t->Grel = G;
 }
 
 typedef struct { int64_t *v; int64_t n, cap; } ivec;
@@ -716,9 +750,11 @@ int64_t sfgo_walk(sfgo_tree *t, const int64_t *active, int64_t n_active, int gsi
             G->hi[a] = 0;
         }
         G->hq = 0;
+        G->gmin = HUGE_VAL;
         for (int64_t k = G->tfirst; k < G->tfirst + G->tcount; k++) {
             int64_t r = t->tgt[k];
             t->tgroup[r] = g;
+            if (t->gprev && t->gprev[r] < G->gmin) G->gmin = t->gprev[r];
             for (int a = 0; a < 3; a++) {
                 if (t->q[3 * r + a] < G->lo[a]) G->lo[a] = t->q[3 * r + a];
                 if (t->q[3 * r + a] > G->hi[a]) G->hi[a] = t->q[3 * r + a];
@@ -985,7 +1021,7 @@ int sfgo_eval_frozen(const sfgo_tree *t0, double G, int quad, const double *pos,
 }
 
 /* ---------------- per-particle, paper-faithful FP64 opening rule --------- */
-static int accept_pp(const sfgo_tree *t, const onode *nd, const double *x, double h, double theta)
+static int accept_pp(const sfgo_tree *t, const onode *nd, const double *x, double h, double theta, double gp)
 {
     double L = ldexp(t->L0, -nd->level);
     double d0 = nd->com[0] - x[0], d1 = nd->com[1] - x[1], d2 = nd->com[2] - x[2];
@@ -999,7 +1035,10 @@ static int accept_pp(const sfgo_tree *t, const onode *nd, const double *x, doubl
         b2 += g * g;
     }
     double hh = h > nd->hmax ? h : nd->hmax;
-    return b2 >= hh * hh;
+    if (!(b2 >= hh * hh)) return 0;
+    if (gp < 0.0) return 1;
+    /* relative criterion, per target: G M L^2 <= alpha |g_prev| r^4 */
+    return t->Grel * nd->M * L * L <= t->alpha * gp * r2 * r2;
 }
 
 static void walk_pp(const sfgo_tree *t, int64_t r, int64_t ni, double theta, int quad, double a[3], double *p,
@@ -1007,7 +1046,7 @@ static void walk_pp(const sfgo_tree *t, int64_t r, int64_t ni, double theta, int
 {
     const onode *nd = &t->nodes[ni];
     const double *x = t->pos + 3 * r;
-    if (accept_pp(t, nd, x, t->soft[r], theta)) {
+    if (accept_pp(t, nd, x, t->soft[r], theta, t->gprev ? t->gprev[r] : -1.0)) {
         double ta[3], tp;
         p2m_term(nd, nd->com, nd->M, nd->Q, x, quad, ta, &tp);
         for (int c = 0; c < 3; c++) a[c] += ta[c];
