@@ -166,6 +166,24 @@ int sfg_accel(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, doubl
 int sfg_accel_tidal(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, double *accel, double *phi,
                     double *tidal, void *stream);
 
+/* Relative (acceleration-based) opening criterion of Sec. 2.2, which the
+ * paper applies together with the geometric rule: a node is accepted only if
+ * its quadrupole-order error scale stays below a fraction alpha of the field
+ * of the previous step,
+ *   G M L^2 / r^4 <= alpha |g_prev,i|  for every target i of the group,
+ * tested conservatively per group (r bounded below by the whole-cell gap
+ * between the node's centre-of-mass cell and the group's box, |g_prev| by the
+ * group's minimum) in fixed FP64 products.
+ *   g_prev [n] float64, device: |g| of every particle (input order) from the
+ *          previous step; copied (gathered into the sorted order), so it may
+ *          be freed once the stream has passed the call.  NULL switches the
+ *          criterion off.
+ *   alpha  >= 0, finite (alpha = 0 opens every node of positive mass)
+ * It applies to every following sfg_accel / sfg_accel_tidal / sfg_accel_vjp
+ * walk of this tree; kept interaction lists are dropped.  Errors: SFG_EINVAL
+ * (NULL tree, bad alpha), SFG_ENOMEM, SFG_ECUDA. */
+int sfg_set_relative_criterion(sfg_tree *tree, const double *g_prev, double alpha, void *stream);
+
 /* Tidal timestep constraint of Sec. 2.3:
  *   dt[k] = sqrt(eta) * (|T_k|^2 / 6)^(-1/4),
  * |T| the Frobenius norm of the symmetric tensor given by its six components

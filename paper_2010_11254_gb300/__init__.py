@@ -94,6 +94,8 @@ def _load():
         lib.sfg_accel_tidal.restype = i32
         lib.sfg_tidal_timestep.argtypes = [vp, i64, ctypes.c_double, vp, vp]
         lib.sfg_tidal_timestep.restype = i32
+        lib.sfg_set_relative_criterion.argtypes = [vp, vp, ctypes.c_double, vp]
+        lib.sfg_set_relative_criterion.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.sfg_get_stats.restype = i32
         lib.sfg_cloud_times.argtypes = [vp, vp, vp]
@@ -200,6 +202,17 @@ class Tree:
                                    phi.data_ptr() if phi is not None else None, _stream(self.device))
         _check(rc, "sfg_accel")
         return acc, phi
+
+    def set_relative(self, g_prev=None, alpha: float = 0.0):
+        """Relative opening criterion of Sec. 2.2 for the following walks:
+        g_prev = |g| per particle (input order, CUDA float64), or None (off)."""
+        ptr = None
+        if g_prev is not None:
+            g_prev = _dev(g_prev, torch.float64, "g_prev")
+            ptr = g_prev.data_ptr()
+        with torch.cuda.device(self.device):
+            rc = _load().sfg_set_relative_criterion(self._h, ptr, float(alpha), _stream(self.device))
+        _check(rc, "sfg_set_relative_criterion")
 
     def accel_tidal(self, active=None):
         """(accel [n][3], phi [n], tidal [n][6] = xx yy zz xy xz yz) at the active rows."""

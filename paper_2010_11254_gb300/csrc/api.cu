@@ -190,6 +190,14 @@ int sfg_accel_tidal(sfg_tree *tree, const int64_t *active_idx, int64_t n_active,
     return sfg::accel_tidal(&tree->t, active_idx, n_active, accel, phi, tidal, (cudaStream_t)stream);
 }
 
+int sfg_set_relative_criterion(sfg_tree *tree, const double *g_prev, double alpha, void *stream)
+{
+    if (!tree || (g_prev && (!(alpha >= 0.0) || !std::isfinite(alpha)))) return SFG_EINVAL;
+    tree->t.stream = (cudaStream_t)stream;
+    cudaGetLastError();
+    return sfg::set_relative(&tree->t, g_prev, alpha, (cudaStream_t)stream);
+}
+
 int sfg_tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, void *stream)
 {
     if (n < 0 || (n > 0 && (!tidal || !dt)) || !(eta > 0.0) || !std::isfinite(eta)) return SFG_EINVAL;

@@ -352,18 +352,61 @@ __global__ void k_pack(const double *pos, const double *mass, const double *soft
 }
 
 // --------------------------------------------------------------- octree ----
+// Every KS-th sorted key, so that the child boundaries of a large node are
+// first bracketed in this small, cache-resident array and then searched in a
+// window of at most KS keys, instead of by long strides through the keys.
+constexpr int KS_LOG = 8, KS = 1 << KS_LOG;
+
+__global__ void k_key_samples(const uint64_t *key, int n, uint64_t *ks)
+{
+    const int ns = (n + KS - 1) >> KS_LOG;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x)
+        ks[j] = key[(size_t)j << KS_LOG];
+}
+
 // Child boundaries of the node [f, e) at child shift cshift: s[d] = first
-// index whose child digit is >= d (s[0] = f, s[8] = e).  The seven binary
-// searches run in lockstep, so their loads overlap instead of chaining.
-__device__ inline void digit_bounds(const uint64_t *key, int f, int e, int cshift, int s[9])
+// index whose child digit is >= d (s[0] = f, s[8] = e; digits are
+// non-decreasing inside the node).  The seven searches run in lockstep so
+// their loads overlap; a node longer than a few sample strides is bracketed
+// on the samples first.
+__device__ inline void digit_bounds(const uint64_t *key, const uint64_t *ks, int f, int e, int cshift, int s[9])
 {
     int lo[7], hi[7];
+    const int k0 = (f + KS - 1) >> KS_LOG, k1 = (e - 1) >> KS_LOG; // samples inside [f, e): k0..k1
+    if (k1 - k0 >= 4) {
+        // first sample k in [k0, k1 + 1) with digit >= d
 #pragma unroll
-    for (int d = 0; d < 7; d++) {
-        lo[d] = f;
-        hi[d] = e;
+        for (int d = 0; d < 7; d++) {
+            lo[d] = k0;
+            hi[d] = k1 + 1;
+        }
+        for (int it = 0; it < 32 && (1 << it) <= k1 + 1 - k0; it++) {
+#pragma unroll
+            for (int d = 0; d < 7; d++) {
+                if (lo[d] < hi[d]) {
+                    int mid = (lo[d] + hi[d]) >> 1;
+                    if (((ks[mid] >> cshift) & 7u) < (uint32_t)(d + 1)) lo[d] = mid + 1;
+                    else hi[d] = mid;
+                }
+            }
+        }
+        // the boundary lies after sample k - 1 and at or before sample k
+#pragma unroll
+        for (int d = 0; d < 7; d++) {
+            const int k = lo[d];
+            lo[d] = k == k0 ? f : ((k - 1) << KS_LOG) + 1;
+            hi[d] = k > k1 ? e : (k << KS_LOG);
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < 7; d++) {
+            lo[d] = f;
+            hi[d] = e;
+        }
     }
-    const int n = e - f;
+    int n = 0;
+#pragma unroll
+    for (int d = 0; d < 7; d++) n = max(n, hi[d] - lo[d]);
     for (int it = 0; it < 32 && (1 << it) <= n; it++) {
 #pragma unroll
         for (int d = 0; d < 7; d++) {
@@ -397,7 +440,7 @@ __global__ void k_oct_root(const int64_t *off, int C, int32_t *nfirst, int32_t *
     }
 }
 
-__global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int leaf_size, int cap,
+__global__ void k_oct_count(const uint64_t *key, const uint64_t *ks, const int *lvl, int level, int leaf_size, int cap,
                             const int32_t *nfirst, const int32_t *ncount, int *tmp, int *status)
 {
     int b = lvl[level], e = lvl[level + 1];
@@ -410,7 +453,7 @@ __global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int 
         int nch = 0;
         if (c > leaf_size && level < SFG_LMAX) {
             int sb[9];
-            digit_bounds(key, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
+            digit_bounds(key, ks, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
 #pragma unroll
             for (int d = 0; d < 8; d++) nch += sb[d + 1] > sb[d];
         }
@@ -418,7 +461,8 @@ __global__ void k_oct_count(const uint64_t *key, const int *lvl, int level, int 
     }
 }
 
-__global__ void k_oct_write(const uint64_t *key, const int *lvl, int level, int leaf_size, int cap, int32_t *nfirst,
+__global__ void k_oct_write(const uint64_t *key, const uint64_t *ks, const int *lvl, int level, int leaf_size, int cap,
+                            int32_t *nfirst,
                             int32_t *ncount, int32_t *nparent, int32_t *nchild_first, int32_t *nnchild,
                             int32_t *nlevel, int32_t *ncloud, const int *tmp_off, int *status)
 {
@@ -433,7 +477,7 @@ __global__ void k_oct_write(const uint64_t *key, const int *lvl, int level, int 
         }
         int cf = next + tmp_off[node - b];
         int sb[9];
-        digit_bounds(key, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
+        digit_bounds(key, ks, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
         int k = 0;
         const int cl = ncloud[node];
         for (int d = 0; d < 8; d++) {
@@ -628,6 +672,8 @@ __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
 
 // Leaves of every level (one thread per leaf), then internal nodes one level
 // at a time from the deepest (one thread per node; its children are final).
+// (A node's FP64 reduction runs on one lane, so the internal levels keep
+// whole warps busy only when each level is its own pass.)
 __global__ void k_leaf_moments(MomArgs A)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nn; i += gridDim.x * blockDim.x) {
@@ -792,6 +838,10 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     // 0.32, 0.16 for leaf sizes 1, 4, 8, 16, 32
     int64_t cap64 = 6 * ((int64_t)n / (t->prm.leaf_size + 2)) + 4096 + 64 * (int64_t)C;
     int *tmp = nullptr, *tmpo = nullptr;
+    uint64_t *ks = nullptr;
+    ALLOC(ks, uint64_t, (n + KS - 1) / KS);
+    k_key_samples<<<grid_for((n + KS - 1) / KS, BT), BT, 0, s>>>(t->key, n, ks);
+    t->n_launch += 1;
     for (int attempt = 0;; attempt++) {
         if (cap64 > 0x7fffffff) cap64 = 0x7fffffff;
         int cap = (int)cap64;
@@ -805,11 +855,11 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         // grid-stride over a level (its size is only known on the device)
         const int og = std::min(grid_for(cap, BT), num_sms() * 4);
         for (int level = 0; level <= SFG_LMAX; level++) {
-            k_oct_count<<<og, BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+            k_oct_count<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, tmp, t->d_status);
             scan_range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
                        t->d_lvl + level + 1, scr, s);
-            k_oct_write<<<og, BT, 0, s>>>(t->key, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+            k_oct_write<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, t->nparent, t->nchild_first, t->nnchild,
                                                          t->nlevel, t->ncloud, tmpo, t->d_status);
         }
@@ -827,6 +877,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         cap64 *= 2;
         if (attempt > 8) return SFG_ENOMEM;
     }
+    dev_free(t, ks, s);
     const int nn = t->lvl_off[SFG_LMAX + 2];
     t->nn = nn;
     t->depth = 0;

@@ -106,6 +106,10 @@ struct Tree {
     int64_t la_cap = 0, la_n = -1;
     bool la_all = false;   // it was NULL (every particle)
     bool lists_ok = false;
+    // relative opening criterion: |g_prev| per sorted rank, alpha
+    double *gps = nullptr;
+    double rel_alpha = 0.0;
+    bool rel_on = false;
     int *d_flag = nullptr;       // device scratch word
     long long *d_lscan = nullptr; // list-offset scan scratch + totals
     std::unordered_set<void *> live; // every device allocation still held
@@ -134,6 +138,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
 int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *accel, double *phi, double *tidal,
                 cudaStream_t s);
 int tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, cudaStream_t s);
+int set_relative(Tree *t, const double *g_prev, double alpha, cudaStream_t s);
 int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
                 int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s);
 

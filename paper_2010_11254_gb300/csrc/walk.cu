@@ -82,6 +82,9 @@ struct WalkParams {
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
+    // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
+    const double *gps;
+    double ralpha, rG;
     unsigned long long *counters; // [0] p2p [1] p2m [2] overflowed groups [3] work [4] retry work
     int *ovf_list;
     int *status;
@@ -124,6 +127,9 @@ struct Tgt {
     int tp, R, tl, slice;
     float s22;                  // half-cell size of the group's cloud (FP32)
     double x64[3], h64, hinv64; // all-FP64 evaluation only
+    // relative criterion: alpha * min |g_prev| over the group, the cloud's root side, cell^2
+    bool rel;
+    double rel_ag, rel_L0, rel_cell2;
 };
 
 // ------------------------------------------------------------ kernels ----
@@ -658,9 +664,9 @@ __device__ __forceinline__ void stage_p2p(const WalkParams &P, SM &S, int cnt, i
 // leaf, or an internal node wholly inside the group's softening reach, whose
 // leaves would all be opened); op = open (push its children).  link/cnt:
 // child range (op) or particle range (lf).
-__device__ __forceinline__ void test_node(const WalkParams &P, int node, const int glo[3], const int ghi[3],
-                                          unsigned long long hq, bool &acc, bool &lf, bool &op, bool &nw, int &link,
-                                          int &cnt)
+__device__ __forceinline__ void test_node(const WalkParams &P, const Tgt &T, int node, const int glo[3],
+                                          const int ghi[3], unsigned long long hq, bool &acc, bool &lf, bool &op,
+                                          bool &nw, int &link, int &cnt)
 {
     acc = lf = op = nw = false;
     link = cnt = 0;
@@ -681,6 +687,15 @@ __device__ __forceinline__ void test_node(const WalkParams &P, int node, const i
                             (unsigned long long)gb2 * (unsigned)gb2;
     unsigned long long need = nhq > hq ? nhq : hq;
     acc = sc >= P.T[level] && sb >= need;
+    if (acc && T.rel) {
+        // relative criterion (Sec. 2.2, from GADGET-2), conservative for every
+        // target: G M L^2 <= alpha min|g_prev| (sc cell^2)^2, the same IEEE
+        // products in the same order as the oracle's
+        const double L = ldexp(T.rel_L0, -level);
+        const double lhs = __dmul_rn(__dmul_rn(P.rG, P.nM[node]), __dmul_rn(L, L));
+        const double r2 = __dmul_rn((double)sc, T.rel_cell2);
+        acc = lhs <= __dmul_rn(T.rel_ag, __dmul_rn(r2, r2));
+    }
     lf = !acc && leaf;
     op = !acc && !leaf;
     // an opened leaf that passes clause (ii): every pair it contributes is
@@ -907,6 +922,15 @@ __device__ __forceinline__ void setup_group(const WalkParams &P, int g, int lane
         unsigned long long t = __shfl_xor_sync(FULL, hq, o);
         hq = t > hq ? t : hq;
     }
+    T.rel = P.gps != nullptr;
+    if (T.rel) {
+        double gm = T.has ? P.gps[T.r] : __longlong_as_double(0x7ff0000000000000ll);
+        for (int o = 16; o > 0; o >>= 1) gm = fmin(gm, __shfl_xor_sync(FULL, gm, o));
+        T.rel_ag = __dmul_rn(P.ralpha, gm);
+        T.rel_L0 = fr.L0;
+        const double cell = ldexp(fr.L0, -SFG_LMAX);
+        T.rel_cell2 = __dmul_rn(cell, cell);
+    }
     double c0 = fr.x0[0] + (double)T.cg[0] * fr.half_cell;
     double c1 = fr.x0[1] + (double)T.cg[1] * fr.half_cell;
     double c2 = fr.x0[2] + (double)T.cg[2] * fr.half_cell;
@@ -1052,7 +1076,7 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
         }
         bool acc, lf, op, nw;
         int link, cnt;
-        test_node(P, node, glo, ghi, hq, acc, lf, op, nw, link, cnt);
+        test_node(P, T, node, glo, ghi, hq, acc, lf, op, nw, link, cnt);
         unsigned bo = __ballot_sync(FULL, op);
         int npush = __popc(bo);
         if (W.sp + npush > cap) {
@@ -2194,6 +2218,9 @@ struct Work {
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
+    // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
+    const double *gps;
+    double ralpha, rG;
     int *cnt, *kcnt, *is_split, *soff, *ioff, *gdone, *hist; // cnt: NCNT list sizes per group
     long long *lmo, *lro; // stored lists: first P2M entry / first P2P range of every group (exclusive scans)
     int2 *items;
@@ -2319,6 +2346,9 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
         double v = ldexp(1.0, 2 * (SFG_LMAX - l)) / (th * th);
         P.T[l] = (v < 4611686018427387904.0) ? (unsigned long long)ceil(v) : SFG_CAP62;
     }
+    P.gps = t->rel_on ? t->gps : nullptr;
+    P.ralpha = t->rel_alpha;
+    P.rG = t->prm.G;
     P.gtab = w.gtab;
     P.tgt = w.tgt;
     P.res_a = w.res_a;
@@ -2600,6 +2630,30 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
     }
     t->n_launch += 1;
     ph_end(t, PH_FWD, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+__global__ void k_gather_sorted(const double *g, const int32_t *order, int n, double *gs)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) gs[r] = g[order[r]];
+}
+
+int set_relative(Tree *t, const double *g_prev, double alpha, cudaStream_t s)
+{
+    t->lists_ok = false; // lists depend on the opening criterion
+    if (!g_prev) {
+        t->rel_on = false;
+        return SFG_OK;
+    }
+    if (!t->gps) {
+        t->gps = (double *)dev_alloc(t, sizeof(double) * (size_t)t->n, s);
+        if (!t->gps) return SFG_ENOMEM;
+    }
+    k_gather_sorted<<<grid_for(t->n, 256), 256, 0, s>>>(g_prev, t->order, (int)t->n, t->gps);
+    t->n_launch += 1;
+    t->rel_on = true;
+    t->rel_alpha = alpha;
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
 }
