@@ -101,6 +101,11 @@ def _load():
         lib.sfgo_tidal_group.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _f64p]
         lib.sfgo_tidal_dt.restype = None
         lib.sfgo_tidal_dt.argtypes = [ctypes.c_int64, _f64p, ctypes.c_double, _f64p]
+        lib.sfgo_direct_jerk.restype = None
+        lib.sfgo_direct_jerk.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, _u8p, ctypes.c_double,
+                                         ctypes.c_int64, _i64p, _f64p]
+        lib.sfgo_jerk_group.restype = ctypes.c_int
+        lib.sfgo_jerk_group.argtypes = [_vp, _f64p, ctypes.c_double, _i64p, ctypes.c_int64, _f64p]
         lib.sfgo_set_relative.restype = None
         lib.sfgo_set_relative.argtypes = [_vp, _f64p, ctypes.c_double, ctypes.c_double]
         lib.sfgo_num_threads.restype = ctypes.c_int
@@ -176,6 +181,18 @@ def direct_tidal(pos, mass, soft, is_sink=None, targets=None, G: float = 1.0):
     _load().sfgo_direct_tidal(n, _p(pos, _f64p), _p(mass, _f64p), _p(soft, _f64p), _p(sink, _u8p), float(G),
                               tg.size, _p(tg, _i64p), _p(T, _f64p))
     return T
+
+
+def direct_jerk(pos, vel, mass, soft, is_sink=None, targets=None, G: float = 1.0):
+    """FP64 direct-sum jerk j = da/dt (Sec. 2.2) at the targets, [n][3]."""
+    pos, vel, mass, soft = _f64(pos), _f64(vel), _f64(mass), _f64(soft)
+    n = pos.shape[0]
+    tg = _i64(np.arange(n) if targets is None else targets)
+    sink = _u8(np.zeros(n) if is_sink is None else is_sink)
+    J = np.zeros((tg.size, 3))
+    _load().sfgo_direct_jerk(n, _p(pos, _f64p), _p(vel, _f64p), _p(mass, _f64p), _p(soft, _f64p), _p(sink, _u8p),
+                             float(G), tg.size, _p(tg, _i64p), _p(J, _f64p))
+    return J
 
 
 def tidal_dt(tidal, eta: float):
@@ -284,6 +301,15 @@ class Tree:
             return
         g = _f64(g_prev)
         self._lib.sfgo_set_relative(self._h, _p(g, _f64p), float(alpha), float(G))
+
+    def jerk_group(self, vel, idx, G: float = 1.0):
+        """Group-form jerk [n][3] on the last walk's lists (nodes by monopole)."""
+        vel, idx = _f64(vel), _i64(idx)
+        J = np.zeros((idx.size, 3))
+        rc = self._lib.sfgo_jerk_group(self._h, _p(vel, _f64p), float(G), _p(idx, _i64p), idx.size, _p(J, _f64p))
+        if rc != 0:
+            raise ValueError("a requested row is not a walked target")
+        return J
 
     def tidal_group(self, idx, G: float = 1.0, quadrupole: bool = True):
         """Group-form tidal tensor [n][6] (xx yy zz xy xz yz) on the last walk's lists."""

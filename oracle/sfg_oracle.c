@@ -174,6 +174,42 @@ void sfgo_direct_tidal(int64_t n, const double *pos, const double *mass, const d
     }
 }
 
+/* One pair's jerk term (per unit G m_j): the time derivative of a = m K(r) d
+ * along the motion, d = x_j - x_i, w = v_j - v_i:
+ *   j += K w + (dK/dr / r) (d . w) d
+ * (Sec. 2.2: j in the same pass as g, with spatial derivatives of the same
+ * softened kernel and symmetrisation, Sec. 2.2.1). */
+static void pair_jerk(double m, double K, double Kr, const double d[3], const double w[3], double j[3])
+{
+    double dw = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+    for (int a = 0; a < 3; a++) j[a] += m * (K * w[a] + Kr * dw * d[a]);
+}
+
+/* Direct-sum jerk at the targets (all pairs j != i), vel [n][3]. */
+void sfgo_direct_jerk(int64_t n, const double *pos, const double *vel, const double *mass, const double *soft,
+                      const uint8_t *sink, double G, int64_t nt, const int64_t *targets, double *jerk)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets[t];
+        double J[3] = {0, 0, 0};
+        for (int64_t k = 0; k < n; k++) {
+            if (k == i)
+                continue;
+            double d[3], w[3];
+            for (int a = 0; a < 3; a++) {
+                d[a] = pos[3 * k + a] - pos[3 * i + a];
+                w[a] = vel[3 * k + a] - vel[3 * i + a];
+            }
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double K, P, Kr;
+            pair_law(r, soft[i], soft[k], sink ? sink[i] : 0, sink ? sink[k] : 0, &K, &P, &Kr);
+            pair_jerk(mass[k], K, Kr, d, w, J);
+        }
+        for (int a = 0; a < 3; a++) jerk[3 * t + a] = G * J[a];
+    }
+}
+
 /* Tidal timestep of Sec. 2.3, Eq. for Delta t_tidal: sqrt(eta) (|T|^2 / 6)^(-1/4)
  * with |T| the Frobenius norm (T given as xx yy zz xy xz yz); infinite when T = 0. */
 void sfgo_tidal_dt(int64_t n, const double *tidal, double eta, double *dt)
@@ -981,6 +1017,78 @@ int sfgo_tidal_group(const sfgo_tree *t, double G, int quad, const int64_t *idx,
         }
         for (int c = 0; c < 6; c++) tidal[6 * k + c] = G * T[c];
     }
+    return bad ? -1 : 0;
+}
+
+/* Group-form jerk at the listed original indices on the last walk's lists,
+ * vel [n][3] in the input order.  Pairs as sfgo_direct_jerk; an accepted node
+ * contributes its monopole term (Sec. 2.2 sums T and j from the monopole
+ * contributions of nodes): M [w / r^3 - 3 (d . w) d / r^5], d = com - x_i,
+ * w = v_com - v_i, with the node's mass-weighted velocity v_com summed like
+ * the centre of mass (members in sorted order, children in octant order). */
+int sfgo_jerk_group(const sfgo_tree *t, const double *vel, double G, const int64_t *idx, int64_t n_idx,
+                    double *jerk)
+{
+    int64_t n = t->n, nn = t->nn;
+    double *vs = (double *)malloc(24 * n), *pn = (double *)malloc(24 * nn), *vn = (double *)malloc(24 * nn);
+    for (int64_t r = 0; r < n; r++)
+        for (int a = 0; a < 3; a++) vs[3 * r + a] = vel[3 * t->order[r] + a];
+    for (int64_t i = nn - 1; i >= 0; i--) { /* node momenta, then velocities */
+        const onode *nd = &t->nodes[i];
+        double p[3] = {0, 0, 0};
+        if (nd->nchild == 0) {
+            for (int64_t k = nd->first; k < nd->first + nd->count; k++)
+                for (int a = 0; a < 3; a++) p[a] = p[a] + t->mass[k] * vs[3 * k + a];
+        } else {
+            for (int q = 0; q < nd->nchild; q++)
+                for (int a = 0; a < 3; a++) p[a] = p[a] + pn[3 * (nd->child_first + q) + a];
+        }
+        for (int a = 0; a < 3; a++) {
+            pn[3 * i + a] = p[a];
+            vn[3 * i + a] = nd->M > 0.0 ? p[a] / nd->M : 0.0;
+        }
+    }
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n_idx; k++) {
+        int64_t r = t->rank[idx[k]];
+        if (t->tgroup[r] < 0 || !t->groups[t->tgroup[r]].walked) {
+            bad = 1;
+            continue;
+        }
+        const ogroup *g = &t->groups[t->tgroup[r]];
+        const double *x = t->pos + 3 * r, *v = vs + 3 * r;
+        double J[3] = {0, 0, 0};
+        for (int64_t q = 0; q < g->n_p2m; q++) {
+            int64_t ni = g->p2m[q];
+            const onode *nd = &t->nodes[ni];
+            double d[3], w[3];
+            for (int a = 0; a < 3; a++) {
+                d[a] = nd->com[a] - x[a];
+                w[a] = vn[3 * ni + a] - v[a];
+            }
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
+            pair_jerk(nd->M, ir3, -3.0 * ir3 * ir * ir, d, w, J);
+        }
+        for (int64_t q = 0; q < g->n_p2p; q++) {
+            const onode *nd = &t->nodes[g->p2p[q]];
+            for (int64_t j = nd->first; j < nd->first + nd->count; j++) {
+                if (j == r) continue;
+                double d[3], w[3];
+                for (int a = 0; a < 3; a++) {
+                    d[a] = t->pos[3 * j + a] - x[a];
+                    w[a] = vs[3 * j + a] - v[a];
+                }
+                double rr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                double K, P, Kr;
+                pair_law(rr, t->soft[r], t->soft[j], t->sink[r], t->sink[j], &K, &P, &Kr);
+                pair_jerk(t->mass[j], K, Kr, d, w, J);
+            }
+        }
+        for (int a = 0; a < 3; a++) jerk[3 * k + a] = G * J[a];
+    }
+    free(vs); free(pn); free(vn);
     return bad ? -1 : 0;
 }
 
