@@ -184,6 +184,23 @@ int sfg_accel_tidal(sfg_tree *tree, const int64_t *active_idx, int64_t n_active,
  * (NULL tree, bad alpha), SFG_ENOMEM, SFG_ECUDA. */
 int sfg_set_relative_criterion(sfg_tree *tree, const double *g_prev, double alpha, void *stream);
 
+/* Field, potential and gravitational jerk j = dg/dt at the active particles
+ * (Sec. 2.2: j is summed in the same pass and with the same opening
+ * criterion as g; pairs use spatial derivatives of the same softened kernel
+ * with the same symmetrisation, nodes their monopole contributions).  With
+ * d = x_j - x_i and w = v_j - v_i, a pair adds
+ *   G m_j [K w + (dK/dr / r) (d . w) d]      (a = G m_j K d),
+ * an accepted node G M [w / r^3 - 3 (d . w) d / r^5] with d from the target
+ * to its centre of mass and w from the target's velocity to the node's
+ * mass-weighted velocity (FP64 sums, members in sorted order, children in
+ * octant order).  accel and phi are as for sfg_accel.
+ *   vel  [n][3] float64, device: every particle's velocity (input order)
+ *   jerk [n_active][3] float64, device, overwritten
+ * Sums are FP32 per lane and per work item.  Stored lists, precision and
+ * capture rules and errors as for sfg_accel_tidal. */
+int sfg_accel_jerk(sfg_tree *tree, const double *vel, const int64_t *active_idx, int64_t n_active, double *accel,
+                   double *phi, double *jerk, void *stream);
+
 /* Tidal timestep constraint of Sec. 2.3:
  *   dt[k] = sqrt(eta) * (|T_k|^2 / 6)^(-1/4),
  * |T| the Frobenius norm of the symmetric tensor given by its six components

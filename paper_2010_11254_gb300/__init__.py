@@ -94,6 +94,8 @@ def _load():
         lib.sfg_accel_tidal.restype = i32
         lib.sfg_tidal_timestep.argtypes = [vp, i64, ctypes.c_double, vp, vp]
         lib.sfg_tidal_timestep.restype = i32
+        lib.sfg_accel_jerk.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+        lib.sfg_accel_jerk.restype = i32
         lib.sfg_set_relative_criterion.argtypes = [vp, vp, ctypes.c_double, vp]
         lib.sfg_set_relative_criterion.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -213,6 +215,19 @@ class Tree:
         with torch.cuda.device(self.device):
             rc = _load().sfg_set_relative_criterion(self._h, ptr, float(alpha), _stream(self.device))
         _check(rc, "sfg_set_relative_criterion")
+
+    def accel_jerk(self, vel, active=None):
+        """(accel [n][3], phi [n], jerk [n][3]) at the active rows; vel [N][3] per particle."""
+        a, na = self._active(active)
+        vel = _dev(vel, torch.float64, "vel")
+        acc = torch.empty((na, 3), dtype=torch.float64, device=self.device)
+        phi = torch.empty(na, dtype=torch.float64, device=self.device)
+        jerk = torch.empty((na, 3), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            rc = _load().sfg_accel_jerk(self._h, vel.data_ptr(), None if a is None else a.data_ptr(), na,
+                                        acc.data_ptr(), phi.data_ptr(), jerk.data_ptr(), _stream(self.device))
+        _check(rc, "sfg_accel_jerk")
+        return acc, phi, jerk
 
     def accel_tidal(self, active=None):
         """(accel [n][3], phi [n], tidal [n][6] = xx yy zz xy xz yz) at the active rows."""

@@ -83,8 +83,8 @@ struct Tree {
     float4 *E0 = nullptr, *E1 = nullptr, *E2 = nullptr;
     double *nM = nullptr, *ncom = nullptr, *nQ = nullptr, *nhmax = nullptr;
     // per-call workspace (grow-only)
-    void *ws = nullptr, *ws2 = nullptr, *ws3 = nullptr; // forward, adjoint, tidal sums
-    size_t ws_bytes = 0, ws2_bytes = 0, ws3_bytes = 0;
+    void *ws = nullptr, *ws2 = nullptr, *ws3 = nullptr, *ws4 = nullptr; // forward, adjoint, tidal, jerk
+    size_t ws_bytes = 0, ws2_bytes = 0, ws3_bytes = 0, ws4_bytes = 0;
     sfg_stats last{};
     // [0] p2p, [1] p2m, [2] overflowed groups, [3] work, [4] retry work, [5] groups, [6] distinct targets,
     // [7] item cost total, [8] Newtonian-list P2P interactions
@@ -139,6 +139,8 @@ int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *accel,
                 cudaStream_t s);
 int tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, cudaStream_t s);
 int set_relative(Tree *t, const double *g_prev, double alpha, cudaStream_t s);
+int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double *accel, double *phi,
+               double *jerk, cudaStream_t s);
 int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
                 int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s);
 

@@ -38,7 +38,8 @@ constexpr int WALK_MINB = 6;   // resident blocks per SM the register budget mus
 constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
 constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
 constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4, MODE_LIST = 5,
-              MODE_TIDAL = 6; // MODE_TIDAL: forward evaluation plus the tidal tensor (stored lists only)
+              MODE_TIDAL = 6, // forward evaluation plus the tidal tensor (stored lists only)
+              MODE_JERK = 7;  // forward evaluation plus the jerk (stored lists only)
 // list sizes per group written by the counting walk: P2M nodes, softened P2P
 // ranges and particles, Newtonian P2P ranges and particles
 constexpr int NCNT = 5;
@@ -82,6 +83,9 @@ struct WalkParams {
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
+    float *res_J;        // jerk mode: [U][4] = j (x y z), -; summed
+    const float4 *pv;    // jerk mode: particle velocities, sorted (FP32)
+    const float4 *nV;    // jerk mode: node mass-weighted velocities (FP32 of the FP64 sums)
     // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
     const double *gps;
     double ralpha, rG;
@@ -127,6 +131,7 @@ struct Tgt {
     int tp, R, tl, slice;
     float s22;                  // half-cell size of the group's cloud (FP32)
     double x64[3], h64, hinv64; // all-FP64 evaluation only
+    float vx, vy, vz; // jerk mode: the target's velocity
     // relative criterion: alpha * min |g_prev| over the group, the cloud's root side, cell^2
     bool rel;
     double rel_ag, rel_L0, rel_cell2;
@@ -955,7 +960,7 @@ __device__ __forceinline__ void finish_targets(const WalkParams &P, const Tgt &T
         az += __shfl_xor_sync(FULL, az, o);
         phi += __shfl_xor_sync(FULL, phi, o);
     }
-    if (MODE == MODE_EVAL || MODE == MODE_TIDAL) {
+    if (MODE == MODE_EVAL || MODE == MODE_TIDAL || MODE == MODE_JERK) {
         if (K == 1) {
             if (T.has && T.slice == 0) {
                 P.res_a[tfirst + T.tl] = make_float4(ax, ay, az, 0.f);
@@ -1153,7 +1158,9 @@ struct EvalSmem {
     float4 sAcc[32]; // per-target sums of the softened pairs: forward (a, phi), adjoint (-dL/dx_i, -)
     float4 gC[32];   // adjoint: the targets' cotangents (cot_a, cot_phi)
     float4 sS[32];   // adjoint: per-source sums of the softened pairs of a tile (dL/dx_j, dL/dm_j)
-    float sTid[32][8]; // tidal mode: per-target sums of the softened pairs (as res_T)
+    float sTid[32][8]; // tidal / jerk mode: per-target sums of the softened pairs (as res_T / res_J)
+    float4 tV[32];     // jerk mode: source velocities of the tile
+    float4 gV[32];     // jerk mode: the group's target velocities
     unsigned short sq[1024]; // softened pairs of a tile: target | source << 5
 };
 
@@ -1335,9 +1342,25 @@ __device__ __forceinline__ void tid_add_dd(TidAcc &A, float c, float dx, float d
     A.t[5] = fmaf(cy, dz, A.t[5]);
 }
 
+// Jerk of one term of the field a = c d (c = m K(r)), d the source minus the
+// target position and w the source minus the target velocity:
+// j += c w + m (dK/dr / r) (d . w) d, here for the Newtonian kernel
+// (dK/dr / r = -3 K / r^2), mK = m K.  In jerk mode t[0..2] of the extra
+// accumulator hold j.
+__device__ __forceinline__ void jerk_add(TidAcc &A, float mK, float ri2, float dx, float dy, float dz, float wx,
+                                         float wy, float wz)
+{
+    const float c2 = -3.f * mK * ri2 * fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+    A.t[0] = fmaf(mK, wx, fmaf(c2, dx, A.t[0]));
+    A.t[1] = fmaf(mK, wy, fmaf(c2, dy, A.t[1]));
+    A.t[2] = fmaf(mK, wz, fmaf(c2, dz, A.t[2]));
+}
+
 // P2M with its tidal term: monopole -M I / r^3 + 3 M d d^T / r^5; quadrupole
 // Q / r^5 - 5 (Qd d^T + d Qd^T) / r^7 - 5/2 q I / r^7 + 35/2 q d d^T / r^9.
-template <bool QUAD, class SM>
+// Jerk mode: the node's monopole jerk (Sec. 2.2 sums j from the monopole
+// contributions of nodes), with its mass-weighted velocity.
+template <int MODE, bool QUAD, class SM>
 __device__ __forceinline__ void tid_p2m_step(const SM &S, int k, const Tgt &T, float &ax, float &ay, float &az,
                                              float &pt, TidAcc &A)
 {
@@ -1361,6 +1384,11 @@ __device__ __forceinline__ void tid_p2m_step(const SM &S, int k, const Tgt &T, f
         ay = fmaf(c, dy, fmaf(-ri5, Qd1, ay));
         az = fmaf(c, dz, fmaf(-ri5, Qd2, az));
         pt = fmaf(-p.w, rinv, fmaf(-0.5f, t, pt));
+        if (MODE == MODE_JERK) {
+            const float4 v = S.tV[k];
+            jerk_add(A, Mri3, ri2, dx, dy, dz, v.x - T.vx, v.y - T.vy, v.z - T.vz);
+            return;
+        }
         A.iso += c; // M / r^3 + 5/2 q / r^7
         tid_add_dd(A, fmaf(17.5f * t, ri2 * ri2, 3.f * Mri3 * ri2), dx, dy, dz);
         const float b = -5.f * ri5 * ri2;
@@ -1376,23 +1404,28 @@ __device__ __forceinline__ void tid_p2m_step(const SM &S, int k, const Tgt &T, f
         ay = fmaf(Mri3, dy, ay);
         az = fmaf(Mri3, dz, az);
         pt = fmaf(-p.w, rinv, pt);
+        if (MODE == MODE_JERK) {
+            const float4 v = S.tV[k];
+            jerk_add(A, Mri3, ri2, dx, dy, dz, v.x - T.vx, v.y - T.vy, v.z - T.vz);
+            return;
+        }
         A.iso += Mri3;
         tid_add_dd(A, 3.f * Mri3 * ri2, dx, dy, dz);
     }
 }
 
-template <bool QUAD, class SM>
+template <int MODE, bool QUAD, class SM>
 __device__ __forceinline__ void tid_p2m(const SM &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
                                         double &phi, TidAcc &A)
 {
     float pt = 0.f;
-    for (int k = T.slice; k < cnt; k += T.R) tid_p2m_step<QUAD>(S, k, T, ax, ay, az, pt, A);
+    for (int k = T.slice; k < cnt; k += T.R) tid_p2m_step<MODE, QUAD>(S, k, T, ax, ay, az, pt, A);
     phi += (double)pt;
 }
 
 // Newtonian pair (every pair of a Newtonian range; the pairs outside both
 // supports of a softened range, the others flagged in mask).
-template <bool SOFT, class SM>
+template <int MODE, bool SOFT, class SM>
 __device__ __forceinline__ void tid_p2p_step(const SM &S, int k, const Tgt &T, float ht2, float &ax, float &ay,
                                              float &az, float &pt, unsigned &mask, TidAcc &A)
 {
@@ -1412,6 +1445,11 @@ __device__ __forceinline__ void tid_p2p_step(const SM &S, int k, const Tgt &T, f
     ay = fmaf(mr3, dy, ay);
     az = fmaf(mr3, dz, az);
     pt -= mr;
+    if (MODE == MODE_JERK) {
+        const float4 v = S.tV[k];
+        jerk_add(A, mr3, ri2, dx, dy, dz, v.x - T.vx, v.y - T.vy, v.z - T.vz);
+        return;
+    }
     A.iso += mr3;
     tid_add_dd(A, 3.f * mr3 * ri2, dx, dy, dz);
 }
@@ -1493,7 +1531,7 @@ __device__ __forceinline__ void fwd_p2p_defer(EvalSmem &S, int cnt, const Tgt &T
 // Tidal mode, one P2P tile: Newtonian pairs on the lanes; for a softened
 // range the pairs inside max(h_i, h_j) are deferred as in fwd_p2p_defer and
 // evaluated with K, P and dK/dr / r of the pair rule.
-template <bool SOFT>
+template <int MODE, bool SOFT>
 __device__ __forceinline__ void tid_p2p(EvalSmem &S, int cnt, const Tgt &T, float &ax, float &ay, float &az,
                                         double &phi, TidAcc &A, int lane)
 {
@@ -1501,7 +1539,7 @@ __device__ __forceinline__ void tid_p2p(EvalSmem &S, int cnt, const Tgt &T, floa
     unsigned mask = 0u;
     const float ht2 = T.h * T.h;
     if (T.has) {
-        for (int k = T.slice; k < cnt; k += T.R) tid_p2p_step<SOFT>(S, k, T, ht2, ax, ay, az, pt, mask, A);
+        for (int k = T.slice; k < cnt; k += T.R) tid_p2p_step<MODE, SOFT>(S, k, T, ht2, ax, ay, az, pt, mask, A);
     }
     phi += (double)pt;
     if (!SOFT) return;
@@ -1538,6 +1576,16 @@ __device__ __forceinline__ void tid_p2p(EvalSmem &S, int cnt, const Tgt &T, floa
                 atomicAdd(&S.sAcc[t].y, mK * dy);
                 atomicAdd(&S.sAcc[t].z, mK * dz);
                 atomicAdd(&S.sAcc[t].w, m * 0.5f * (P1 + P2));
+                if (MODE == MODE_JERK) {
+                    // j += m [K w + (dK/dr / r) (d . w) d]
+                    const float4 tv = S.gV[t], sv = S.tV[k];
+                    const float wx = sv.x - tv.x, wy = sv.y - tv.y, wz = sv.z - tv.z;
+                    const float c2 = mR * fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+                    atomicAdd(&S.sTid[t][0], fmaf(mK, wx, c2 * dx));
+                    atomicAdd(&S.sTid[t][1], fmaf(mK, wy, c2 * dy));
+                    atomicAdd(&S.sTid[t][2], fmaf(mK, wz, c2 * dz));
+                    continue;
+                }
                 // T += -m [K I + (dK/dr / r) d d^T]
                 atomicAdd(&S.sTid[t][0], -mR * dx * dx);
                 atomicAdd(&S.sTid[t][1], -mR * dy * dy);
@@ -1673,6 +1721,13 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
 }
 
 
+// Jerk mode: the velocity of this lane's staged source particle j (or node).
+__device__ __forceinline__ void stage_vel(const WalkParams &P, EvalSmem &S, int cnt, int j, int lane)
+{
+    if (lane < cnt) S.tV[lane] = (j >= 0 && j < P.npart) ? P.pv[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+}
+
 // This item's share of one P2P list: nr ranges holding np particles.
 template <int MODE, bool NEWT>
 __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, const Tgt &T, const int2 *rr, int nr,
@@ -1717,15 +1772,18 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
             rn += k;
             __syncwarp();
         }
+        constexpr bool EXTRA = MODE == MODE_TIDAL || MODE == MODE_JERK;
         if (NEWT) {
             stage_p2p_newt(P, S, c, qh, qoff, T, lane);
+            if (MODE == MODE_JERK) stage_vel(P, S, c, S.tN[lane & 31], lane);
             if (MODE == MODE_VJP) vjp_p2p_newt(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (MODE == MODE_TIDAL) tid_p2p<false>(S, c, T, ax, ay, az, phi, A, lane);
+            else if (EXTRA) tid_p2p<MODE, false>(S, c, T, ax, ay, az, phi, A, lane);
             else if (T.has) fwd_p2p_newt(S, c, T, ax, ay, az, phi);
         } else {
             stage_p2p(P, S, c, qh, qoff, T, lane);
+            if (MODE == MODE_JERK) stage_vel(P, S, c, __float_as_int(S.tA[lane & 31].z), lane);
             if (MODE == MODE_VJP) vjp_p2p_defer(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (MODE == MODE_TIDAL) tid_p2p<true>(S, c, T, ax, ay, az, phi, A, lane);
+            else if (EXTRA) tid_p2p<MODE, true>(S, c, T, ax, ay, az, phi, A, lane);
             else fwd_p2p_defer(S, c, T, ax, ay, az, phi, lane);
         }
         __syncwarp();
@@ -1757,9 +1815,18 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     }
     S.sAcc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     TidAcc A = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, 0.f};
-    if (MODE == MODE_TIDAL) {
+    constexpr bool EXTRA = MODE == MODE_TIDAL || MODE == MODE_JERK;
+    if (EXTRA) {
 #pragma unroll
         for (int c = 0; c < 8; c++) S.sTid[lane][c] = 0.f;
+    }
+    T.vx = T.vy = T.vz = 0.f;
+    if (MODE == MODE_JERK) {
+        const float4 v = T.has ? P.pv[T.r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        T.vx = v.x;
+        T.vy = v.y;
+        T.vz = v.z;
+        if (T.slice == 0) S.gV[T.tl] = v;
     }
     __syncwarp();
     const int *cn = P.lcnt + NCNT * (size_t)g;
@@ -1771,9 +1838,16 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         for (int tt = t0; tt < t1; tt++) {
             const int b = tt * 32, c = min(32, nm - b);
             stage_p2m<QUAD, MODE == MODE_VJP>(P, S, lm + b, c, T, lane);
+            if (MODE == MODE_JERK) {
+                if (lane < c) {
+                    const int id = lm[b + lane];
+                    S.tV[lane] = (unsigned)id < (unsigned)P.nn ? P.nV[id] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                __syncwarp();
+            }
             if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
-            else if (MODE == MODE_TIDAL) {
-                if (T.has) tid_p2m<QUAD>(S, c, T, ax, ay, az, phi, A);
+            else if (EXTRA) {
+                if (T.has) tid_p2m<MODE, QUAD>(S, c, T, ax, ay, az, phi, A);
             } else if (T.has) fwd_p2m<QUAD>(S, c, T, ax, ay, az, phi);
             __syncwarp();
         }
@@ -1786,13 +1860,24 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         ax += v.x;
         ay += v.y;
         az += v.z;
-        if (MODE == MODE_TIDAL) {
+        if (EXTRA) {
 #pragma unroll
             for (int c = 0; c < 6; c++) A.t[c] += S.sTid[T.tl][c];
             A.iso += S.sTid[T.tl][6];
         }
     }
     __syncwarp();
+    if (MODE == MODE_JERK) {
+        for (int o = T.tp; o < 32; o <<= 1) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) A.t[c] += __shfl_xor_sync(FULL, A.t[c], o);
+        }
+        if (T.has && T.slice == 0) {
+            float *dst = P.res_J + 4 * (size_t)(tfirst + T.tl);
+#pragma unroll
+            for (int c = 0; c < 3; c++) atomicAdd(dst + c, A.t[c]);
+        }
+    }
     if (MODE == MODE_TIDAL) {
         // slices -> one sum per target; items of a split group add theirs
         for (int o = T.tp; o < 32; o <<= 1) {
@@ -1815,7 +1900,7 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
 // resident blocks per SM of the evaluation kernel (the tidal mode carries
 // seven more accumulators per lane)
 constexpr int TIDAL_MINB = 4;
-constexpr int eval_minb(int mode) { return mode == MODE_TIDAL ? TIDAL_MINB : EVAL_MINB; }
+constexpr int eval_minb(int mode) { return mode == MODE_TIDAL || mode == MODE_JERK ? TIDAL_MINB : EVAL_MINB; }
 
 template <bool QUAD, int MODE>
 __global__ void __launch_bounds__(EVAL_WARPS * 32, eval_minb(MODE)) k_eval(WalkParams P)
@@ -2218,6 +2303,9 @@ struct Work {
     double *res_phi;
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
+    float *res_J;        // jerk mode: [U][4] = j (x y z), -; summed
+    const float4 *pv;    // jerk mode: particle velocities, sorted (FP32)
+    const float4 *nV;    // jerk mode: node mass-weighted velocities (FP32 of the FP64 sums)
     // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
     const double *gps;
     double ralpha, rG;
@@ -2704,6 +2792,139 @@ int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *acc, d
     k_rows_out_tidal<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, (int)t->n, t->rank, w.pre, P.res_T,
                                                              t->prm.G, tidal);
     t->n_launch += 2;
+    ph_end(t, PH_FWD, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+// ---- jerk mode: velocities of particles (sorted, FP32) and nodes ----
+__global__ void k_vel_sorted(const double *vel, const int32_t *order, int n, float4 *pv)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const double *v = vel + 3 * (size_t)order[r];
+        pv[r] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+    }
+}
+
+// Node momenta in FP64, like the centre of mass: a leaf sums m v over its
+// members in sorted order, an internal node its children's in octant order.
+__global__ void k_mom_leaf(const double *vel, const int32_t *order, const double *mass_s, const int32_t *nfirst,
+                           const int32_t *ncount, const int32_t *nnchild, int nn, double *np)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        if (nnchild[i] != 0) continue;
+        double p[3] = {0.0, 0.0, 0.0};
+        for (int k = nfirst[i]; k < nfirst[i] + ncount[i]; k++) {
+            const double m = mass_s[k];
+            const double *v = vel + 3 * (size_t)order[k];
+            for (int a = 0; a < 3; a++) p[a] = p[a] + m * v[a];
+        }
+        for (int a = 0; a < 3; a++) np[3 * (size_t)i + a] = p[a];
+    }
+}
+
+__global__ void k_mom_internal(const int32_t *nchild_first, const int32_t *nnchild, int b, int e, double *np)
+{
+    for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+        if (nnchild[i] == 0) continue;
+        double p[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < nnchild[i]; q++)
+            for (int a = 0; a < 3; a++) p[a] = p[a] + np[3 * (size_t)(nchild_first[i] + q) + a];
+        for (int a = 0; a < 3; a++) np[3 * (size_t)i + a] = p[a];
+    }
+}
+
+__global__ void k_node_vel(const double *np, const double *nM, int nn, float4 *nV)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        const double M = nM[i];
+        const double *p = np + 3 * (size_t)i;
+        nV[i] = M > 0.0 ? make_float4((float)(p[0] / M), (float)(p[1] / M), (float)(p[2] / M), 0.f)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Jerk rows in the caller's order, G applied, FP64.
+__global__ void k_rows_out_jerk(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
+                                const float *res_J, double G, double *jerk)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) continue;
+        const float *r = res_J + 4 * (size_t)pre[rank[i]];
+        for (int c = 0; c < 3; c++) jerk[3 * k + c] = G * (double)r[c];
+    }
+}
+
+// Field, potential and jerk (stored lists, like accel_tidal).
+int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double *acc, double *phi,
+               double *jerk, cudaStream_t s)
+{
+    if (n_active == 0) return SFG_OK;
+    if (t->prm.precision != 0 || capturing(s)) return SFG_EINVAL;
+    const int n = (int)t->n, nn = t->nn, BT = 256;
+    Work w;
+    WalkParams P;
+    ph_begin(t, PH_FWD, s);
+    int rc = prepare(t, active, n_active, w, P, s);
+    if (rc) return rc;
+    bool match = false;
+    rc = lists_match(t, active, n_active, s, match);
+    if (rc) return rc;
+    if (!match) {
+        rc = build_lists(t, w, P, s);
+        if (rc) return rc;
+        rc = remember_active(t, active, n_active, s);
+        if (rc) return rc;
+    }
+    items_from_counts(t, w, P, s, WT_EVAL);
+    // workspace: res_J [n][4] f32, pv [n] float4, node momenta [nn][3] f64, nV [nn] float4
+    const size_t need = align_up(16 * (size_t)n) + align_up(16 * (size_t)n) + align_up(24 * (size_t)nn) +
+                        align_up(16 * (size_t)nn);
+    if (t->ws4_bytes < need) {
+        if (t->ws4) dev_free(t, t->ws4, s);
+        t->ws4 = dev_alloc(t, need, s);
+        if (!t->ws4) {
+            t->ws4_bytes = 0;
+            return SFG_ENOMEM;
+        }
+        t->ws4_bytes = need;
+    }
+    char *p = (char *)t->ws4;
+    float *res_J = (float *)p;
+    p += align_up(16 * (size_t)n);
+    float4 *pv = (float4 *)p;
+    p += align_up(16 * (size_t)n);
+    double *np = (double *)p;
+    p += align_up(24 * (size_t)nn);
+    float4 *nV = (float4 *)p;
+    SFG_CUDA_OK(cudaMemsetAsync(res_J, 0, 16 * (size_t)n, s));
+    k_vel_sorted<<<grid_for(n, BT), BT, 0, s>>>(vel, t->order, n, pv);
+    k_mom_leaf<<<grid_for(nn, 128), 128, 0, s>>>(vel, t->order, t->mass_s, t->nfirst, t->ncount, t->nnchild, nn,
+                                                 np);
+    t->n_launch += 3;
+    for (int l = t->depth - 1; l >= 0; l--) {
+        const int b = t->lvl_off[l], e = t->lvl_off[l + 1];
+        k_mom_internal<<<grid_for(e - b, 128), 128, 0, s>>>(t->nchild_first, t->nnchild, b, e, np);
+        t->n_launch += 1;
+    }
+    k_node_vel<<<grid_for(nn, BT), BT, 0, s>>>(np, t->nM, nn, nV);
+    P.res_J = res_J;
+    P.pv = pv;
+    P.nV = nV;
+    if (t->timing) {
+        int rc2 = cloud_timer_begin(t, 0, s, P);
+        if (rc2) return rc2;
+    }
+    ph_begin(t, PH_FWD_WALK, s);
+    launch_eval<MODE_JERK>(t, P, s);
+    ph_end(t, PH_FWD_WALK, s);
+    k_rows_out<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, n, t->rank, w.pre, w.res_a, w.res_phi,
+                                                       t->prm.G, acc, phi);
+    k_rows_out_jerk<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, n, t->rank, w.pre, res_J, t->prm.G,
+                                                            jerk);
+    t->n_launch += 3;
     ph_end(t, PH_FWD, s);
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
