@@ -106,6 +106,12 @@ def _load():
                                          ctypes.c_int64, _i64p, _f64p]
         lib.sfgo_jerk_group.restype = ctypes.c_int
         lib.sfgo_jerk_group.argtypes = [_vp, _f64p, ctypes.c_double, _i64p, ctypes.c_int64, _f64p]
+        lib.sfgo_direct_tstep.restype = None
+        lib.sfgo_direct_tstep.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int64, _i64p, _f64p]
+        lib.sfgo_tstep_group.restype = ctypes.c_int
+        lib.sfgo_tstep_group.argtypes = [_vp, _f64p, ctypes.c_double, ctypes.c_double, _i64p, ctypes.c_int64,
+                                         _f64p]
         lib.sfgo_set_relative.restype = None
         lib.sfgo_set_relative.argtypes = [_vp, _f64p, ctypes.c_double, ctypes.c_double]
         lib.sfgo_num_threads.restype = ctypes.c_int
@@ -193,6 +199,17 @@ def direct_jerk(pos, vel, mass, soft, is_sink=None, targets=None, G: float = 1.0
     _load().sfgo_direct_jerk(n, _p(pos, _f64p), _p(vel, _f64p), _p(mass, _f64p), _p(soft, _f64p), _p(sink, _u8p),
                              float(G), tg.size, _p(tg, _i64p), _p(J, _f64p))
     return J
+
+
+def direct_tstep(pos, vel, mass, soft, eta: float, targets=None, G: float = 1.0):
+    """Sink two-body timestep of Sec. 2.3 over all other particles (direct)."""
+    pos, vel, mass, soft = _f64(pos), _f64(vel), _f64(mass), _f64(soft)
+    n = pos.shape[0]
+    tg = _i64(np.arange(n) if targets is None else targets)
+    dt = np.zeros(tg.size)
+    _load().sfgo_direct_tstep(n, _p(pos, _f64p), _p(vel, _f64p), _p(mass, _f64p), _p(soft, _f64p), float(G),
+                              float(eta), tg.size, _p(tg, _i64p), _p(dt, _f64p))
+    return dt
 
 
 def tidal_dt(tidal, eta: float):
@@ -310,6 +327,16 @@ class Tree:
         if rc != 0:
             raise ValueError("a requested row is not a walked target")
         return J
+
+    def tstep_group(self, vel, eta: float, idx, G: float = 1.0):
+        """Sink two-body timestep over the last walk's lists (nodes combined)."""
+        vel, idx = _f64(vel), _i64(idx)
+        dt = np.zeros(idx.size)
+        rc = self._lib.sfgo_tstep_group(self._h, _p(vel, _f64p), float(G), float(eta), _p(idx, _i64p), idx.size,
+                                        _p(dt, _f64p))
+        if rc != 0:
+            raise ValueError("a requested row is not a walked target")
+        return dt
 
     def tidal_group(self, idx, G: float = 1.0, quadrupole: bool = True):
         """Group-form tidal tensor [n][6] (xx yy zz xy xz yz) on the last walk's lists."""

@@ -1092,6 +1092,115 @@ int sfgo_jerk_group(const sfgo_tree *t, const double *vel, double G, const int64
     return bad ? -1 : 0;
 }
 
+/* Sink two-body timestep (Sec. 2.3, Delta t_2-body): per target,
+ *   dt = sqrt(eta) / (1 / t_c,min + 1 / t_dyn,min),
+ *   t_c = sqrt(r^2 + eps^2) / |v_s' - v_s|,  t_dyn = sqrt((r^2 + eps^2)^{3/2} / (G (m_s + m_s'))),
+ * eps the Plummer-equivalent softening h / 2.8.  Over the group's lists (the
+ * minima "in the pass through the gravity tree", masses combined within an
+ * accepted node): a pair uses eps = max(h_s, h_s') / 2.8, a node its total
+ * mass, centre of mass, mass-weighted velocity and eps = h_s / 2.8.  A zero
+ * relative velocity gives no crossing-time limit. */
+static void tstep_term(double r2, double eps, double dv2, double msum, double G, double *tc, double *td)
+{
+    double s2 = r2 + eps * eps;
+    if (dv2 > 0.0) {
+        double t = sqrt(s2 / dv2);
+        if (t < *tc) *tc = t;
+    }
+    double t = sqrt(s2 * sqrt(s2) / (G * msum));
+    if (t < *td) *td = t;
+}
+
+static double tstep_dt(double tc, double td, double eta)
+{
+    return sqrt(eta) / (1.0 / tc + 1.0 / td);
+}
+
+/* Direct form over all other particles (input order), vel [n][3]. */
+void sfgo_direct_tstep(int64_t n, const double *pos, const double *vel, const double *mass, const double *soft,
+                       double G, double eta, int64_t nt, const int64_t *targets, double *dt)
+{
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets[t];
+        double tc = HUGE_VAL, td = HUGE_VAL;
+        for (int64_t k = 0; k < n; k++) {
+            if (k == i) continue;
+            double r2 = 0.0, dv2 = 0.0;
+            for (int a = 0; a < 3; a++) {
+                double d = pos[3 * k + a] - pos[3 * i + a], w = vel[3 * k + a] - vel[3 * i + a];
+                r2 += d * d;
+                dv2 += w * w;
+            }
+            double h = soft[i] > soft[k] ? soft[i] : soft[k];
+            tstep_term(r2, h / 2.8, dv2, mass[i] + mass[k], G, &tc, &td);
+        }
+        dt[t] = tstep_dt(tc, td, eta);
+    }
+}
+
+int sfgo_tstep_group(const sfgo_tree *t, const double *vel, double G, double eta, const int64_t *idx, int64_t n_idx,
+                     double *dt)
+{
+    int64_t n = t->n, nn = t->nn;
+    double *vs = (double *)malloc(24 * n), *pn = (double *)malloc(24 * nn), *vn = (double *)malloc(24 * nn);
+    for (int64_t r = 0; r < n; r++)
+        for (int a = 0; a < 3; a++) vs[3 * r + a] = vel[3 * t->order[r] + a];
+    for (int64_t i = nn - 1; i >= 0; i--) {
+        const onode *nd = &t->nodes[i];
+        double p[3] = {0, 0, 0};
+        if (nd->nchild == 0) {
+            for (int64_t k = nd->first; k < nd->first + nd->count; k++)
+                for (int a = 0; a < 3; a++) p[a] = p[a] + t->mass[k] * vs[3 * k + a];
+        } else {
+            for (int q = 0; q < nd->nchild; q++)
+                for (int a = 0; a < 3; a++) p[a] = p[a] + pn[3 * (nd->child_first + q) + a];
+        }
+        for (int a = 0; a < 3; a++) {
+            pn[3 * i + a] = p[a];
+            vn[3 * i + a] = nd->M > 0.0 ? p[a] / nd->M : 0.0;
+        }
+    }
+    int bad = 0;
+    for (int64_t k = 0; k < n_idx; k++) {
+        int64_t r = t->rank[idx[k]];
+        if (t->tgroup[r] < 0 || !t->groups[t->tgroup[r]].walked) {
+            bad = 1;
+            continue;
+        }
+        const ogroup *g = &t->groups[t->tgroup[r]];
+        const double *x = t->pos + 3 * r, *v = vs + 3 * r;
+        double tc = HUGE_VAL, td = HUGE_VAL;
+        for (int64_t q = 0; q < g->n_p2m; q++) {
+            int64_t ni = g->p2m[q];
+            const onode *nd = &t->nodes[ni];
+            double r2 = 0.0, dv2 = 0.0;
+            for (int a = 0; a < 3; a++) {
+                double d = nd->com[a] - x[a], w = vn[3 * ni + a] - v[a];
+                r2 += d * d;
+                dv2 += w * w;
+            }
+            tstep_term(r2, t->soft[r] / 2.8, dv2, t->mass[r] + nd->M, G, &tc, &td);
+        }
+        for (int64_t q = 0; q < g->n_p2p; q++) {
+            const onode *nd = &t->nodes[g->p2p[q]];
+            for (int64_t j = nd->first; j < nd->first + nd->count; j++) {
+                if (j == r) continue;
+                double r2 = 0.0, dv2 = 0.0;
+                for (int a = 0; a < 3; a++) {
+                    double d = t->pos[3 * j + a] - x[a], w = vs[3 * j + a] - v[a];
+                    r2 += d * d;
+                    dv2 += w * w;
+                }
+                double h = t->soft[r] > t->soft[j] ? t->soft[r] : t->soft[j];
+                tstep_term(r2, h / 2.8, dv2, t->mass[r] + t->mass[j], G, &tc, &td);
+            }
+        }
+        dt[k] = tstep_dt(tc, td, eta);
+    }
+    free(vs); free(pn); free(vn);
+    return bad ? -1 : 0;
+}
+
 /* Frozen-list re-evaluation with new positions/masses (original order):
  * the topology and the lists of the last walk are kept; the moments are
  * recomputed by the same hierarchical combination. */
