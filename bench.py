@@ -39,20 +39,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # FP32 operations per interaction, counted from the evaluation source
-# (walk.cu: fwd_p2p Newtonian branch, fwd_p2m with quadrupole / monopole);
-# FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The softened branch's extra work is not
-# counted.
-FLOP_P2P = 21
+# (walk.cu: fwd_newt_step for every P2P pair, fwd_p2m_step with quadrupole /
+# monopole); FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The deferred evaluation of
+# the pairs inside a softening support is extra work and not counted.
+FLOP_P2P = 19
 FLOP_P2M_QUAD = 55
-FLOP_P2M_MONO = 20
-# Adjoint (walk.cu: vjp_p2p Newtonian branch, vjp_p2m with quadrupole), same
-# counting rule; the source-side rotation shuffles are not counted.
-FLOP_VJP_P2P = 43
-FLOP_VJP_P2M_QUAD = 174
-# DRAM bytes per launch of the walk kernels on the default workload
-# (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture; see
-# profiles/), valid only for the walk source they were taken on.
-WALK_TRAFFIC = {"sha256": None, "fwd": None, "vjp": None}
+FLOP_P2M_MONO = 19
+# Adjoint (walk.cu: vjp_p2p_newt for every P2P pair, vjp_p2m_tile with
+# quadrupole), same counting rule; the source-side rotation shuffles and the
+# deferred softened pairs are not counted.
+FLOP_VJP_P2P = 42
+FLOP_VJP_P2M_QUAD = 139
+# DRAM bytes per launch of the evaluation kernels on the default workload
+# (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture), valid only
+# for the walk source (sha256 of walk.cu) and launch shape they were taken on.
+WALK_TRAFFIC = {"sha256": None, "leaf_size": None, "group_size": None, "fwd": None, "vjp": None}
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576
@@ -448,7 +449,16 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
     d_cp = torch.from_numpy(cp).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    kw = dict(theta=wl["theta"], leaf_size=args.leaf_size, group_size=args.group_size, quadrupole=True,
+    tuned = None
+    leaf, group = args.leaf_size, args.group_size
+    if leaf is None or group is None:
+        # launch shape from the autotuner (untimed; cached per GPU and workload class)
+        from paper_2010_11254_gb300 import autotune
+        tuned = autotune.tune(d_pos, d_mass, d_soft, d_sink, active=d_act, cot_a=d_ca, cot_phi=d_cp,
+                              theta=wl["theta"])
+        leaf = tuned["leaf_size"] if leaf is None else leaf
+        group = tuned["group_size"] if group is None else group
+    kw = dict(theta=wl["theta"], leaf_size=leaf, group_size=group, quadrupole=True,
               precision=args.precision, store_lists=bool(args.store_lists))
     lists = bool(args.store_lists) and args.precision == 0
     kname = "k_eval" if lists else "k_walk"
@@ -539,7 +549,9 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         a = flops / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": kernel, "achieved": round(a, 3), "peak": round(fp32_peak, 2),
                 "unit": "TFLOP/s", "frac": round(a / fp32_peak, 4),
-                "traffic": WALK_TRAFFIC[traffic_key] if (same_src and args.workload == "clumpy-2M") else None,
+                "traffic": WALK_TRAFFIC[traffic_key] if (same_src and args.workload == "clumpy-2M"
+                                                          and (leaf, group) == (WALK_TRAFFIC["leaf_size"],
+                                                                                WALK_TRAFFIC["group_size"])) else None,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
                 "flops_per_launch": int(flops), "launch_ms": round(ms, 4), "flop_model": model}
 
@@ -559,8 +571,10 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         "dtype": "f32+f64" if args.precision == 0 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
                    "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"],
-                   "leaf_size": args.leaf_size, "group_size": args.group_size, "quadrupole": True,
+                   "leaf_size": leaf, "group_size": group, "quadrupole": True,
                    "precision": args.precision, "store_lists": bool(args.store_lists),
+                   "autotune": None if tuned is None else {"key": tuned["key"], "cached": tuned["cached"],
+                                                            "trials": tuned.get("trials")},
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"independent clouds x{world}"},
         "roofline": dominant,
@@ -601,8 +615,8 @@ def main():
                     help="active rows checked against the FP64 direct sum")
     ap.add_argument("--store-lists", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--leaf-size", type=int, default=16)
-    ap.add_argument("--group-size", type=int, default=32)
+    ap.add_argument("--leaf-size", type=int, default=None, help="default: the autotuner's choice")
+    ap.add_argument("--group-size", type=int, default=None, help="default: the autotuner's choice")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     args = ap.parse_args()

@@ -201,6 +201,21 @@ int sfg_set_relative_criterion(sfg_tree *tree, const double *g_prev, double alph
 int sfg_accel_jerk(sfg_tree *tree, const double *vel, const int64_t *active_idx, int64_t n_active, double *accel,
                    double *phi, double *jerk, void *stream);
 
+/* Sink two-body timestep of Sec. 2.3 with its minima taken in the tree pass,
+ * masses within an accepted node combined (the paper's sink criterion,
+ * evaluated on a tree of the sinks alone):
+ *   dt[k] = sqrt(eta) / (1 / t_c,min + 1 / t_dyn,min),
+ *   t_c = sqrt(r^2 + eps^2) / |v_s' - v_s|,  t_dyn = sqrt((r^2 + eps^2)^{3/2} / (G (m_s + m_s'))),
+ * minimised over the particles of opened leaves (eps = max(h_s, h_s') / 2.8,
+ * the Plummer-equivalent softening) and the accepted nodes (total mass at the
+ * centre of mass, mass-weighted velocity, eps = h_s / 2.8).  FP32 terms, FP64
+ * output; +infinity when no other particle limits the step.
+ *   vel [n][3] float64, device (input order); dt [n_active] float64, device;
+ *   eta > 0 the tolerance parameter.
+ * Stored lists, precision and capture rules and errors as for sfg_accel_tidal. */
+int sfg_sink_timestep(sfg_tree *tree, const double *vel, const int64_t *active_idx, int64_t n_active, double eta,
+                      double *dt, void *stream);
+
 /* Tidal timestep constraint of Sec. 2.3:
  *   dt[k] = sqrt(eta) * (|T_k|^2 / 6)^(-1/4),
  * |T| the Frobenius norm of the symmetric tensor given by its six components

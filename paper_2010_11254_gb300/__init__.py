@@ -96,6 +96,8 @@ def _load():
         lib.sfg_tidal_timestep.restype = i32
         lib.sfg_accel_jerk.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
         lib.sfg_accel_jerk.restype = i32
+        lib.sfg_sink_timestep.argtypes = [vp, vp, vp, i64, ctypes.c_double, vp, vp]
+        lib.sfg_sink_timestep.restype = i32
         lib.sfg_set_relative_criterion.argtypes = [vp, vp, ctypes.c_double, vp]
         lib.sfg_set_relative_criterion.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -228,6 +230,17 @@ class Tree:
                                         acc.data_ptr(), phi.data_ptr(), jerk.data_ptr(), _stream(self.device))
         _check(rc, "sfg_accel_jerk")
         return acc, phi, jerk
+
+    def sink_timestep(self, vel, eta: float, active=None):
+        """Two-body timestep [n] of the active rows (Sec. 2.3), minima over the tree lists."""
+        a, na = self._active(active)
+        vel = _dev(vel, torch.float64, "vel")
+        dt = torch.empty(na, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            rc = _load().sfg_sink_timestep(self._h, vel.data_ptr(), None if a is None else a.data_ptr(), na,
+                                           float(eta), dt.data_ptr(), _stream(self.device))
+        _check(rc, "sfg_sink_timestep")
+        return dt
 
     def accel_tidal(self, active=None):
         """(accel [n][3], phi [n], tidal [n][6] = xx yy zz xy xz yz) at the active rows."""

@@ -199,6 +199,16 @@ int sfg_accel_jerk(sfg_tree *tree, const double *vel, const int64_t *active_idx,
     return sfg::accel_jerk(&tree->t, vel, active_idx, n_active, accel, phi, jerk, (cudaStream_t)stream);
 }
 
+int sfg_sink_timestep(sfg_tree *tree, const double *vel, const int64_t *active_idx, int64_t n_active, double eta,
+                      double *dt, void *stream)
+{
+    if (!tree || !vel || n_active < 0 || (n_active > 0 && !dt) || !(eta > 0.0) || !std::isfinite(eta))
+        return SFG_EINVAL;
+    tree->t.stream = (cudaStream_t)stream;
+    cudaGetLastError();
+    return sfg::sink_timestep(&tree->t, vel, active_idx, n_active, eta, dt, (cudaStream_t)stream);
+}
+
 int sfg_set_relative_criterion(sfg_tree *tree, const double *g_prev, double alpha, void *stream)
 {
     if (!tree || (g_prev && (!(alpha >= 0.0) || !std::isfinite(alpha)))) return SFG_EINVAL;

@@ -440,8 +440,10 @@ __global__ void k_oct_root(const int64_t *off, int C, int32_t *nfirst, int32_t *
     }
 }
 
+// Child counts of the level's nodes (tmp) and their child boundaries s[1..7]
+// (bnd, 7 per node, read back by k_oct_write instead of searching again).
 __global__ void k_oct_count(const uint64_t *key, const uint64_t *ks, const int *lvl, int level, int leaf_size, int cap,
-                            const int32_t *nfirst, const int32_t *ncount, int *tmp, int *status)
+                            const int32_t *nfirst, const int32_t *ncount, int *tmp, int *bnd, int *status)
 {
     int b = lvl[level], e = lvl[level + 1];
     if (e > cap) {
@@ -456,13 +458,14 @@ __global__ void k_oct_count(const uint64_t *key, const uint64_t *ks, const int *
             digit_bounds(key, ks, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
 #pragma unroll
             for (int d = 0; d < 8; d++) nch += sb[d + 1] > sb[d];
+#pragma unroll
+            for (int d = 1; d < 8; d++) bnd[7 * (size_t)(node - b) + d - 1] = sb[d];
         }
         tmp[node - b] = nch;
     }
 }
 
-__global__ void k_oct_write(const uint64_t *key, const uint64_t *ks, const int *lvl, int level, int leaf_size, int cap,
-                            int32_t *nfirst,
+__global__ void k_oct_write(const int *bnd, const int *lvl, int level, int leaf_size, int cap, int32_t *nfirst,
                             int32_t *ncount, int32_t *nparent, int32_t *nchild_first, int32_t *nnchild,
                             int32_t *nlevel, int32_t *ncloud, const int *tmp_off, int *status)
 {
@@ -477,7 +480,10 @@ __global__ void k_oct_write(const uint64_t *key, const uint64_t *ks, const int *
         }
         int cf = next + tmp_off[node - b];
         int sb[9];
-        digit_bounds(key, ks, f, f + c, 3 * (SFG_LMAX - level - 1), sb);
+        sb[0] = f;
+#pragma unroll
+        for (int d = 1; d < 8; d++) sb[d] = bnd[7 * (size_t)(node - b) + d - 1];
+        sb[8] = f + c;
         int k = 0;
         const int cl = ncloud[node];
         for (int d = 0; d < 8; d++) {
@@ -837,7 +843,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     // measured on uniform and clumpy clouds: nodes / n <= 1.5, 0.77, 0.52,
     // 0.32, 0.16 for leaf sizes 1, 4, 8, 16, 32
     int64_t cap64 = 6 * ((int64_t)n / (t->prm.leaf_size + 2)) + 4096 + 64 * (int64_t)C;
-    int *tmp = nullptr, *tmpo = nullptr;
+    int *tmp = nullptr, *tmpo = nullptr, *bnd = nullptr;
     uint64_t *ks = nullptr;
     ALLOC(ks, uint64_t, (n + KS - 1) / KS);
     k_key_samples<<<grid_for((n + KS - 1) / KS, BT), BT, 0, s>>>(t->key, n, ks);
@@ -849,6 +855,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         if (rc) return rc;
         ALLOC(tmp, int, cap + 1);
         ALLOC(tmpo, int, cap + 1);
+        ALLOC(bnd, int, 7 * (size_t)cap);
         k_oct_root<<<(C + 127) / 128, 128, 0, s>>>(t->d_off, C, t->nfirst, t->ncount, t->nparent, t->nlevel,
                                                    t->ncloud, t->d_lvl);
         t->n_launch += 1 + (SFG_LMAX + 1) * 5;
@@ -856,10 +863,10 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         const int og = std::min(grid_for(cap, BT), num_sms() * 4);
         for (int level = 0; level <= SFG_LMAX; level++) {
             k_oct_count<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
-                                                         t->ncount, tmp, t->d_status);
+                                          t->ncount, tmp, bnd, t->d_status);
             scan_range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
                        t->d_lvl + level + 1, scr, s);
-            k_oct_write<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+            k_oct_write<<<og, BT, 0, s>>>(bnd, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, t->nparent, t->nchild_first, t->nnchild,
                                                          t->nlevel, t->ncloud, tmpo, t->d_status);
         }
@@ -870,6 +877,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         SFG_CUDA_OK(cudaGetLastError());
         dev_free(t, tmp, s);
         dev_free(t, tmpo, s);
+        dev_free(t, bnd, s);
         if (st & ST_EINVAL) return SFG_EINVAL;
         if (!(st & ST_NODECAP)) break;
         free_nodes(t, s);

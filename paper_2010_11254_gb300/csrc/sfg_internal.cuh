@@ -141,6 +141,8 @@ int tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, cudaS
 int set_relative(Tree *t, const double *g_prev, double alpha, cudaStream_t s);
 int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double *accel, double *phi,
                double *jerk, cudaStream_t s);
+int sink_timestep(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double eta, double *dt,
+                  cudaStream_t s);
 int debug_lists(Tree *t, const int64_t *active, int64_t n_active, int64_t *n_groups, int64_t *n_p2m_total,
                 int64_t *n_p2p_total, int64_t *groups, int32_t *p2m, int32_t *p2p, cudaStream_t s);
 

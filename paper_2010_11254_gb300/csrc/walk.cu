@@ -39,7 +39,8 @@ constexpr int STK = 224;       // shared-memory stack capacity (ranges) per warp
 constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry launch
 constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4, MODE_LIST = 5,
               MODE_TIDAL = 6, // forward evaluation plus the tidal tensor (stored lists only)
-              MODE_JERK = 7;  // forward evaluation plus the jerk (stored lists only)
+              MODE_JERK = 7,  // forward evaluation plus the jerk (stored lists only)
+              MODE_TSTEP = 8; // sink two-body timestep minima only (stored lists only)
 // list sizes per group written by the counting walk: P2M nodes, softened P2P
 // ranges and particles, Newtonian P2P ranges and particles
 constexpr int NCNT = 5;
@@ -84,6 +85,7 @@ struct WalkParams {
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
     float *res_J;        // jerk mode: [U][4] = j (x y z), -; summed
+    unsigned *res_TS;    // timestep mode: [U][2] = min t_c^2, min (r^2 + eps^2)^{3/2} / (m_s + m_s') (float bits)
     const float4 *pv;    // jerk mode: particle velocities, sorted (FP32)
     const float4 *nV;    // jerk mode: node mass-weighted velocities (FP32 of the FP64 sums)
     // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
@@ -131,7 +133,8 @@ struct Tgt {
     int tp, R, tl, slice;
     float s22;                  // half-cell size of the group's cloud (FP32)
     double x64[3], h64, hinv64; // all-FP64 evaluation only
-    float vx, vy, vz; // jerk mode: the target's velocity
+    float vx, vy, vz; // jerk / timestep mode: the target's velocity
+    float mt;         // timestep mode: the target's mass
     // relative criterion: alpha * min |g_prev| over the group, the cloud's root side, cell^2
     bool rel;
     double rel_ag, rel_L0, rel_cell2;
@@ -1721,6 +1724,32 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
 }
 
 
+// Timestep mode (Sec. 2.3, Delta t_2-body with the minima taken over the
+// lists): per target, the smallest t_c^2 = (r^2 + eps^2) / |v_s' - v_s|^2 and
+// q = (r^2 + eps^2)^{3/2} / (m_s + m_s') over the tile's sources (t_dyn^2 =
+// q / G); eps = max(h_s, h_s') / 2.8 for a particle, h_s / 2.8 for a node
+// (its mass combined at its centre of mass, with its mass-weighted velocity).
+template <bool NODE, class SM>
+__device__ __forceinline__ void ts_tile(const SM &S, int cnt, const Tgt &T, float mt, float &tc2, float &q)
+{
+    const float eps_n = T.h * (1.f / 2.8f);
+    for (int k = T.slice; k < cnt; k += T.R) {
+        const float4 p = S.tP[k], v = S.tV[k];
+        float e = eps_n;
+        if (!NODE) {
+            const float4 hh = S.tA[k];
+            if (__float_as_int(hh.z) == T.r) continue; // the target itself
+            e = fmaxf(T.h, hh.x) * (1.f / 2.8f);
+        }
+        const float dx = p.x - T.ox, dy = p.y - T.oy, dz = p.z - T.oz;
+        const float wx = v.x - T.vx, wy = v.y - T.vy, wz = v.z - T.vz;
+        const float s2 = fmaf(e, e, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float dv2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+        tc2 = fminf(tc2, __fdividef(s2, dv2));
+        q = fminf(q, __fdividef(s2 * sqrtf(s2), mt + p.w));
+    }
+}
+
 // Jerk mode: the velocity of this lane's staged source particle j (or node).
 __device__ __forceinline__ void stage_vel(const WalkParams &P, EvalSmem &S, int cnt, int j, int lane)
 {
@@ -1773,7 +1802,11 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
             __syncwarp();
         }
         constexpr bool EXTRA = MODE == MODE_TIDAL || MODE == MODE_JERK;
-        if (NEWT) {
+        if (MODE == MODE_TSTEP) {
+            stage_p2p(P, S, c, qh, qoff, T, lane);
+            stage_vel(P, S, c, __float_as_int(S.tA[lane & 31].z), lane);
+            if (T.has) ts_tile<false>(S, c, T, T.mt, A.t[0], A.t[1]);
+        } else if (NEWT) {
             stage_p2p_newt(P, S, c, qh, qoff, T, lane);
             if (MODE == MODE_JERK) stage_vel(P, S, c, S.tN[lane & 31], lane);
             if (MODE == MODE_VJP) vjp_p2p_newt(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
@@ -1821,12 +1854,17 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         for (int c = 0; c < 8; c++) S.sTid[lane][c] = 0.f;
     }
     T.vx = T.vy = T.vz = 0.f;
-    if (MODE == MODE_JERK) {
+    T.mt = 0.f;
+    if (MODE == MODE_JERK || MODE == MODE_TSTEP) {
         const float4 v = T.has ? P.pv[T.r] : make_float4(0.f, 0.f, 0.f, 0.f);
         T.vx = v.x;
         T.vy = v.y;
         T.vz = v.z;
         if (T.slice == 0) S.gV[T.tl] = v;
+        if (MODE == MODE_TSTEP) {
+            T.mt = T.has ? P.pw[T.r].w : 0.f;
+            A.t[0] = A.t[1] = __int_as_float(0x7f800000);
+        }
     }
     __syncwarp();
     const int *cn = P.lcnt + NCNT * (size_t)g;
@@ -1838,14 +1876,16 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         for (int tt = t0; tt < t1; tt++) {
             const int b = tt * 32, c = min(32, nm - b);
             stage_p2m<QUAD, MODE == MODE_VJP>(P, S, lm + b, c, T, lane);
-            if (MODE == MODE_JERK) {
+            if (MODE == MODE_JERK || MODE == MODE_TSTEP) {
                 if (lane < c) {
                     const int id = lm[b + lane];
                     S.tV[lane] = (unsigned)id < (unsigned)P.nn ? P.nV[id] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 __syncwarp();
             }
-            if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
+            if (MODE == MODE_TSTEP) {
+                if (T.has) ts_tile<true>(S, c, T, T.mt, A.t[0], A.t[1]);
+            } else if (MODE == MODE_VJP) vjp_p2m<QUAD>(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
             else if (EXTRA) {
                 if (T.has) tid_p2m<MODE, QUAD>(S, c, T, ax, ay, az, phi, A);
             } else if (T.has) fwd_p2m<QUAD>(S, c, T, ax, ay, az, phi);
@@ -1867,6 +1907,17 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         }
     }
     __syncwarp();
+    if (MODE == MODE_TSTEP) {
+        for (int o = T.tp; o < 32; o <<= 1) {
+            A.t[0] = fminf(A.t[0], __shfl_xor_sync(FULL, A.t[0], o));
+            A.t[1] = fminf(A.t[1], __shfl_xor_sync(FULL, A.t[1], o));
+        }
+        if (T.has && T.slice == 0) { // non-negative floats order like their bits
+            unsigned *dst = P.res_TS + 2 * (size_t)(tfirst + T.tl);
+            atomicMin(dst, __float_as_uint(A.t[0]));
+            atomicMin(dst + 1, __float_as_uint(A.t[1]));
+        }
+    }
     if (MODE == MODE_JERK) {
         for (int o = T.tp; o < 32; o <<= 1) {
 #pragma unroll
@@ -1900,7 +1951,10 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
 // resident blocks per SM of the evaluation kernel (the tidal mode carries
 // seven more accumulators per lane)
 constexpr int TIDAL_MINB = 4;
-constexpr int eval_minb(int mode) { return mode == MODE_TIDAL || mode == MODE_JERK ? TIDAL_MINB : EVAL_MINB; }
+constexpr int eval_minb(int mode)
+{
+    return mode == MODE_TIDAL || mode == MODE_JERK || mode == MODE_TSTEP ? TIDAL_MINB : EVAL_MINB;
+}
 
 template <bool QUAD, int MODE>
 __global__ void __launch_bounds__(EVAL_WARPS * 32, eval_minb(MODE)) k_eval(WalkParams P)
@@ -2304,6 +2358,7 @@ struct Work {
     double *res64; // all-FP64 evaluation: [U][4] (a, phi), accumulated
     float *res_T;  // tidal mode: [U][8] = T without its isotropic part (xx yy zz xy xz yz), that part, -; summed
     float *res_J;        // jerk mode: [U][4] = j (x y z), -; summed
+    unsigned *res_TS;    // timestep mode: [U][2] = min t_c^2, min (r^2 + eps^2)^{3/2} / (m_s + m_s') (float bits)
     const float4 *pv;    // jerk mode: particle velocities, sorted (FP32)
     const float4 *nV;    // jerk mode: node mass-weighted velocities (FP32 of the FP64 sums)
     // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
@@ -2797,6 +2852,12 @@ int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *acc, d
     return SFG_OK;
 }
 
+__global__ void k_fill_u32(unsigned *p, int64_t n, unsigned v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 // ---- jerk mode: velocities of particles (sorted, FP32) and nodes ----
 __global__ void k_vel_sorted(const double *vel, const int32_t *order, int n, float4 *pv)
 {
@@ -2857,16 +2918,13 @@ __global__ void k_rows_out_jerk(const int64_t *idx, int64_t n_active, int n, con
     }
 }
 
-// Field, potential and jerk (stored lists, like accel_tidal).
-int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double *acc, double *phi,
-               double *jerk, cudaStream_t s)
+// Stored lists for the active set (walked here unless kept), work items, and
+// the velocities of particles (sorted, FP32) and nodes (FP64 momentum sums).
+// Returns the per-target result slots (16 B each) of the jerk / timestep mode.
+static int prepare_vel(Tree *t, const double *vel, const int64_t *active, int64_t n_active, Work &w, WalkParams &P,
+                       cudaStream_t s, float **res)
 {
-    if (n_active == 0) return SFG_OK;
-    if (t->prm.precision != 0 || capturing(s)) return SFG_EINVAL;
     const int n = (int)t->n, nn = t->nn, BT = 256;
-    Work w;
-    WalkParams P;
-    ph_begin(t, PH_FWD, s);
     int rc = prepare(t, active, n_active, w, P, s);
     if (rc) return rc;
     bool match = false;
@@ -2879,7 +2937,7 @@ int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_acti
         if (rc) return rc;
     }
     items_from_counts(t, w, P, s, WT_EVAL);
-    // workspace: res_J [n][4] f32, pv [n] float4, node momenta [nn][3] f64, nV [nn] float4
+    // workspace: results [n][4] f32, pv [n] float4, node momenta [nn][3] f64, nV [nn] float4
     const size_t need = align_up(16 * (size_t)n) + align_up(16 * (size_t)n) + align_up(24 * (size_t)nn) +
                         align_up(16 * (size_t)nn);
     if (t->ws4_bytes < need) {
@@ -2892,27 +2950,45 @@ int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_acti
         t->ws4_bytes = need;
     }
     char *p = (char *)t->ws4;
-    float *res_J = (float *)p;
+    *res = (float *)p;
     p += align_up(16 * (size_t)n);
     float4 *pv = (float4 *)p;
     p += align_up(16 * (size_t)n);
     double *np = (double *)p;
     p += align_up(24 * (size_t)nn);
     float4 *nV = (float4 *)p;
-    SFG_CUDA_OK(cudaMemsetAsync(res_J, 0, 16 * (size_t)n, s));
     k_vel_sorted<<<grid_for(n, BT), BT, 0, s>>>(vel, t->order, n, pv);
     k_mom_leaf<<<grid_for(nn, 128), 128, 0, s>>>(vel, t->order, t->mass_s, t->nfirst, t->ncount, t->nnchild, nn,
                                                  np);
-    t->n_launch += 3;
+    t->n_launch += 2;
     for (int l = t->depth - 1; l >= 0; l--) {
         const int b = t->lvl_off[l], e = t->lvl_off[l + 1];
         k_mom_internal<<<grid_for(e - b, 128), 128, 0, s>>>(t->nchild_first, t->nnchild, b, e, np);
         t->n_launch += 1;
     }
     k_node_vel<<<grid_for(nn, BT), BT, 0, s>>>(np, t->nM, nn, nV);
-    P.res_J = res_J;
+    t->n_launch += 1;
     P.pv = pv;
     P.nV = nV;
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+// Field, potential and jerk (stored lists, like accel_tidal).
+int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double *acc, double *phi,
+               double *jerk, cudaStream_t s)
+{
+    if (n_active == 0) return SFG_OK;
+    if (t->prm.precision != 0 || capturing(s)) return SFG_EINVAL;
+    const int n = (int)t->n;
+    Work w;
+    WalkParams P;
+    ph_begin(t, PH_FWD, s);
+    float *res_J = nullptr;
+    int rc = prepare_vel(t, vel, active, n_active, w, P, s, &res_J);
+    if (rc) return rc;
+    SFG_CUDA_OK(cudaMemsetAsync(res_J, 0, 16 * (size_t)n, s));
+    P.res_J = res_J;
     if (t->timing) {
         int rc2 = cloud_timer_begin(t, 0, s, P);
         if (rc2) return rc2;
@@ -2924,7 +3000,49 @@ int accel_jerk(Tree *t, const double *vel, const int64_t *active, int64_t n_acti
                                                        t->prm.G, acc, phi);
     k_rows_out_jerk<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, n, t->rank, w.pre, res_J, t->prm.G,
                                                             jerk);
-    t->n_launch += 3;
+    t->n_launch += 2;
+    ph_end(t, PH_FWD, s);
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
+// dt = sqrt(eta) / (1 / t_c + 1 / t_dyn) from the per-target minima; a
+// minimum left at the +inf sentinel imposes no limit.
+__global__ void k_rows_out_tstep(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, const int *pre,
+                                 const unsigned *res_TS, double G, double eta, double *dt)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx ? idx[k] : k;
+        if (i < 0 || i >= n) continue;
+        const unsigned *r = res_TS + 2 * (size_t)pre[rank[i]];
+        const double tc2 = (double)__uint_as_float(r[0]), q = (double)__uint_as_float(r[1]);
+        const double inv_tc = isinf(tc2) ? 0.0 : rsqrt(tc2);
+        const double inv_td = isinf(q) ? 0.0 : sqrt(G / q);
+        dt[k] = sqrt(eta) / (inv_tc + inv_td);
+    }
+}
+
+int sink_timestep(Tree *t, const double *vel, const int64_t *active, int64_t n_active, double eta, double *dt,
+                  cudaStream_t s)
+{
+    if (n_active == 0) return SFG_OK;
+    if (t->prm.precision != 0 || capturing(s)) return SFG_EINVAL;
+    const int n = (int)t->n;
+    Work w;
+    WalkParams P;
+    ph_begin(t, PH_FWD, s);
+    float *res = nullptr;
+    int rc = prepare_vel(t, vel, active, n_active, w, P, s, &res);
+    if (rc) return rc;
+    P.res_TS = (unsigned *)res;
+    k_fill_u32<<<grid_for(2 * (int64_t)n, 256), 256, 0, s>>>(P.res_TS, 2 * (int64_t)n, 0x7f800000u); // +inf
+    ph_begin(t, PH_FWD_WALK, s);
+    launch_eval<MODE_TSTEP>(t, P, s);
+    ph_end(t, PH_FWD_WALK, s);
+    k_rows_out_tstep<<<grid_for(n_active, 256), 256, 0, s>>>(active, n_active, n, t->rank, w.pre, P.res_TS,
+                                                             t->prm.G, eta, dt);
+    t->n_launch += 2;
     ph_end(t, PH_FWD, s);
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
@@ -3005,26 +3123,38 @@ __global__ void k_gnode_push(double *gnode, const double *ncom, const int32_t *n
 }
 
 // Leaves to their members, then unpermute into the caller's order with G.
-__global__ void k_gleaf(const double *gnode, const double *ncom, const int32_t *nfirst, const int32_t *ncount,
-                        const int32_t *nnchild, int nn, const double *pos_s, const double *mass_s, double *gpart)
+// Leaves to their members.  A member's terms are a polynomial in its offset
+// s = x - c from the leaf's centre of mass, evaluated in FP32 (s from the
+// stored FP32 offsets of member and centre of mass against the leaf centre)
+// and added to the FP64 particle gradients; the node gradients stay FP64
+// and gM enters in FP64.
+__global__ void k_gleaf(const double *gnode, const float4 *E0, const float4 *pw, const int32_t *nfirst,
+                        const int32_t *ncount, const int32_t *nnchild, int nn, double *gpart)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
         if (nnchild[i] != 0) continue;
         const double *g = gnode + 10 * (size_t)i;
-        const double *S = g + 4;
-        double tr = S[0] + S[1] + S[2];
-        double c[3] = {ncom[3 * (size_t)i], ncom[3 * (size_t)i + 1], ncom[3 * (size_t)i + 2]};
+        const double g0 = g[0];
+        const float v0 = (float)g[1], v1 = (float)g[2], v2 = (float)g[3];
+        const float S0 = (float)g[4], S1 = (float)g[5], S2 = (float)g[6], S3 = (float)g[7], S4 = (float)g[8],
+                    S5 = (float)g[9];
+        const float tr = S0 + S1 + S2;
+        const float4 c = E0[i];
         for (int k = nfirst[i]; k < nfirst[i] + ncount[i]; k++) {
-            double s[3];
-            for (int a = 0; a < 3; a++) s[a] = pos_s[3 * (size_t)k + a] - c[a];
-            double Ss[3] = {S[0] * s[0] + S[3] * s[1] + S[4] * s[2], S[3] * s[0] + S[1] * s[1] + S[5] * s[2],
-                            S[4] * s[0] + S[5] * s[1] + S[2] * s[2]};
-            double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
-            double sSs = s[0] * Ss[0] + s[1] * Ss[1] + s[2] * Ss[2];
-            double m = mass_s[k];
+            const float4 x = pw[k];
+            const float s0 = x.x - c.x, s1 = x.y - c.y, s2 = x.z - c.z;
+            const float Ss0 = fmaf(S0, s0, fmaf(S3, s1, S4 * s2));
+            const float Ss1 = fmaf(S3, s0, fmaf(S1, s1, S5 * s2));
+            const float Ss2 = fmaf(S4, s0, fmaf(S5, s1, S2 * s2));
+            const float ss = fmaf(s0, s0, fmaf(s1, s1, s2 * s2));
+            const float sSs = fmaf(s0, Ss0, fmaf(s1, Ss1, s2 * Ss2));
+            const float tm = fmaf(v0, s0, fmaf(v1, s1, fmaf(v2, s2, fmaf(3.f, sSs, -ss * tr))));
+            const float m = x.w;
             double *o = gpart + 4 * (size_t)k;
-            o[3] += g[0] + g[1] * s[0] + g[2] * s[1] + g[3] * s[2] + 3.0 * sSs - ss * tr;
-            for (int a = 0; a < 3; a++) o[a] += m * (g[1 + a] + 6.0 * Ss[a] - 2.0 * tr * s[a]);
+            o[3] += g0 + (double)tm;
+            o[0] += (double)(m * fmaf(6.f, Ss0, fmaf(-2.f * tr, s0, v0)));
+            o[1] += (double)(m * fmaf(6.f, Ss1, fmaf(-2.f * tr, s1, v1)));
+            o[2] += (double)(m * fmaf(6.f, Ss2, fmaf(-2.f * tr, s2, v2)));
         }
     }
 }
@@ -3114,8 +3244,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
                 t->n_launch += 1;
             }
         }
-        k_gleaf<<<grid_for(nn, 128), 128, 0, s>>>(gnode, t->ncom, t->nfirst, t->ncount, t->nnchild, nn, t->pos_s,
-                                                  t->mass_s, gpart);
+        k_gleaf<<<grid_for(nn, 128), 128, 0, s>>>(gnode, t->E0, t->pw, t->nfirst, t->ncount, t->nnchild, nn, gpart);
     }
     k_unpermute<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->order, n, t->prm.G, d_pos, d_mass);
     t->n_launch += 1;
