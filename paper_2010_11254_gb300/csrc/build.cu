@@ -440,18 +440,94 @@ __global__ void k_oct_root(const int64_t *off, int C, int32_t *nfirst, int32_t *
     }
 }
 
+// Child boundaries of a large node [f, e) found by the whole block: every
+// round, PROBE threads per digit read keys spread evenly over that digit's
+// remaining interval, so each interval shrinks about PROBE + 1-fold per
+// dependent load instead of 2-fold.  Invariant: the answer for digit d (first
+// index with child digit >= d + 1) lies in [lo[d], hi[d]], and is hi[d] when
+// no index of [lo[d], hi[d]) qualifies.  Every thread of the block calls it.
+constexpr int BIG_NODE = 4096;
+
+__device__ void block_digit_bounds(const uint64_t *key, int f, int e, int cshift, int *lo, int *hi, int *first)
+{
+    const int PROBE = blockDim.x / 7;
+    const int tid = threadIdx.x, d = tid / PROBE, j = tid - d * PROBE;
+    if (tid < 7) {
+        lo[tid] = f;
+        hi[tid] = e;
+    }
+    __syncthreads();
+    for (int round = 0; round < 32; round++) {
+        bool open = false;
+#pragma unroll
+        for (int q = 0; q < 7; q++) open |= lo[q] < hi[q];
+        if (!open) break; // uniform: every thread reads the same shared values
+        if (tid < 7) first[tid] = PROBE;
+        __syncthreads();
+        int pos = -1;
+        if (d < 7 && lo[d] < hi[d]) {
+            const int len = hi[d] - lo[d];
+            pos = len <= PROBE ? (j < len ? lo[d] + j : -1)
+                               : lo[d] + (int)(((long long)(j + 1) * len) / (PROBE + 1));
+            if (pos >= 0 && ((key[pos] >> cshift) & 7u) >= (uint32_t)(d + 1)) atomicMin(&first[d], j);
+        }
+        __syncthreads();
+        if (tid < 7 && lo[tid] < hi[tid]) {
+            const int len = hi[tid] - lo[tid], k = first[tid];
+            if (len <= PROBE) {
+                const int a = k < len ? lo[tid] + k : hi[tid];
+                lo[tid] = hi[tid] = a;
+            } else {
+                const int qk = lo[tid] + (int)(((long long)(k + 1) * len) / (PROBE + 1));
+                const int qp = lo[tid] + (int)(((long long)k * len) / (PROBE + 1)); // probe k - 1 (k > 0)
+                const int nlo = k == 0 ? lo[tid] : qp + 1;
+                const int nhi = k < PROBE ? qk : hi[tid];
+                lo[tid] = nlo;
+                hi[tid] = nhi;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Child counts of the level's nodes (tmp) and their child boundaries s[1..7]
 // (bnd, 7 per node, read back by k_oct_write instead of searching again).
+// Nodes longer than BIG_NODE are searched by a whole block each, the others
+// by one thread each.
 __global__ void k_oct_count(const uint64_t *key, const uint64_t *ks, const int *lvl, int level, int leaf_size, int cap,
                             const int32_t *nfirst, const int32_t *ncount, int *tmp, int *bnd, int *status)
 {
+    __shared__ int s_lo[7], s_hi[7], s_first[7];
     int b = lvl[level], e = lvl[level + 1];
     if (e > cap) {
         e = cap;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_NODECAP);
     }
+    // block searches only on levels with few nodes (the top of the tree, where
+    // the nodes are long); elsewhere every node goes to the thread path
+    const bool blocks = level < SFG_LMAX && e - b <= 2 * (int)gridDim.x;
+    if (blocks) {
+        for (int node = b + blockIdx.x; node < e; node += gridDim.x) {
+            const int c = ncount[node];
+            if (c <= BIG_NODE || c <= leaf_size) continue;
+            const int f = nfirst[node];
+            block_digit_bounds(key, f, f + c, 3 * (SFG_LMAX - level - 1), s_lo, s_hi, s_first);
+            if (threadIdx.x == 0) {
+                int nch = 0, prev = f;
+                for (int q = 0; q < 7; q++) {
+                    nch += s_lo[q] > prev;
+                    prev = s_lo[q];
+                    bnd[7 * (size_t)(node - b) + q] = s_lo[q];
+                }
+                nch += f + c > prev;
+                tmp[node - b] = nch;
+            }
+            __syncthreads();
+        }
+    }
     for (int node = b + blockIdx.x * blockDim.x + threadIdx.x; node < e; node += gridDim.x * blockDim.x) {
         int f = nfirst[node], c = ncount[node];
+        if (blocks && c > BIG_NODE && c > leaf_size) continue; // done by a block above
         int nch = 0;
         if (c > leaf_size && level < SFG_LMAX) {
             int sb[9];
