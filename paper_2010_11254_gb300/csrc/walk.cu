@@ -1159,11 +1159,20 @@ struct EvalSmem {
     float4 gT[32];  // (ox, oy, oz, h)
     float4 gU[32];  // (1/h, sink flag, target rank bits, h^2)
     float4 sAcc[32]; // per-target sums of the softened pairs: forward (a, phi), adjoint (-dL/dx_i, -)
-    float4 gC[32];   // adjoint: the targets' cotangents (cot_a, cot_phi)
-    float4 sS[32];   // adjoint: per-source sums of the softened pairs of a tile (dL/dx_j, dL/dm_j)
-    float sTid[32][8]; // tidal / jerk mode: per-target sums of the softened pairs (as res_T / res_J)
-    float4 tV[32];     // jerk mode: source velocities of the tile
-    float4 gV[32];     // jerk mode: the group's target velocities
+    union {          // arrays of one mode only
+        struct {
+            float4 gC[32]; // adjoint: the targets' cotangents (cot_a, cot_phi)
+            float4 sS[32]; // adjoint: per-source sums of the softened pairs of a tile (dL/dx_j, dL/dm_j)
+        } a;
+        struct {
+            float sTid[32][8]; // tidal / jerk mode: per-target sums of the softened pairs (as res_T / res_J)
+            float4 tV[32];     // jerk / timestep mode: source velocities of the tile
+            float4 gV[32];     // jerk / timestep mode: the group's target velocities
+        } x;
+    } m;
+    // the next tile's source records in flight (asynchronous copies): P2P
+    // (pw, pc), P2M (E0, E1, E2); each lane copies and later converts its own
+    float4 raw[3][32];
     unsigned short sq[1024]; // softened pairs of a tile: target | source << 5
 };
 
@@ -1388,7 +1397,7 @@ __device__ __forceinline__ void tid_p2m_step(const SM &S, int k, const Tgt &T, f
         az = fmaf(c, dz, fmaf(-ri5, Qd2, az));
         pt = fmaf(-p.w, rinv, fmaf(-0.5f, t, pt));
         if (MODE == MODE_JERK) {
-            const float4 v = S.tV[k];
+            const float4 v = S.m.x.tV[k];
             jerk_add(A, Mri3, ri2, dx, dy, dz, v.x - T.vx, v.y - T.vy, v.z - T.vz);
             return;
         }
@@ -1408,7 +1417,7 @@ __device__ __forceinline__ void tid_p2m_step(const SM &S, int k, const Tgt &T, f
         az = fmaf(Mri3, dz, az);
         pt = fmaf(-p.w, rinv, pt);
         if (MODE == MODE_JERK) {
-            const float4 v = S.tV[k];
+            const float4 v = S.m.x.tV[k];
             jerk_add(A, Mri3, ri2, dx, dy, dz, v.x - T.vx, v.y - T.vy, v.z - T.vz);
             return;
         }
@@ -1449,7 +1458,7 @@ __device__ __forceinline__ void tid_p2p_step(const SM &S, int k, const Tgt &T, f
     az = fmaf(mr3, dz, az);
     pt -= mr;
     if (MODE == MODE_JERK) {
-        const float4 v = S.tV[k];
+        const float4 v = S.m.x.tV[k];
         jerk_add(A, mr3, ri2, dx, dy, dz, v.x - T.vx, v.y - T.vy, v.z - T.vz);
         return;
     }
@@ -1581,22 +1590,22 @@ __device__ __forceinline__ void tid_p2p(EvalSmem &S, int cnt, const Tgt &T, floa
                 atomicAdd(&S.sAcc[t].w, m * 0.5f * (P1 + P2));
                 if (MODE == MODE_JERK) {
                     // j += m [K w + (dK/dr / r) (d . w) d]
-                    const float4 tv = S.gV[t], sv = S.tV[k];
+                    const float4 tv = S.m.x.gV[t], sv = S.m.x.tV[k];
                     const float wx = sv.x - tv.x, wy = sv.y - tv.y, wz = sv.z - tv.z;
                     const float c2 = mR * fmaf(dx, wx, fmaf(dy, wy, dz * wz));
-                    atomicAdd(&S.sTid[t][0], fmaf(mK, wx, c2 * dx));
-                    atomicAdd(&S.sTid[t][1], fmaf(mK, wy, c2 * dy));
-                    atomicAdd(&S.sTid[t][2], fmaf(mK, wz, c2 * dz));
+                    atomicAdd(&S.m.x.sTid[t][0], fmaf(mK, wx, c2 * dx));
+                    atomicAdd(&S.m.x.sTid[t][1], fmaf(mK, wy, c2 * dy));
+                    atomicAdd(&S.m.x.sTid[t][2], fmaf(mK, wz, c2 * dz));
                     continue;
                 }
                 // T += -m [K I + (dK/dr / r) d d^T]
-                atomicAdd(&S.sTid[t][0], -mR * dx * dx);
-                atomicAdd(&S.sTid[t][1], -mR * dy * dy);
-                atomicAdd(&S.sTid[t][2], -mR * dz * dz);
-                atomicAdd(&S.sTid[t][3], -mR * dx * dy);
-                atomicAdd(&S.sTid[t][4], -mR * dx * dz);
-                atomicAdd(&S.sTid[t][5], -mR * dy * dz);
-                atomicAdd(&S.sTid[t][6], mK);
+                atomicAdd(&S.m.x.sTid[t][0], -mR * dx * dx);
+                atomicAdd(&S.m.x.sTid[t][1], -mR * dy * dy);
+                atomicAdd(&S.m.x.sTid[t][2], -mR * dz * dz);
+                atomicAdd(&S.m.x.sTid[t][3], -mR * dx * dy);
+                atomicAdd(&S.m.x.sTid[t][4], -mR * dx * dz);
+                atomicAdd(&S.m.x.sTid[t][5], -mR * dy * dz);
+                atomicAdd(&S.m.x.sTid[t][6], mK);
             }
         }
     }
@@ -1661,7 +1670,7 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
     int at = warp_excl(__popc(mask), lane, total);
     const int ks = base + T.tl; // the source whose sums this lane holds
     if (total > 0) {
-        S.sS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.m.a.sS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         while (mask) {
             const int k = __ffs(mask) - 1;
             mask &= mask - 1;
@@ -1672,7 +1681,7 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
             if (b + lane < total) {
                 const unsigned e = S.sq[b + lane];
                 const int t = e & 31, k = e >> 5;
-                const float4 tg = S.gT[t], tu = S.gU[t], tc = S.gC[t];
+                const float4 tg = S.gT[t], tu = S.gU[t], tc = S.m.a.gC[t];
                 const float4 p = S.tP[k], hh = S.tA[k];
                 if (__float_as_int(hh.z) != __float_as_int(tu.z)) { // not the self pair
                     float dx = p.x - tg.x, dy = p.y - tg.y, dz = p.z - tg.z;
@@ -1695,10 +1704,10 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
                     float l0 = fmaf(mK, tc.x, sv * dx);
                     float l1 = fmaf(mK, tc.y, sv * dy);
                     float l2 = fmaf(mK, tc.z, sv * dz);
-                    atomicAdd(&S.sS[k].x, l0);
-                    atomicAdd(&S.sS[k].y, l1);
-                    atomicAdd(&S.sS[k].z, l2);
-                    atomicAdd(&S.sS[k].w, fmaf(K, cd, Pp * tc.w));
+                    atomicAdd(&S.m.a.sS[k].x, l0);
+                    atomicAdd(&S.m.a.sS[k].y, l1);
+                    atomicAdd(&S.m.a.sS[k].z, l2);
+                    atomicAdd(&S.m.a.sS[k].w, fmaf(K, cd, Pp * tc.w));
                     atomicAdd(&S.sAcc[t].x, -l0);
                     atomicAdd(&S.sAcc[t].y, -l1);
                     atomicAdd(&S.sAcc[t].z, -l2);
@@ -1707,7 +1716,7 @@ __device__ __forceinline__ void vjp_p2p_defer(const WalkParams &P, EvalSmem &S, 
         }
         __syncwarp();
         if (ks < cnt) { // padded lanes carry source sums too
-            const float4 v = S.sS[ks];
+            const float4 v = S.m.a.sS[ks];
             a0 += v.x;
             a1 += v.y;
             a2 += v.z;
@@ -1734,7 +1743,7 @@ __device__ __forceinline__ void ts_tile(const SM &S, int cnt, const Tgt &T, floa
 {
     const float eps_n = T.h * (1.f / 2.8f);
     for (int k = T.slice; k < cnt; k += T.R) {
-        const float4 p = S.tP[k], v = S.tV[k];
+        const float4 p = S.tP[k], v = S.m.x.tV[k];
         float e = eps_n;
         if (!NODE) {
             const float4 hh = S.tA[k];
@@ -1750,10 +1759,107 @@ __device__ __forceinline__ void ts_tile(const SM &S, int cnt, const Tgt &T, floa
     }
 }
 
+// --------------------------------------------- prefetched tile staging ----
+// The evaluation kernel copies the next tile's source records into
+// S.raw with asynchronous 16-byte copies (cp.async) while it evaluates the
+// current tile, then converts them in place of the synchronous staging
+// (same layouts as stage_p2p / stage_p2p_newt / stage_p2m).  Each lane
+// copies, waits for and converts only its own slot.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Particle j (this lane's source of a tile of cnt, -1 if none) in flight.
+__device__ __forceinline__ void fetch_p2p(const WalkParams &P, EvalSmem &S, int j, int cnt, int lane)
+{
+    if (lane < cnt && j >= 0 && j < P.npart) {
+        cp_async16(&S.raw[0][lane], &P.pw[j]);
+        cp_async16(&S.raw[1][lane], &P.pc[j]);
+    }
+    cp_async_commit();
+}
+
+// Convert this lane's fetched particle (softened-range layout, or the
+// Newtonian-range layout when NEWT).
+template <bool NEWT>
+__device__ __forceinline__ void convert_p2p(const WalkParams &P, EvalSmem &S, int j, int cnt, const Tgt &T,
+                                            int lane)
+{
+    if (lane >= cnt) return;
+    if (j >= 0 && j < P.npart) {
+        const float4 a = S.raw[0][lane];
+        const float4 bf = S.raw[1][lane];
+        const int bx = __float_as_int(bf.x), by = __float_as_int(bf.y), bz = __float_as_int(bf.z);
+        const float px = fmaf((float)(bx - T.cg[0]), T.s22, a.x);
+        const float py = fmaf((float)(by - T.cg[1]), T.s22, a.y);
+        const float pz = fmaf((float)(bz - T.cg[2]), T.s22, a.z);
+        S.tP[lane] = make_float4(px, py, pz, a.w);
+        if (NEWT) {
+            S.tN[lane] = j;
+        } else {
+            const float h = bf.w; // negative for a sink
+            const float ha = fabsf(h);
+            S.tA[lane] = make_float4(ha, 1.f / ha, __int_as_float(j), h < 0.f ? 1.f : 0.f);
+            S.tB[lane] = ha * ha;
+        }
+    } else { // the ring ran dry or a corrupt range: massless and far, no gradient
+        atomicOr(P.status, ST_ETIMEOUT);
+        S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f);
+        if (NEWT) {
+            S.tN[lane] = -1;
+        } else {
+            S.tA[lane] = make_float4(1.f, 1.f, __int_as_float(-1), 0.f);
+            S.tB[lane] = 0.f;
+        }
+    }
+}
+
+// Node id (this lane's entry of a P2M tile of cnt) in flight.
+__device__ __forceinline__ void fetch_p2m(const WalkParams &P, EvalSmem &S, int id, int cnt, int lane)
+{
+    if (lane < cnt && (unsigned)id < (unsigned)P.nn) {
+        cp_async16(&S.raw[0][lane], &P.E0[id]);
+        cp_async16(&S.raw[1][lane], &P.E1[id]);
+        cp_async16(&S.raw[2][lane], &P.E2[id]);
+    }
+    cp_async_commit();
+}
+
+template <bool QUAD, bool NODEID>
+__device__ __forceinline__ void convert_p2m(const WalkParams &P, EvalSmem &S, int id, int cnt, const Tgt &T,
+                                            int lane)
+{
+    if (lane >= cnt) return;
+    if ((unsigned)id < (unsigned)P.nn) {
+        const float4 e0 = S.raw[0][lane], e2 = S.raw[2][lane];
+        const float px = fmaf((float)(__float_as_int(e2.y) - T.cg[0]), T.s22, e0.x);
+        const float py = fmaf((float)(__float_as_int(e2.z) - T.cg[1]), T.s22, e0.y);
+        const float pz = fmaf((float)(__float_as_int(e2.w) - T.cg[2]), T.s22, e0.z);
+        S.tP[lane] = make_float4(px, py, pz, e0.w);
+        if (QUAD) {
+            S.tA[lane] = S.raw[1][lane];
+            S.tB[lane] = e2.x;
+        }
+    } else { // not a node (a corrupt list): massless and far, no gradient
+        atomicOr(P.status, ST_ETIMEOUT);
+        id = -1;
+        S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f);
+        if (QUAD) {
+            S.tA[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            S.tB[lane] = 0.f;
+        }
+    }
+    if (NODEID) S.tN[lane] = id;
+}
+
 // Jerk mode: the velocity of this lane's staged source particle j (or node).
 __device__ __forceinline__ void stage_vel(const WalkParams &P, EvalSmem &S, int cnt, int j, int lane)
 {
-    if (lane < cnt) S.tV[lane] = (j >= 0 && j < P.npart) ? P.pv[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < cnt) S.m.x.tV[lane] = (j >= 0 && j < P.npart) ? P.pv[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
 }
 
@@ -1791,9 +1897,8 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
         return;
     }
     int qh = 0, qt = 0, rn = r;
-    for (int b = pb; b < pe; b += 32) {
-        const int c = min(32, pe - b);
-        // keep >= 32 ranges (or all that are left) queued: a tile spans at most 32
+    // keep >= 32 ranges (or all that are left) queued: a tile spans at most 32
+    auto refill = [&]() {
         if (qt - qh < 32 && rn < nr) {
             const int k = min(32, nr - rn);
             if (lane < k) S.leafq[(qt + lane) & 63] = rr[rn + lane];
@@ -1801,20 +1906,36 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
             rn += k;
             __syncwarp();
         }
+    };
+    // the first tile's sources in flight
+    refill();
+    int jn = ring_take(P, S, min(32, pe - pb), qh, qoff, lane);
+    fetch_p2p(P, S, jn, min(32, pe - pb), lane);
+    for (int b = pb; b < pe; b += 32) {
+        const int c = min(32, pe - b);
+        const int j = jn;
+        cp_async_wait();
+        if (NEWT && MODE != MODE_TSTEP) convert_p2p<true>(P, S, j, c, T, lane);
+        else convert_p2p<false>(P, S, j, c, T, lane);
+        __syncwarp();
+        // the next tile's sources in flight while this one is evaluated
+        if (b + 32 < pe) {
+            refill();
+            const int cn = min(32, pe - b - 32);
+            jn = ring_take(P, S, cn, qh, qoff, lane);
+            fetch_p2p(P, S, jn, cn, lane);
+        }
         constexpr bool EXTRA = MODE == MODE_TIDAL || MODE == MODE_JERK;
         if (MODE == MODE_TSTEP) {
-            stage_p2p(P, S, c, qh, qoff, T, lane);
-            stage_vel(P, S, c, __float_as_int(S.tA[lane & 31].z), lane);
+            stage_vel(P, S, c, j, lane);
             if (T.has) ts_tile<false>(S, c, T, T.mt, A.t[0], A.t[1]);
         } else if (NEWT) {
-            stage_p2p_newt(P, S, c, qh, qoff, T, lane);
-            if (MODE == MODE_JERK) stage_vel(P, S, c, S.tN[lane & 31], lane);
+            if (MODE == MODE_JERK) stage_vel(P, S, c, j, lane);
             if (MODE == MODE_VJP) vjp_p2p_newt(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
             else if (EXTRA) tid_p2p<MODE, false>(S, c, T, ax, ay, az, phi, A, lane);
             else if (T.has) fwd_p2p_newt(S, c, T, ax, ay, az, phi);
         } else {
-            stage_p2p(P, S, c, qh, qoff, T, lane);
-            if (MODE == MODE_JERK) stage_vel(P, S, c, __float_as_int(S.tA[lane & 31].z), lane);
+            if (MODE == MODE_JERK) stage_vel(P, S, c, j, lane);
             if (MODE == MODE_VJP) vjp_p2p_defer(P, S, c, T, c0, c1, c2, cf, ax, ay, az, lane);
             else if (EXTRA) tid_p2p<MODE, true>(S, c, T, ax, ay, az, phi, A, lane);
             else fwd_p2p_defer(S, c, T, ax, ay, az, phi, lane);
@@ -1844,14 +1965,14 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     if (T.slice == 0) {
         S.gT[T.tl] = make_float4(T.ox, T.oy, T.oz, T.h);
         S.gU[T.tl] = make_float4(T.hinv, T.sink ? 1.f : 0.f, __int_as_float(T.r), T.h * T.h);
-        if (MODE == MODE_VJP) S.gC[T.tl] = make_float4(c0, c1, c2, cf);
+        if (MODE == MODE_VJP) S.m.a.gC[T.tl] = make_float4(c0, c1, c2, cf);
     }
     S.sAcc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     TidAcc A = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, 0.f};
     constexpr bool EXTRA = MODE == MODE_TIDAL || MODE == MODE_JERK;
     if (EXTRA) {
 #pragma unroll
-        for (int c = 0; c < 8; c++) S.sTid[lane][c] = 0.f;
+        for (int c = 0; c < 8; c++) S.m.x.sTid[lane][c] = 0.f;
     }
     T.vx = T.vy = T.vz = 0.f;
     T.mt = 0.f;
@@ -1860,7 +1981,7 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         T.vx = v.x;
         T.vy = v.y;
         T.vz = v.z;
-        if (T.slice == 0) S.gV[T.tl] = v;
+        if (T.slice == 0) S.m.x.gV[T.tl] = v;
         if (MODE == MODE_TSTEP) {
             T.mt = T.has ? P.pw[T.r].w : 0.f;
             A.t[0] = A.t[1] = __int_as_float(0x7f800000);
@@ -1873,14 +1994,26 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         const int *lm = P.lm + P.lmo[g];
         const int nt = (nm + 31) >> 5;
         const int t0 = (int)((long long)nt * kk / K), t1 = (int)((long long)nt * (kk + 1) / K);
+        int idn = -1;
+        if (t0 < t1) {
+            const int c = min(32, nm - t0 * 32);
+            idn = lane < c ? lm[t0 * 32 + lane] : -1;
+            fetch_p2m(P, S, idn, c, lane);
+        }
         for (int tt = t0; tt < t1; tt++) {
             const int b = tt * 32, c = min(32, nm - b);
-            stage_p2m<QUAD, MODE == MODE_VJP>(P, S, lm + b, c, T, lane);
+            const int id = idn;
+            cp_async_wait();
+            convert_p2m<QUAD, MODE == MODE_VJP>(P, S, id, c, T, lane);
+            __syncwarp();
+            if (tt + 1 < t1) { // the next tile's nodes in flight while this one is evaluated
+                const int cn = min(32, nm - b - 32);
+                idn = lane < cn ? lm[b + 32 + lane] : -1;
+                fetch_p2m(P, S, idn, cn, lane);
+            }
             if (MODE == MODE_JERK || MODE == MODE_TSTEP) {
-                if (lane < c) {
-                    const int id = lm[b + lane];
-                    S.tV[lane] = (unsigned)id < (unsigned)P.nn ? P.nV[id] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                if (lane < c)
+                    S.m.x.tV[lane] = (unsigned)id < (unsigned)P.nn ? P.nV[id] : make_float4(0.f, 0.f, 0.f, 0.f);
                 __syncwarp();
             }
             if (MODE == MODE_TSTEP) {
@@ -1902,8 +2035,8 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         az += v.z;
         if (EXTRA) {
 #pragma unroll
-            for (int c = 0; c < 6; c++) A.t[c] += S.sTid[T.tl][c];
-            A.iso += S.sTid[T.tl][6];
+            for (int c = 0; c < 6; c++) A.t[c] += S.m.x.sTid[T.tl][c];
+            A.iso += S.m.x.sTid[T.tl][6];
         }
     }
     __syncwarp();
