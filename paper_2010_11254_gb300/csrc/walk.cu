@@ -1897,13 +1897,16 @@ __device__ __forceinline__ void eval_p2p_list(const WalkParams &P, EvalSmem &S, 
         return;
     }
     int qh = 0, qt = 0, rn = r;
-    // keep >= 32 ranges (or all that are left) queued: a tile spans at most 32
+    // keep >= 32 ranges (or all that are left) queued: a tile spans at most
+    // 32; the next batch of ranges is read into a register one refill ahead
+    int2 nextr = lane < nr - rn ? rr[rn + lane] : make_int2(0, 0);
     auto refill = [&]() {
         if (qt - qh < 32 && rn < nr) {
             const int k = min(32, nr - rn);
-            if (lane < k) S.leafq[(qt + lane) & 63] = rr[rn + lane];
+            if (lane < k) S.leafq[(qt + lane) & 63] = nextr;
             qt += k;
             rn += k;
+            nextr = lane < nr - rn ? rr[rn + lane] : make_int2(0, 0);
             __syncwarp();
         }
     };
@@ -1994,11 +1997,14 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
         const int *lm = P.lm + P.lmo[g];
         const int nt = (nm + 31) >> 5;
         const int t0 = (int)((long long)nt * kk / K), t1 = (int)((long long)nt * (kk + 1) / K);
-        int idn = -1;
+        // node ids are read one tile ahead of their records' copies, which run
+        // one tile ahead of the evaluation
+        auto list_id = [&](int tt) { return (tt < t1 && tt * 32 + lane < nm) ? lm[tt * 32 + lane] : -1; };
+        int idn = -1, idnn = -1;
         if (t0 < t1) {
-            const int c = min(32, nm - t0 * 32);
-            idn = lane < c ? lm[t0 * 32 + lane] : -1;
-            fetch_p2m(P, S, idn, c, lane);
+            idn = list_id(t0);
+            fetch_p2m(P, S, idn, min(32, nm - t0 * 32), lane);
+            idnn = list_id(t0 + 1);
         }
         for (int tt = t0; tt < t1; tt++) {
             const int b = tt * 32, c = min(32, nm - b);
@@ -2007,9 +2013,9 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
             convert_p2m<QUAD, MODE == MODE_VJP>(P, S, id, c, T, lane);
             __syncwarp();
             if (tt + 1 < t1) { // the next tile's nodes in flight while this one is evaluated
-                const int cn = min(32, nm - b - 32);
-                idn = lane < cn ? lm[b + 32 + lane] : -1;
-                fetch_p2m(P, S, idn, cn, lane);
+                idn = idnn;
+                fetch_p2m(P, S, idn, min(32, nm - b - 32), lane);
+                idnn = list_id(tt + 2);
             }
             if (MODE == MODE_JERK || MODE == MODE_TSTEP) {
                 if (lane < c)
@@ -2651,7 +2657,9 @@ template <int MODE>
 static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
 {
     t->n_launch += 2;
-    const int blocks = num_sms() * WALK_MINB;
+    // the list-only walks (no evaluation, fewer registers) are latency-bound:
+    // two more resident blocks per SM keep more groups in flight
+    const int blocks = num_sms() * (MODE == MODE_COUNT || MODE == MODE_LIST ? WALK_MINB + 2 : WALK_MINB);
     const int retry_blocks = num_sms();
     if (t->prm.quadrupole) {
         k_walk<true, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
