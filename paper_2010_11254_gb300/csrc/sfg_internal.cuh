@@ -106,6 +106,8 @@ struct Tree {
     int64_t la_cap = 0, la_n = -1;
     bool la_all = false;   // it was NULL (every particle)
     bool lists_ok = false;
+    long long grp_gen = 0;        // groups formed so far (each call forms its active set's, unless reused)
+    long long lists_grp_gen = -1; // grp_gen when the kept lists were built for the groups in the workspace
     // relative opening criterion: |g_prev| per sorted rank, alpha
     double *gps = nullptr;
     double rel_alpha = 0.0;

@@ -2671,14 +2671,22 @@ static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
 }
 
 // counters: [0] p2p [1] p2m [2] overflow count [3] work [4] retry work [5] ngroups (int)
-static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, WalkParams &P, cudaStream_t s)
+// reuse_groups: the workspace still holds the groups of this active set (the
+// last groups formed, for the kept lists): take them as they are.
+static int prepare(Tree *t, const int64_t *active, int64_t n_active, Work &w, WalkParams &P, cudaStream_t s,
+                   bool reuse_groups = false)
 {
+    const size_t ws_before = t->ws_bytes;
     int rc = get_work(t, s, w);
     if (rc) return rc;
+    if (t->ws_bytes != ws_before) reuse_groups = false; // a new workspace holds no groups
     SFG_CUDA_OK(cudaMemsetAsync(t->d_counters, 0, NCOUNTERS * sizeof(unsigned long long), s));
-    const int *dng;
-    rc = form_groups(t, active, n_active, w, &dng, s);
-    if (rc) return rc;
+    if (!reuse_groups) {
+        const int *dng;
+        rc = form_groups(t, active, n_active, w, &dng, s);
+        if (rc) return rc;
+        t->grp_gen++;
+    }
     int *d_ngroups = (int *)(t->d_counters + 5);
     k_ngroups<<<1, 1, 0, s>>>(w.pre, (int)t->n, w.goff, t->d_counters);
     t->n_launch += 1;
@@ -2818,9 +2826,11 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
     return SFG_OK;
 }
 
-// Record the active set the stored lists belong to.
+// Record the active set the stored lists belong to (and that the groups now
+// in the workspace are theirs).
 static int remember_active(Tree *t, const int64_t *active, int64_t n_active, cudaStream_t s)
 {
+    t->lists_grp_gen = t->grp_gen;
     t->la_all = active == nullptr;
     t->la_n = n_active;
     if (active) {
@@ -3243,27 +3253,46 @@ __global__ void k_gnode_unit(double *gnode, const double *nM, int nn)
 //   dL/dm_k  += gM + v.(x - c) + 3 (x-c)^T S (x-c) - |x-c|^2 tr S
 //   dL/dx_k  += m_k (v + 6 S (x-c) - 2 tr S (x-c)),
 // are re-expanded about each child's centre c' = c + d (exact identity).
+__device__ __forceinline__ void push_node(double *gnode, const double *ncom, const int32_t *nparent, int c)
+{
+    int p = nparent[c];
+    const double *gp = gnode + 10 * (size_t)p;
+    double *gc = gnode + 10 * (size_t)c;
+    double d[3];
+    for (int a = 0; a < 3; a++) d[a] = ncom[3 * (size_t)c + a] - ncom[3 * (size_t)p + a];
+    const double *S = gp + 4; // xx yy zz xy xz yz
+    double tr = S[0] + S[1] + S[2];
+    double Sd[3] = {S[0] * d[0] + S[3] * d[1] + S[4] * d[2], S[3] * d[0] + S[1] * d[1] + S[5] * d[2],
+                    S[4] * d[0] + S[5] * d[1] + S[2] * d[2]};
+    double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double dSd = d[0] * Sd[0] + d[1] * Sd[1] + d[2] * Sd[2];
+    gc[0] += gp[0] + gp[1] * d[0] + gp[2] * d[1] + gp[3] * d[2] + 3.0 * dSd - dd * tr;
+    for (int a = 0; a < 3; a++) gc[1 + a] += gp[1 + a] + 6.0 * Sd[a] - 2.0 * tr * d[a];
+    for (int q = 0; q < 6; q++) gc[4 + q] += S[q];
+}
+
 __global__ void k_gnode_push(double *gnode, const double *ncom, const int32_t *nparent, int b, int e)
 {
-    for (int c = b + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x) {
-        int p = nparent[c];
-        const double *gp = gnode + 10 * (size_t)p;
-        double *gc = gnode + 10 * (size_t)c;
-        double d[3];
-        for (int a = 0; a < 3; a++) d[a] = ncom[3 * (size_t)c + a] - ncom[3 * (size_t)p + a];
-        const double *S = gp + 4; // xx yy zz xy xz yz
-        double tr = S[0] + S[1] + S[2];
-        double Sd[3] = {S[0] * d[0] + S[3] * d[1] + S[4] * d[2], S[3] * d[0] + S[1] * d[1] + S[5] * d[2],
-                        S[4] * d[0] + S[5] * d[1] + S[2] * d[2]};
-        double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        double dSd = d[0] * Sd[0] + d[1] * Sd[1] + d[2] * Sd[2];
-        gc[0] += gp[0] + gp[1] * d[0] + gp[2] * d[1] + gp[3] * d[2] + 3.0 * dSd - dd * tr;
-        for (int a = 0; a < 3; a++) gc[1 + a] += gp[1 + a] + 6.0 * Sd[a] - 2.0 * tr * d[a];
-        for (int q = 0; q < 6; q++) gc[4 + q] += S[q];
-    }
+    for (int c = b + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x)
+        push_node(gnode, ncom, nparent, c);
 }
 
 // Leaves to their members, then unpermute into the caller's order with G.
+// The small top levels (1..top) in one block, top-down, a barrier between
+// levels (a parent's terms are final before its children take them).
+struct PushLevels {
+    int off[SFG_LMAX + 3];
+};
+
+__global__ void __launch_bounds__(256)
+    k_gnode_push_top(double *gnode, const double *ncom, const int32_t *nparent, PushLevels L, int top)
+{
+    for (int l = 1; l <= top; l++) {
+        for (int c = L.off[l] + threadIdx.x; c < L.off[l + 1]; c += blockDim.x) push_node(gnode, ncom, nparent, c);
+        __syncthreads();
+    }
+}
+
 // Leaves to their members.  A member's terms are a polynomial in its offset
 // s = x - c from the leaf's centre of mass, evaluated in FP32 (s from the
 // stored FP32 offsets of member and centre of mass against the leaf centre)
@@ -3320,8 +3349,16 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
     Work w;
     WalkParams P;
     ph_begin(t, PH_VJP, s);
-    int rc = prepare(t, active, n_active, w, P, s);
+    // the forward's lists and groups when it was called with the same active set
+    bool match = false;
+    const bool lists = n_active > 0 && use_lists(t, s);
+    if (lists) {
+        int rc0 = lists_match(t, active, n_active, s, match);
+        if (rc0) return rc0;
+    }
+    int rc = prepare(t, active, n_active, w, P, s, match && t->lists_grp_gen == t->grp_gen);
     if (rc) return rc;
+    if (!t->lists_ok) match = false; // a new workspace: the list sizes were dropped with the old one
     // adjoint workspace: cotd [n][4] f64, cot [n] float4, gpart [n][4] f64, gnode [nn][10] f64
     size_t need = align_up(32 * (size_t)n) + align_up(16 * (size_t)n) + align_up(32 * (size_t)n) +
                   align_up(80 * (size_t)nn);
@@ -3351,12 +3388,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         P.cot = cot;
         P.gpart = gpart;
         P.gnode = gnode;
-        const bool lists = use_lists(t, s);
         if (lists) {
-            // the forward's lists when it was called with the same active set
-            bool match = false;
-            rc = lists_match(t, active, n_active, s, match);
-            if (rc) return rc;
             if (!match) {
                 rc = build_lists(t, w, P, s);
                 if (rc) return rc;
@@ -3378,7 +3410,16 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         ph_end(t, PH_VJP_WALK, s);
         k_gnode_unit<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nM, nn);
         t->n_launch += 4;
-        for (int l = 1; l <= t->depth; l++) {
+        // levels 1..top hold few nodes each: one block pushes them in one launch
+        int top = 0;
+        while (top + 1 <= t->depth && t->lvl_off[top + 2] - t->lvl_off[top + 1] <= 2048) top++;
+        if (top >= 1) {
+            PushLevels L;
+            for (int l = 0; l < SFG_LMAX + 3; l++) L.off[l] = t->lvl_off[l];
+            k_gnode_push_top<<<1, 256, 0, s>>>(gnode, t->ncom, t->nparent, L, top);
+            t->n_launch += 1;
+        }
+        for (int l = top + 1; l <= t->depth; l++) {
             int b = t->lvl_off[l], e = t->lvl_off[l + 1];
             if (e > b) {
                 k_gnode_push<<<grid_for(e - b, BT), BT, 0, s>>>(gnode, t->ncom, t->nparent, b, e);
