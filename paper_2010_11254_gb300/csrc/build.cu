@@ -332,6 +332,142 @@ __global__ void __launch_bounds__(RS_WARPS * 32)
 }
 
 
+// ----------------------------------------------------- one-sweep passes ----
+// Each pass of the stable LSD sort in one launch: the global count of every
+// digit of every pass is taken once up front (it does not depend on the
+// order), and each tile finds its offsets per digit by a decoupled look-back
+// over the tiles before it.  Tiles are numbered in the order blocks start
+// (an atomic counter), so every tile a block waits on has started and never
+// waits on a later one; the waits are bounded all the same and give up with
+// ST_ETIMEOUT.
+constexpr int RS_MAXPASS = 10;                     // 8 key passes + up to 2 cloud-id passes
+constexpr unsigned long long RS_AGG = 1ull << 32;  // look-back word: flag in the high half, count below
+constexpr unsigned long long RS_INC = 2ull << 32;
+
+__global__ void __launch_bounds__(256)
+    k_rs_count_all(const uint64_t *key, int n, const uint16_t *cloud_of, int cloud_passes, unsigned *gcount)
+{
+    __shared__ unsigned h[RS_MAXPASS][256];
+    for (int i = threadIdx.x; i < RS_MAXPASS * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t k = key[i];
+#pragma unroll
+        for (int p = 0; p < 8; p++) atomicAdd(&h[p][(k >> (8 * p)) & 255], 1u);
+        if (cloud_passes) {
+            const unsigned c = cloud_of[i]; // the values are the input indices at this point
+            for (int q = 0; q < cloud_passes; q++) atomicAdd(&h[8 + q][(c >> (8 * q)) & 255], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (8 + cloud_passes) * 256; i += blockDim.x) {
+        const unsigned v = (&h[0][0])[i];
+        if (v) atomicAdd(&gcount[i], v);
+    }
+}
+
+// Exclusive prefix of the digit counts of each pass (one block of 256).
+__global__ void k_rs_start(const unsigned *gcount, int npass, unsigned *gstart)
+{
+    __shared__ unsigned sh[256];
+    for (int p = 0; p < npass; p++) {
+        sh[threadIdx.x] = gcount[p * 256 + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned run = 0;
+            for (int d = 0; d < 256; d++) {
+                const unsigned c = sh[d];
+                sh[d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        gstart[p * 256 + threadIdx.x] = sh[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RS_WARPS * 32)
+    k_rs_onesweep(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n, int shift,
+                  const uint16_t *cl, const unsigned *gstart, unsigned long long *look, unsigned *tile_ctr,
+                  int *status)
+{
+    __shared__ int wcnt[RS_WARPS][256];
+    __shared__ unsigned start[256];
+    __shared__ int s_tile;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+    for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+    __syncthreads();
+    const int tile = s_tile;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t k[RS_ITEMS];
+    uint32_t v[RS_ITEMS];
+    int dg[RS_ITEMS], loc[RS_ITEMS];
+    const int base = tile * RS_TILE + w * 32 * RS_ITEMS;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        int i = base + r * 32 + lane;
+        bool valid = i < n;
+        k[r] = valid ? kin[i] : 0;
+        v[r] = valid ? vin[i] : 0;
+        int d = valid ? rs_digit(k[r], v[r], shift, cl) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = __popc(peers & lt);
+        int c0 = valid ? wcnt[w][d] : 0;
+        __syncwarp();
+        if (valid && (31 - __clz(peers)) == lane) wcnt[w][d] = c0 + __popc(peers);
+        __syncwarp();
+        dg[r] = d;
+        loc[r] = c0 + before;
+    }
+    __syncthreads();
+    {
+        // thread t owns digit t: exclusive prefix over the warps, the tile's
+        // count, then the count of all earlier tiles by look-back
+        const int d = threadIdx.x;
+        unsigned run = 0;
+        for (int ww = 0; ww < RS_WARPS; ww++) {
+            const int c = wcnt[ww][d];
+            wcnt[ww][d] = (int)run;
+            run += (unsigned)c;
+        }
+        unsigned long long *mine = look + (size_t)tile * 256 + d;
+        unsigned excl = 0;
+        if (tile == 0) {
+            atomicExch(mine, RS_INC | run);
+        } else {
+            atomicExch(mine, RS_AGG | run);
+            int j = tile - 1;
+            for (long long spin = 0; j >= 0;) {
+                const unsigned long long x = *(volatile unsigned long long *)(look + (size_t)j * 256 + d);
+                const unsigned long long f = x & ~0xffffffffull;
+                if (f == 0ull) {
+                    if (++spin > (1ll << 24)) { // a tile that never published: give up
+                        atomicOr(status, ST_ETIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                excl += (unsigned)x;
+                if (f == RS_INC) break;
+                j--;
+            }
+            atomicExch(mine, RS_INC | (excl + run));
+        }
+        start[d] = gstart[d] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        if (dg[r] < 256) {
+            const unsigned p = start[dg[r]] + (unsigned)wcnt[w][dg[r]] + (unsigned)loc[r];
+            kout[p] = k[r];
+            vout[p] = v[r];
+        }
+    }
+}
+
 // --------------------------------------------------------------- gather ----
 __global__ void k_pack(const double *pos, const double *mass, const double *soft, const uint8_t *sink, int n,
                        const uint32_t *val, int32_t *order, int32_t *rank, double *pos_s, double *mass_s,
@@ -770,6 +906,23 @@ __global__ void k_internal_moments(MomArgs A, int b, int e)
         if (A.nnchild[node] != 0) internal_moments(A, A.fr[A.ncloud[node]], node);
 }
 
+constexpr int SMALL_LEVEL = 2048; // nodes per level taken by the single-block pass
+
+// The small top levels (0..top) in one block, deepest first, a barrier
+// between levels (the children of a level are final before it starts).
+struct LevelOffsets {
+    int off[SFG_LMAX + 3];
+};
+
+__global__ void __launch_bounds__(256) k_internal_moments_top(MomArgs A, LevelOffsets L, int top)
+{
+    for (int l = top; l >= 0; l--) {
+        for (int node = L.off[l] + threadIdx.x; node < L.off[l + 1]; node += blockDim.x)
+            if (A.nnchild[node] != 0) internal_moments(A, A.fr[A.ncloud[node]], node);
+        __syncthreads();
+    }
+}
+
 // Leaf ids in node order (the slots past the leaf count hold -1).
 __global__ void k_leaf_flags(const int32_t *nnchild, int nn, int *flag)
 {
@@ -872,21 +1025,28 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     if (C > 1) ALLOC(cloud_of, uint16_t, n);
     k_keys<<<cg, BT, 0, s>>>(pos, t->d_off, t->d_frame, k0, v0, cloud_of);
     const int nb = (n + RS_TILE - 1) / RS_TILE;
-    int *hist, *hoff, *d_hn, *scr;
-    ALLOC(hist, int, 256 * (size_t)nb);
-    ALLOC(hoff, int, 256 * (size_t)nb + 1);
-    ALLOC(d_hn, int, 1);
+    int *scr;
+    unsigned *gcount, *gstart, *tile_ctr;
+    unsigned long long *look;
     ALLOC(scr, int, scan_scratch_bytes() / sizeof(int));
-    k_set_int<<<1, 1, 0, s>>>(d_hn, 256 * nb);
+    ALLOC(gcount, unsigned, RS_MAXPASS * 256);
+    ALLOC(gstart, unsigned, RS_MAXPASS * 256);
+    ALLOC(tile_ctr, unsigned, RS_MAXPASS);
+    ALLOC(look, unsigned long long, 256 * (size_t)nb);
     const int cloud_passes = C <= 1 ? 0 : (C <= 256 ? 1 : 2);
-    t->n_launch += 1 + (8 + cloud_passes) * 5 + 1; // set, passes x (hist, 3 scan, scatter), pack
-    for (int pass = 0; pass < 8 + cloud_passes; pass++) {
+    const int npass = 8 + cloud_passes;
+    SFG_CUDA_OK(cudaMemsetAsync(gcount, 0, sizeof(unsigned) * RS_MAXPASS * 256, s));
+    SFG_CUDA_OK(cudaMemsetAsync(tile_ctr, 0, sizeof(unsigned) * RS_MAXPASS, s));
+    k_rs_count_all<<<std::min(nb, num_sms() * 2), 256, 0, s>>>(k0, n, cloud_of, cloud_passes, gcount);
+    k_rs_start<<<1, 256, 0, s>>>(gcount, npass, gstart);
+    t->n_launch += 2 + npass + 1; // counts, starts, one launch per pass, pack
+    for (int pass = 0; pass < npass; pass++) {
         const bool by_cloud = pass >= 8;
         int shift = by_cloud ? 8 * (pass - 8) : 8 * pass;
         const uint16_t *cl = by_cloud ? cloud_of : nullptr;
-        k_rs_hist<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, n, shift, hist, nb, cl);
-        scan_exclusive(hist, hoff, d_hn, 256 * nb, nullptr, nullptr, scr, s);
-        k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, k1, v1, n, shift, hoff, nb, cl);
+        SFG_CUDA_OK(cudaMemsetAsync(look, 0, sizeof(unsigned long long) * 256 * (size_t)nb, s));
+        k_rs_onesweep<<<nb, RS_WARPS * 32, 0, s>>>(k0, v0, k1, v1, n, shift, cl, gstart + 256 * pass, look,
+                                                   tile_ctr + pass, t->d_status);
         uint64_t *tk = k0;
         k0 = k1;
         k1 = tk;
@@ -896,9 +1056,10 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     }
     t->key = k0;
     dev_free(t, k1, s);
-    dev_free(t, hist, s);
-    dev_free(t, hoff, s);
-    dev_free(t, d_hn, s);
+    dev_free(t, gcount, s);
+    dev_free(t, gstart, s);
+    dev_free(t, tile_ctr, s);
+    dev_free(t, look, s);
 
     ALLOC(t->order, int32_t, n);
     ALLOC(t->rank, int32_t, n);
@@ -1024,9 +1185,18 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.nn = nn;
     k_leaf_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);
     t->n_launch += 1;
-    for (int l = t->depth - 1; l >= 0; l--) {
+    // levels 0..top hold few nodes each: one block takes them in one launch
+    int top = -1;
+    while (top + 1 < t->depth && t->lvl_off[top + 2] - t->lvl_off[top + 1] <= SMALL_LEVEL) top++;
+    for (int l = t->depth - 1; l > top; l--) {
         int b = t->lvl_off[l], e = t->lvl_off[l + 1];
         k_internal_moments<<<grid_for(e - b, 128), 128, 0, s>>>(A, b, e);
+        t->n_launch += 1;
+    }
+    if (top >= 0) {
+        LevelOffsets L;
+        for (int l = 0; l < SFG_LMAX + 3; l++) L.off[l] = t->lvl_off[l];
+        k_internal_moments_top<<<1, 256, 0, s>>>(A, L, top);
         t->n_launch += 1;
     }
     dev_free(t, nS, s);
