@@ -95,3 +95,31 @@ def test_timestep_matches_oracle():
     do = oracle.tidal_dt(T, 0.02)
     assert np.isinf(dt[0]) and np.isinf(do[0])
     np.testing.assert_allclose(dt[1:], do[1:], rtol=1e-13)
+
+
+def test_error_paths():
+    """The stored-list passes refuse an all-FP64 tree; empty active sets are no-ops."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.uniform_cloud(500, seed=3)
+    pos, mass, soft, sink = to_dev(c, torch)
+    t64 = sfg.Tree(pos, mass, soft, sink, precision=1)
+    with pytest.raises(sfg.SfgError) as e:
+        t64.accel_tidal(None)
+    assert e.value.code == sfg.SFG_EINVAL
+    vel = torch.zeros((c.n, 3), dtype=torch.float64, device=pos.device)
+    with pytest.raises(sfg.SfgError):
+        t64.accel_jerk(vel)
+    with pytest.raises(sfg.SfgError):
+        t64.sink_timestep(vel, 0.01)
+    t64.close()
+    t = sfg.Tree(pos, mass, soft, sink)
+    empty = torch.zeros(0, dtype=torch.int64, device=pos.device)
+    a, p, T = t.accel_tidal(empty)
+    assert a.shape == (0, 3) and T.shape == (0, 6)
+    with pytest.raises(sfg.SfgError):
+        t.sink_timestep(vel, -1.0)
+    with pytest.raises(sfg.SfgError):
+        t.set_relative(torch.ones(c.n, dtype=torch.float64, device=pos.device), -0.5)
+    assert t.status() == sfg.SFG_OK
+    t.close()
