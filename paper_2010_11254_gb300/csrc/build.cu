@@ -341,6 +341,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32)
 // waits on a later one; the waits are bounded all the same and give up with
 // ST_ETIMEOUT.
 constexpr int RS_MAXPASS = 10;                     // 8 key passes + up to 2 cloud-id passes
+constexpr int OS_ITEMS = 8;                        // keys per thread of a one-sweep tile
+constexpr int OS_TILE = RS_WARPS * 32 * OS_ITEMS;  // 2048 keys: few registers, 4 blocks per SM
 constexpr unsigned long long RS_AGG = 1ull << 32;  // look-back word: flag in the high half, count below
 constexpr unsigned long long RS_INC = 2ull << 32;
 
@@ -387,7 +389,7 @@ __global__ void k_rs_start(const unsigned *gcount, int npass, unsigned *gstart)
     }
 }
 
-__global__ void __launch_bounds__(RS_WARPS * 32)
+__global__ void __launch_bounds__(RS_WARPS * 32, 4)
     k_rs_onesweep(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n, int shift,
                   const uint16_t *cl, const unsigned *gstart, unsigned long long *look, unsigned *tile_ctr,
                   int *status)
@@ -401,12 +403,12 @@ __global__ void __launch_bounds__(RS_WARPS * 32)
     __syncthreads();
     const int tile = s_tile;
     const unsigned lt = (1u << lane) - 1u;
-    uint64_t k[RS_ITEMS];
-    uint32_t v[RS_ITEMS];
-    int dg[RS_ITEMS], loc[RS_ITEMS];
-    const int base = tile * RS_TILE + w * 32 * RS_ITEMS;
+    uint64_t k[OS_ITEMS];
+    uint32_t v[OS_ITEMS];
+    int dg[OS_ITEMS], loc[OS_ITEMS];
+    const int base = tile * OS_TILE + w * 32 * OS_ITEMS;
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; r++) {
+    for (int r = 0; r < OS_ITEMS; r++) {
         int i = base + r * 32 + lane;
         bool valid = i < n;
         k[r] = valid ? kin[i] : 0;
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32)
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; r++) {
+    for (int r = 0; r < OS_ITEMS; r++) {
         if (dg[r] < 256) {
             const unsigned p = start[dg[r]] + (unsigned)wcnt[w][dg[r]] + (unsigned)loc[r];
             kout[p] = k[r];
@@ -1024,7 +1026,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(v1, uint32_t, n);
     if (C > 1) ALLOC(cloud_of, uint16_t, n);
     k_keys<<<cg, BT, 0, s>>>(pos, t->d_off, t->d_frame, k0, v0, cloud_of);
-    const int nb = (n + RS_TILE - 1) / RS_TILE;
+    const int nb = (n + OS_TILE - 1) / OS_TILE;
     int *scr;
     unsigned *gcount, *gstart, *tile_ctr;
     unsigned long long *look;
