@@ -17,6 +17,7 @@ by writing a 512 MB buffer.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload clumpy-2M|paper-20M] [--active-frac F]
+    python bench.py --opening-curve     # accuracy vs cost of the opening rules
 
 Multi-GPU (torchrun): every rank solves its own independent cloud (seed +
 rank); no collective touches the data path; timing is the max over ranks.
@@ -601,6 +602,62 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
     return line
 
 
+def run_opening_curve(args, wl, c, act, dev):
+    """Accuracy against cost of the opening rules of Sec. 2.2 on one cloud:
+    the Theta rule alone over a range of Theta, and Theta together with the
+    acceleration-based relative clause over a range of alpha.  |g_prev| is the
+    field of an accurate pass (Theta = 0.2) standing in for the previous
+    step's.  One JSON line per point: the forward time of sfg_accel (groups,
+    walk, evaluation; the build is the same for every point and excluded),
+    interactions per active row, and the force error against the FP64 direct
+    sum on sampled active rows (the direct sums are taken once)."""
+    import torch
+    import oracle
+    import paper_2010_11254_gb300 as sfg
+    d_pos = torch.from_numpy(c.pos).to(dev)
+    d_mass = torch.from_numpy(c.mass).to(dev)
+    d_soft = torch.from_numpy(c.soft).to(dev)
+    d_sink = torch.from_numpy(c.is_sink).to(dev)
+    d_act = torch.from_numpy(act).to(dev)
+    leaf = args.leaf_size or 32
+    group = args.group_size or 16
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(act.size, min(args.error_sample, act.size), replace=False))
+    ad, _ = oracle.direct(c.pos, c.mass, c.soft, c.is_sink, act[pick])
+    t = sfg.Tree(d_pos, d_mass, d_soft, d_sink, theta=0.2, leaf_size=leaf, group_size=group)
+    acc, _ = t.accel(d_act)
+    t.check()
+    t.close()
+    g_prev = torch.zeros(c.n, dtype=torch.float64, device=dev)
+    g_prev[d_act] = torch.linalg.vector_norm(acc, dim=1)
+    points = [(th, 0.0) for th in (0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 1.0)]
+    points += [(th, al) for th in (0.7, 1.0) for al in (0.001, 0.0025, 0.005, 0.01, 0.02)]
+    for theta, alpha in points:
+        fwd = []
+        for k in range(args.warmup + args.steps):
+            t = sfg.Tree(d_pos, d_mass, d_soft, d_sink, theta=theta, leaf_size=leaf, group_size=group)
+            if alpha > 0.0:
+                t.set_relative(g_prev, alpha)
+            t.set_timing(True)
+            acc, _ = t.accel(d_act)
+            torch.cuda.synchronize(dev)
+            st = t.stats()
+            t.check()
+            t.close()
+            if k >= args.warmup:
+                fwd.append(st["fwd_ms"])
+        a = acc.cpu().numpy()[pick]
+        e = np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        print(json.dumps({
+            "metric": "opening-rule accuracy vs cost", "workload": args.workload, "theta": theta,
+            "rule": "theta" if alpha == 0.0 else "theta + relative", "alpha": alpha or None,
+            "leaf_size": leaf, "group_size": group, "fwd_ms": round(statistics.median(fwd), 4),
+            "interactions_per_active": round((st["n_p2p"] + st["n_p2m"]) / act.size, 1),
+            "p2p_per_active": round(st["n_p2p"] / act.size, 1), "p2m_per_active": round(st["n_p2m"] / act.size, 1),
+            "force_error": {"vs": "FP64 direct sum", "sample": int(pick.size), "median": float(np.median(e)),
+                            "p99": float(np.percentile(e, 99)), "max": float(e.max())}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -619,6 +676,8 @@ def main():
     ap.add_argument("--group-size", type=int, default=None, help="default: the autotuner's choice")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
+    ap.add_argument("--opening-curve", action="store_true",
+                    help="accuracy vs cost of the Theta and relative opening rules (one line per point)")
     args = ap.parse_args()
     wl = WORKLOADS.get(args.workload)
     rank = int(os.environ.get("RANK", "0"))
@@ -649,6 +708,10 @@ def main():
         return
 
     c, seed = make_cloud(wl, rank)
+    if args.opening_curve:
+        act, _, _ = make_active(c, wl["active"] if args.active_frac is None else args.active_frac, seed)
+        run_opening_curve(args, wl, c, act, dev)
+        return
     fracs = ([float(x) for x in args.active_fracs.split(",")] if args.active_fracs
              else [wl["active"] if args.active_frac is None else args.active_frac])
     for frac in fracs:

@@ -138,6 +138,7 @@ struct Tgt {
     // relative criterion: alpha * min |g_prev| over the group, the cloud's root side, cell^2
     bool rel;
     double rel_ag, rel_L0, rel_cell2;
+    float rel_agf, rel_GL0f, rel_cell2f; // FP32 roundings of alpha min|g|, G L0^2, cell^2
 };
 
 // ------------------------------------------------------------ kernels ----
@@ -697,12 +698,28 @@ __device__ __forceinline__ void test_node(const WalkParams &P, const Tgt &T, int
     acc = sc >= P.T[level] && sb >= need;
     if (acc && T.rel) {
         // relative criterion (Sec. 2.2, from GADGET-2), conservative for every
-        // target: G M L^2 <= alpha min|g_prev| (sc cell^2)^2, the same IEEE
-        // products in the same order as the oracle's
-        const double L = ldexp(T.rel_L0, -level);
-        const double lhs = __dmul_rn(__dmul_rn(P.rG, P.nM[node]), __dmul_rn(L, L));
-        const double r2 = __dmul_rn((double)sc, T.rel_cell2);
-        acc = lhs <= __dmul_rn(T.rel_ag, __dmul_rn(r2, r2));
+        // target: G M L^2 <= alpha min|g_prev| (sc cell^2)^2, decided as the
+        // oracle's IEEE FP64 products in the same order.  An FP32 screen goes
+        // first: both of its sides lie within 16 FP32 roundings (< 2^-19
+        // relative) of the FP64 sides, so where they differ by more than
+        // 2^-18 and both are normal (no flush to zero, no overflow) it takes
+        // the same decision; only the rest pays the FP64 products.
+        const float Mf = __ldg(reinterpret_cast<const float *>(P.E0) + 4 * (size_t)node + 3);
+        const float lhsf = Mf * (T.rel_GL0f * __int_as_float((127 - 2 * level) << 23));
+        const float r2f = __ull2float_rn(sc) * T.rel_cell2f;
+        const float rhsf = T.rel_agf * (r2f * r2f);
+        const float lo_ok = 0x1p-100f, hi_ok = 0x1p100f;
+        const bool normal = lhsf >= lo_ok && lhsf <= hi_ok && rhsf >= lo_ok && rhsf <= hi_ok;
+        if (normal && lhsf <= rhsf * (1.f - 0x1p-18f)) {
+            acc = true;
+        } else if (normal && lhsf >= rhsf * (1.f + 0x1p-18f)) {
+            acc = false;
+        } else {
+            const double L = ldexp(T.rel_L0, -level);
+            const double lhs = __dmul_rn(__dmul_rn(P.rG, P.nM[node]), __dmul_rn(L, L));
+            const double r2 = __dmul_rn((double)sc, T.rel_cell2);
+            acc = lhs <= __dmul_rn(T.rel_ag, __dmul_rn(r2, r2));
+        }
     }
     lf = !acc && leaf;
     op = !acc && !leaf;
@@ -938,6 +955,9 @@ __device__ __forceinline__ void setup_group(const WalkParams &P, int g, int lane
         T.rel_L0 = fr.L0;
         const double cell = ldexp(fr.L0, -SFG_LMAX);
         T.rel_cell2 = __dmul_rn(cell, cell);
+        T.rel_agf = (float)T.rel_ag;
+        T.rel_GL0f = (float)__dmul_rn(P.rG, __dmul_rn(fr.L0, fr.L0));
+        T.rel_cell2f = (float)T.rel_cell2;
     }
     double c0 = fr.x0[0] + (double)T.cg[0] * fr.half_cell;
     double c1 = fr.x0[1] + (double)T.cg[1] * fr.half_cell;

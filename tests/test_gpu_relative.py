@@ -92,3 +92,31 @@ def test_relative_adjoint_matches_oracle():
     scale = np.abs(od_pos).max()
     np.testing.assert_allclose(d_pos.cpu().numpy(), od_pos, rtol=0, atol=1e-4 * scale)
     np.testing.assert_allclose(d_mass.cpu().numpy(), od_mass, rtol=0, atol=1e-4 * np.abs(od_mass).max())
+
+
+@pytest.mark.parametrize("G", [1e-45, 1e40])
+def test_relative_lists_extreme_magnitudes(G):
+    """The walk screens the relative test in FP32 and decides in FP64 where
+    the FP32 sides are not normal numbers or lie close together; with G and
+    |g_prev| scaled far from 1 (all of one side, or part of it, outside the
+    FP32 screen's range) the lists stay those of the oracle's FP64 test."""
+    import oracle
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.clumpy_cloud(12000, n_clumps=12, n_sink=8, seed=31)
+    act = gen.active_subset(c.n, 0.3, seed=2)
+    ad, _ = oracle.direct(c.pos, c.mass, c.soft, c.is_sink, targets=np.arange(c.n))
+    gprev = G * np.linalg.norm(ad, axis=1)
+    pos, mass, soft, sink = to_dev(c, torch)
+    t = sfg.Tree(pos, mass, soft, sink, theta=0.8, leaf_size=16, group_size=32, G=G)
+    a_t = torch.from_numpy(act).cuda()
+    t.set_relative(torch.from_numpy(gprev).cuda(), 2e-3)
+    o = oracle_tree(c, 16)
+    o.set_relative(gprev, 2e-3, G=G)
+    o.walk(act, 32, 0.8)
+    n_rel = _lists_equal(t, a_t, o)
+    assert t.status() == sfg.SFG_OK
+    o.set_relative(None)
+    o.walk(act, 32, 0.8)
+    assert n_rel != int(o.groups()[:, 4].sum())  # the relative clause opened nodes
+    t.close()
