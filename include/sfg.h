@@ -286,6 +286,12 @@ const char *sfg_last_cuda_error(void);
  *   SFG_FIELD_NODE_HQ   uint64 [nn]       ceil((h_max / cell)^2), capped at 2^62
  *   SFG_FIELD_NODE_F64  float64 [nn][11]  M, com[3], Q[6] (xx yy zz xy xz yz), h_max
  *   SFG_FIELD_FRAMES    float64 [n_clouds][4]  x0[3], L0 of every cloud
+ *   SFG_FIELD_PARTICLE_F32 float32 [n][4] the evaluation's particle records, sorted:
+ *                                         x - c_leaf (c_leaf = centre of the particle's
+ *                                         leaf cell), m; each the FP32 rounding (to
+ *                                         nearest, even) of the FP64 value
+ *   SFG_FIELD_NODE_F32  float32 [nn][9]   the evaluation's node records: com - c_node,
+ *                                         M, Q xx yy xy xz yz; roundings as above
  * `bytes` must equal the field's size.  With several clouds, node ids are
  * breadth-first over the whole forest (the roots are nodes 0..n_clouds-1). */
 #define SFG_FIELD_FRAMES 6
@@ -294,6 +300,8 @@ const char *sfg_last_cuda_error(void);
 #define SFG_FIELD_NODE_INT 3
 #define SFG_FIELD_NODE_HQ 4
 #define SFG_FIELD_NODE_F64 5
+#define SFG_FIELD_PARTICLE_F32 7
+#define SFG_FIELD_NODE_F32 8
 int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes);
 
 /* Interaction lists of every group for the given active set (same walk as

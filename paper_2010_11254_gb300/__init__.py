@@ -26,6 +26,7 @@ from . import _build
 
 SFG_OK, SFG_EINVAL, SFG_ENOMEM, SFG_ECUDA, SFG_EOVERFLOW, SFG_ETIMEOUT = range(6)
 FIELD_KEYS, FIELD_ORDER, FIELD_NODE_INT, FIELD_NODE_HQ, FIELD_NODE_F64, FIELD_FRAMES = 1, 2, 3, 4, 5, 6
+FIELD_PARTICLE_F32, FIELD_NODE_F32 = 7, 8
 
 _lock = threading.Lock()
 _lib = None
@@ -295,7 +296,8 @@ class Tree:
         n, nn = st["n"], st["n_nodes"]
         shapes = {FIELD_KEYS: ((n,), np.uint64), FIELD_ORDER: ((n,), np.int32), FIELD_NODE_INT: ((nn, 16), np.int32),
                   FIELD_NODE_HQ: ((nn,), np.uint64), FIELD_NODE_F64: ((nn, 11), np.float64),
-                  FIELD_FRAMES: ((st["n_clouds"], 4), np.float64)}
+                  FIELD_FRAMES: ((st["n_clouds"], 4), np.float64), FIELD_PARTICLE_F32: ((n, 4), np.float32),
+                  FIELD_NODE_F32: ((nn, 9), np.float32)}
         shape, dt = shapes[field]
         out = np.zeros(shape, dt)
         _check(_load().sfg_export(self._h, field, out.ctypes.data, out.nbytes), "sfg_export")

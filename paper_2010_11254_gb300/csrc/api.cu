@@ -378,6 +378,24 @@ int sfg_export(sfg_tree *tree, int field, void *host_dst, size_t bytes)
         }
         return SFG_OK;
     }
+    case SFG_FIELD_PARTICLE_F32:
+        if (bytes != 16 * n) return SFG_EINVAL;
+        SFG_CUDA_OK(cudaMemcpy(host_dst, t->pw, bytes, cudaMemcpyDeviceToHost));
+        return SFG_OK;
+    case SFG_FIELD_NODE_F32: {
+        if (bytes != 36 * nn) return SFG_EINVAL;
+        std::vector<float4> e(3 * nn);
+        SFG_CUDA_OK(cudaMemcpy(&e[0], t->E0, 16 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&e[nn], t->E1, 16 * nn, cudaMemcpyDeviceToHost));
+        SFG_CUDA_OK(cudaMemcpy(&e[2 * nn], t->E2, 16 * nn, cudaMemcpyDeviceToHost));
+        float *o = (float *)host_dst;
+        for (size_t i = 0; i < nn; i++) {
+            const float4 a = e[i], b = e[nn + i], c = e[2 * nn + i];
+            const float r[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x};
+            for (int k = 0; k < 9; k++) o[9 * i + k] = r[k];
+        }
+        return SFG_OK;
+    }
     case SFG_FIELD_FRAMES: {
         const size_t C = (size_t)t->nclouds;
         if (bytes != 32 * C) return SFG_EINVAL;

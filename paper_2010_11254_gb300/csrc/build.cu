@@ -748,6 +748,33 @@ __device__ inline void node_centre(const Frame &fr, const uint32_t lo[3], int le
     }
 }
 
+// IEEE 754 round-to-nearest-even conversion FP64 -> FP32 on the integer
+// pipes (FP64 operations, conversions included, issue at 1/64 of the FP32
+// rate on this part, and the moment passes are bound by them).  A value in
+// the normal FP32 exponent range keeps the top 23 of its 52 fraction bits;
+// the 29 bits below decide the rounding (above half: up; exactly half: to
+// even); a carry out of the fraction moves into the exponent, up to infinity
+// past the largest float.  Zeros, FP32-subnormal magnitudes, infinities and
+// NaN take the hardware conversion.
+__device__ __forceinline__ float f32_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    if (e < -126 || e > 127) return (float)x;
+    unsigned f = ((unsigned)(e + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned r = lo & 0x1fffffffu;
+    f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | f);
+}
+
+// max of two non-negative doubles by their bit patterns (same order as the
+// values for +0 and positive finite numbers), off the FP64 pipe
+__device__ __forceinline__ double max_nonneg(double a, double b)
+{
+    return __double_as_longlong(b) > __double_as_longlong(a) ? b : a;
+}
+
 __device__ inline void write_records(const MomArgs &A, const Frame &fr, int node, int level, bool leaf, int link,
                                      int cnt, const uint32_t lo[3], const uint32_t hi[3], double M,
                                      const double com[3], const double Q[6], const double S[6], double hmax,
@@ -759,9 +786,9 @@ __device__ inline void write_records(const MomArgs &A, const Frame &fr, int node
     A.W1[node] = make_int4((int)hi[0], (int)hi[1], (int)hi[2], link);
     A.W2[node] = make_int4((int)cq[0], (int)cq[1], (int)cq[2], cnt);
     A.Whq[node] = hq_of(hmax, fr.scale);
-    A.E0[node] = make_float4((float)(com[0] - c[0]), (float)(com[1] - c[1]), (float)(com[2] - c[2]), (float)M);
-    A.E1[node] = make_float4((float)Q[0], (float)Q[1], (float)Q[3], (float)Q[4]);
-    A.E2[node] = make_float4((float)Q[5], __int_as_float(ci[0]), __int_as_float(ci[1]), __int_as_float(ci[2]));
+    A.E0[node] = make_float4(f32_rn(com[0] - c[0]), f32_rn(com[1] - c[1]), f32_rn(com[2] - c[2]), f32_rn(M));
+    A.E1[node] = make_float4(f32_rn(Q[0]), f32_rn(Q[1]), f32_rn(Q[3]), f32_rn(Q[4]));
+    A.E2[node] = make_float4(f32_rn(Q[5]), __int_as_float(ci[0]), __int_as_float(ci[1]), __int_as_float(ci[2]));
     A.nM[node] = M;
     for (int a = 0; a < 3; a++) A.ncom[3 * (size_t)node + a] = com[a];
     for (int k = 0; k < 6; k++) A.nQ[6 * (size_t)node + k] = Q[k];
@@ -836,11 +863,11 @@ __device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
             hi[a] = q[a] > hi[a] ? q[a] : hi[a];
         }
         double h = A.soft[k];
-        if (h > hmax) hmax = h;
+        hmax = max_nonneg(hmax, h);
         // particle record of the walk: FP32 offset from the leaf centre
-        float hs = (float)h;
+        float hs = f32_rn(h);
         if (A.sink[k]) hs = -hs;
-        A.pw[k] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)m);
+        A.pw[k] = make_float4(f32_rn(d[0]), f32_rn(d[1]), f32_rn(d[2]), f32_rn(m));
         A.pc[k] = make_int4(ci[0], ci[1], ci[2], __float_as_int(hs));
     }
     double com[3], Q[6];
@@ -862,8 +889,7 @@ __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
             lo[a] = l3[a] < lo[a] ? l3[a] : lo[a];
             hi[a] = h3[a] > hi[a] ? h3[a] : hi[a];
         }
-        double h = __ldcg(&A.nhmax[ch]);
-        if (h > hmax) hmax = h;
+        hmax = max_nonneg(hmax, __ldcg(&A.nhmax[ch]));
     }
     int ci[3];
     double cen[3];
@@ -908,7 +934,10 @@ __global__ void k_internal_moments(MomArgs A, int b, int e)
         if (A.nnchild[node] != 0) internal_moments(A, A.fr[A.ncloud[node]], node);
 }
 
-constexpr int SMALL_LEVEL = 2048; // nodes per level taken by the single-block pass
+// Nodes per level taken by the single-block pass.  A node's combine is ~200
+// FP64 operations and one SM retires 2 per clock, so a level in one block
+// costs about as much as a launch of its own at ~64 nodes.
+constexpr int SMALL_LEVEL = 64;
 
 // The small top levels (0..top) in one block, deepest first, a barrier
 // between levels (the children of a level are final before it starts).
@@ -1192,13 +1221,15 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     while (top + 1 < t->depth && t->lvl_off[top + 2] - t->lvl_off[top + 1] <= SMALL_LEVEL) top++;
     for (int l = t->depth - 1; l > top; l--) {
         int b = t->lvl_off[l], e = t->lvl_off[l + 1];
-        k_internal_moments<<<grid_for(e - b, 128), 128, 0, s>>>(A, b, e);
+        // one warp per block on the smaller levels, so that they spread over the SMs
+        const int bs = e - b <= num_sms() * 128 ? 32 : 128;
+        k_internal_moments<<<(e - b + bs - 1) / bs, bs, 0, s>>>(A, b, e);
         t->n_launch += 1;
     }
     if (top >= 0) {
         LevelOffsets L;
         for (int l = 0; l < SFG_LMAX + 3; l++) L.off[l] = t->lvl_off[l];
-        k_internal_moments_top<<<1, 256, 0, s>>>(A, L, top);
+        k_internal_moments_top<<<1, SMALL_LEVEL, 0, s>>>(A, L, top);
         t->n_launch += 1;
     }
     dev_free(t, nS, s);

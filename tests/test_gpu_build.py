@@ -31,8 +31,40 @@ def _compare_build(c, leaf_size):
     gf = t.export(sfg.FIELD_NODE_F64)
     of = o.nodes_f64()
     np.testing.assert_array_equal(gf, of[:, :11])                # M com Q hmax, bit for bit
+    _check_f32_records(t, c, order, gi, gf)
     assert t.status() == sfg.SFG_OK
     t.close()
+
+
+def _cell_centres(level, lo, x0, L0):
+    """Centres of the cells (level, lower corner in grid units): the exact
+    corner-plus-half-side in grid units times the half-cell size, plus x0."""
+    sh = 21 - level
+    corner = (lo >> sh[:, None]) << sh[:, None]
+    return x0[None, :] + (2 * corner + (np.int64(1) << sh)[:, None]).astype(np.float64) * np.ldexp(L0, -22)
+
+
+def _check_f32_records(t, c, order, gi, gf):
+    """The evaluation's FP32 records are the round-to-nearest-even FP32 values
+    of the FP64 quantities (numpy's float64 -> float32 cast), bit for bit:
+    particle offsets from their leaf's cell centre and masses; node centre-
+    of-mass offsets from the cell centre, masses and quadrupoles."""
+    import paper_2010_11254_gb300 as sfg
+    st = t.stats()
+    x0, L0 = np.array(st["x0"]), st["L0"]
+    cen = _cell_centres(gi[:, 0], gi[:, 6:9], x0, L0)
+    ef = t.export(sfg.FIELD_NODE_F32)
+    want = np.concatenate([gf[:, 1:4] - cen, gf[:, 0:1], gf[:, [4, 5, 7, 8, 9]]], 1).astype(np.float32)
+    np.testing.assert_array_equal(ef.view(np.uint32), want.view(np.uint32))
+    leaf = np.flatnonzero(gi[:, 5] == 0)
+    first, count = gi[leaf, 1], gi[leaf, 2]
+    owner = np.repeat(np.arange(leaf.size), count)
+    rank = np.concatenate([np.arange(f, f + k) for f, k in zip(first, count)]) if leaf.size else np.zeros(0, int)
+    pw = t.export(sfg.FIELD_PARTICLE_F32)
+    assert np.array_equal(np.sort(rank), np.arange(c.n))
+    d = c.pos[order[rank]] - cen[leaf[owner]]
+    np.testing.assert_array_equal(pw[rank, :3].view(np.uint32), d.astype(np.float32).view(np.uint32))
+    np.testing.assert_array_equal(pw[rank, 3].view(np.uint32), c.mass[order[rank]].astype(np.float32).view(np.uint32))
 
 
 @pytest.mark.parametrize("leaf_size", [1, 8, 16, 64])
