@@ -8,15 +8,19 @@
 //      two >= the largest extent;
 //   3. keys: cell q = floor((x - x0) 2^21 / L0) per axis (clamped), 63-bit
 //      Morton key, value = original index;
-//   4. stable LSD radix sort of (key, index), 8 passes of 8 bits;
+//   4. stable LSD radix sort of (key, index), 8 passes of 8 bits: every
+//      pass's digit counts in one read of the keys, then one launch per pass
+//      (tile offsets by a bounded decoupled look-back);
 //   5. gather sorted FP64 particle arrays;
 //   6. octree, one level at a time: a node with > N_leaf particles below
 //      level 21 is split into its non-empty octants (binary search of the
 //      child digit in the node's sorted key range); node ids are breadth-first;
-//   7. moments, bottom-up in one launch: leaves sum their members in sorted
-//      order, the last child to finish combines its siblings in octant order
-//      (parallel-axis theorem).  The operation order is fixed and this file
-//      is compiled without FMA contraction, so the FP64 moments are
+//   7. moments, bottom-up: leaves sum their members in sorted order (one
+//      lane per leaf, leaves taken by member count), then the internal
+//      levels, deepest first, combine their children in octant order
+//      (parallel-axis theorem; one launch per level, the small top levels
+//      in one block).  The operation order is fixed and this file is
+//      compiled without FMA contraction, so the FP64 moments are
 //      reproducible bit for bit.
 #include <cuda_runtime.h>
 #include <limits.h>
@@ -954,18 +958,69 @@ __global__ void __launch_bounds__(256) k_internal_moments_top(MomArgs A, LevelOf
     }
 }
 
-// Leaf ids in node order (the slots past the leaf count hold -1).
-__global__ void k_leaf_flags(const int32_t *nnchild, int nn, int *flag)
+// Leaf ids ordered by member count, largest first (the slots past the leaf
+// count hold -1).  A lane sums one leaf, so a warp runs as long as its
+// largest leaf: in node order the counts of neighbouring leaves differ
+// widely (clumpy clouds: ~40% of the lanes busy), by count they match.
+// A leaf's sums do not depend on where it sits in the list.
+constexpr int LB_BINS = 64; // counts 1..63, and >= 64 together
+
+__device__ __forceinline__ int leaf_bin(int count)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
-        flag[i] = nnchild[i] == 0;
+    return LB_BINS - min(max(count, 1), LB_BINS); // bin 0 = the largest leaves
 }
 
-__global__ void k_leaf_list(const int *flag, const int *pre, int nn, int *leaves)
+__global__ void k_leaf_hist(const int32_t *nnchild, const int32_t *ncount, int nn, unsigned *hist)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
-        if (flag[i]) leaves[pre[i]] = i;
-        if (i >= pre[nn]) leaves[i] = -1;
+    __shared__ unsigned h[LB_BINS];
+    for (int b = threadIdx.x; b < LB_BINS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+        if (nnchild[i] == 0) atomicAdd(&h[leaf_bin(ncount[i])], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < LB_BINS; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// exclusive prefix of the bins (one warp)
+__global__ void k_leaf_starts(const unsigned *hist, unsigned *cur)
+{
+    const int lane = threadIdx.x;
+    unsigned a = hist[lane], b = hist[lane + 32];
+    unsigned ia = a, ib = b;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ta;
+            ib += tb;
+        }
+    }
+    const unsigned tot_a = __shfl_sync(0xffffffffu, ia, 31);
+    cur[lane] = ia - a;
+    cur[lane + 32] = tot_a + ib - b;
+}
+
+// one block-wide chunk of nodes per iteration: ranks within the chunk from
+// shared counters, the chunk's range of each bin from one global atomic
+__global__ void k_leaf_scatter(const int32_t *nnchild, const int32_t *ncount, int nn, unsigned *cur, int *leaves)
+{
+    __shared__ unsigned h[LB_BINS], base[LB_BINS];
+    for (int c0 = blockIdx.x * blockDim.x; c0 < nn; c0 += gridDim.x * blockDim.x) {
+        for (int b = threadIdx.x; b < LB_BINS; b += blockDim.x) h[b] = 0;
+        __syncthreads();
+        const int i = c0 + threadIdx.x;
+        int bin = -1;
+        unsigned r = 0;
+        if (i < nn && nnchild[i] == 0) {
+            bin = leaf_bin(ncount[i]);
+            r = atomicAdd(&h[bin], 1u);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < LB_BINS; b += blockDim.x)
+            if (h[b]) base[b] = atomicAdd(&cur[b], h[b]);
+        __syncthreads();
+        if (bin >= 0) leaves[base[bin] + r] = i;
+        __syncthreads();
     }
 }
 
@@ -1172,18 +1227,19 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->ncom, double, 3 * (size_t)nn);
     ALLOC(t->nQ, double, 6 * (size_t)nn);
     ALLOC(t->nhmax, double, nn);
-    int *lflag, *lpre, *leaves, *d_nn;
+    int *leaves;
+    unsigned *lhist, *lcur;
     double *nS;
     ALLOC(nS, double, 6 * (size_t)nn);
-    ALLOC(lflag, int, nn);
-    ALLOC(lpre, int, nn + 1);
     ALLOC(leaves, int, nn);
-    ALLOC(d_nn, int, 1);
-    k_set_int<<<1, 1, 0, s>>>(d_nn, nn);
-    k_leaf_flags<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, nn, lflag);
-    scan_exclusive(lflag, lpre, d_nn, nn, nullptr, nullptr, scr, s);
-    k_leaf_list<<<grid_for(nn, BT), BT, 0, s>>>(lflag, lpre, nn, leaves);
-    t->n_launch += 6;
+    ALLOC(lhist, unsigned, 2 * LB_BINS);
+    lcur = lhist + LB_BINS;
+    SFG_CUDA_OK(cudaMemsetAsync(leaves, 0xff, sizeof(int) * (size_t)nn, s));
+    SFG_CUDA_OK(cudaMemsetAsync(lhist, 0, sizeof(unsigned) * LB_BINS, s));
+    k_leaf_hist<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->ncount, nn, lhist);
+    k_leaf_starts<<<1, 32, 0, s>>>(lhist, lcur);
+    k_leaf_scatter<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->ncount, nn, lcur, leaves);
+    t->n_launch += 3;
     MomArgs A;
     A.key = t->key;
     A.pos = t->pos_s;
@@ -1233,10 +1289,8 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         t->n_launch += 1;
     }
     dev_free(t, nS, s);
-    dev_free(t, lflag, s);
-    dev_free(t, lpre, s);
+    dev_free(t, lhist, s);
     dev_free(t, leaves, s);
-    dev_free(t, d_nn, s);
     dev_free(t, scr, s);
     t->frames_h.resize(C);
     SFG_CUDA_OK(cudaMemcpyAsync(t->frames_h.data(), t->d_frame, sizeof(Frame) * C, cudaMemcpyDeviceToHost, s));
