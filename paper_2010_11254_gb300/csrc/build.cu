@@ -142,6 +142,110 @@ void scan_exclusive(const int *in, int *out, const int *d_n, int max_n, int *ext
     scan_range(in, out, nullptr, d_n, max_n, extra_dst, extra_base, scratch, s);
 }
 
+// Single-pass exclusive scan (one launch): tiles of SP_TILE entries taken
+// in ticket order by a persistent grid; a tile publishes its total, then
+// its inclusive prefix once the tiles before it are known (decoupled
+// look-back, waits bounded: ST_ETIMEOUT).  The last block out zeroes the
+// tickets and look-back words, so the scratch is zero between scans and is
+// cleared once, when allocated.
+constexpr int SP_BT = 256, SP_ITEMS = 8, SP_TILE = SP_BT * SP_ITEMS;
+constexpr unsigned long long SP_AGG = 1ull << 62, SP_INC = 2ull << 62, SP_VAL = 0xffffffffull;
+
+static int sp_tiles(int max_n) { return std::max(1, (max_n + SP_TILE - 1) / SP_TILE); }
+
+size_t scan1p_bytes(int max_n) { return 16 + 8 * (size_t)sp_tiles(max_n); }
+
+__global__ void __launch_bounds__(SP_BT)
+    k_scan_1p(const int *in, int *out, const int *d_lo, const int *d_hi, int max_n, int *extra_dst,
+              const int *extra_base, unsigned *ctr, unsigned long long *look, int *status)
+{
+    __shared__ int sh[32];
+    __shared__ int s_tile, s_pre;
+    __shared__ bool s_last;
+    const int n = scan_len(d_lo, d_hi, max_n);
+    const int ntiles = max(1, (n + SP_TILE - 1) / SP_TILE);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntiles) break;
+        const int i0 = tile * SP_TILE + threadIdx.x * SP_ITEMS;
+        int v[SP_ITEMS], sum = 0;
+#pragma unroll
+        for (int k = 0; k < SP_ITEMS; k++) {
+            v[k] = i0 + k < n ? in[i0 + k] : 0;
+            sum += v[k];
+        }
+        int tot;
+        const int incl = block_incl_scan(sum, sh, &tot);
+        if (threadIdx.x == 0) {
+            unsigned pre = 0;
+            if (tile > 0) {
+                atomicExch(&look[tile], SP_AGG | (unsigned)tot);
+                for (long long j = tile - 1, spin = 0; j >= 0;) {
+                    const unsigned long long x = *(volatile unsigned long long *)(look + j);
+                    const unsigned long long f = x & ~SP_VAL;
+                    if (f == 0ull) {
+                        if (++spin > (1ll << 24)) { // a tile that never published: give up
+                            atomicOr(status, ST_ETIMEOUT);
+                            break;
+                        }
+                        continue;
+                    }
+                    pre += (unsigned)(x & SP_VAL);
+                    if (f == SP_INC) break;
+                    j--;
+                }
+            }
+            atomicExch(&look[tile], SP_INC | (pre + (unsigned)tot));
+            s_pre = (int)pre;
+            if (tile == ntiles - 1) {
+                const int total = (int)pre + tot;
+                out[n] = total;
+                if (extra_dst) *extra_dst = (int)min((long long)*extra_base + total, (long long)INT_MAX);
+            }
+        }
+        __syncthreads();
+        int run = s_pre + incl - sum;
+#pragma unroll
+        for (int k = 0; k < SP_ITEMS; k++) {
+            if (i0 + k < n) out[i0 + k] = run;
+            run += v[k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctr[1], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x) look[t] = 0ull;
+        if (threadIdx.x == 0) {
+            ctr[0] = 0u;
+            ctr[1] = 0u;
+        }
+    }
+}
+
+void Scan1P::attach(void *mem, int max_n_)
+{
+    ctr = (unsigned *)mem;
+    look = (unsigned long long *)((char *)mem + 16);
+    max_n = max_n_;
+}
+
+void Scan1P::init(void *mem, int max_n_, cudaStream_t s)
+{
+    attach(mem, max_n_);
+    cudaMemsetAsync(mem, 0, scan1p_bytes(max_n), s);
+}
+
+void Scan1P::range(const int *in, int *out, const int *d_lo, const int *d_hi, int bound, int *extra_dst,
+                   const int *extra_base, int *status, cudaStream_t s) const
+{
+    const int grid = std::min(sp_tiles(std::min(bound, max_n)), 2 * num_sms());
+    k_scan_1p<<<grid, SP_BT, 0, s>>>(in, out, d_lo, d_hi, std::min(bound, max_n), extra_dst, extra_base, ctr, look,
+                                     status);
+}
+
 int num_sms()
 {
     static int sms = 0;
@@ -1111,10 +1215,8 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     if (C > 1) ALLOC(cloud_of, uint16_t, n);
     k_keys<<<cg, BT, 0, s>>>(pos, t->d_off, t->d_frame, k0, v0, cloud_of);
     const int nb = (n + OS_TILE - 1) / OS_TILE;
-    int *scr;
     unsigned *gcount, *gstart, *tile_ctr;
     unsigned long long *look;
-    ALLOC(scr, int, scan_scratch_bytes() / sizeof(int));
     ALLOC(gcount, unsigned, RS_MAXPASS * 256);
     ALLOC(gstart, unsigned, RS_MAXPASS * 256);
     ALLOC(tile_ctr, unsigned, RS_MAXPASS);
@@ -1179,16 +1281,20 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         ALLOC(tmp, int, cap + 1);
         ALLOC(tmpo, int, cap + 1);
         ALLOC(bnd, int, 7 * (size_t)cap);
+        char *scr = nullptr;
+        ALLOC(scr, char, scan1p_bytes(cap));
+        Scan1P sc;
+        sc.init(scr, cap, s);
         k_oct_root<<<(C + 127) / 128, 128, 0, s>>>(t->d_off, C, t->nfirst, t->ncount, t->nparent, t->nlevel,
                                                    t->ncloud, t->d_lvl);
-        t->n_launch += 1 + (SFG_LMAX + 1) * 5;
+        t->n_launch += 1 + (SFG_LMAX + 1) * 3; // roots; per level: count, scan, write
         // grid-stride over a level (its size is only known on the device)
         const int og = std::min(grid_for(cap, BT), num_sms() * 4);
         for (int level = 0; level <= SFG_LMAX; level++) {
             k_oct_count<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                           t->ncount, tmp, bnd, t->d_status);
-            scan_range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
-                       t->d_lvl + level + 1, scr, s);
+            sc.range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
+                     t->d_lvl + level + 1, t->d_status, s);
             k_oct_write<<<og, BT, 0, s>>>(bnd, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
                                                          t->ncount, t->nparent, t->nchild_first, t->nnchild,
                                                          t->nlevel, t->ncloud, tmpo, t->d_status);
@@ -1201,6 +1307,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         dev_free(t, tmp, s);
         dev_free(t, tmpo, s);
         dev_free(t, bnd, s);
+        dev_free(t, scr, s);
         if (st & ST_EINVAL) return SFG_EINVAL;
         if (!(st & ST_NODECAP)) break;
         free_nodes(t, s);
@@ -1291,7 +1398,6 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     dev_free(t, nS, s);
     dev_free(t, lhist, s);
     dev_free(t, leaves, s);
-    dev_free(t, scr, s);
     t->frames_h.resize(C);
     SFG_CUDA_OK(cudaMemcpyAsync(t->frames_h.data(), t->d_frame, sizeof(Frame) * C, cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));

@@ -132,6 +132,25 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
 size_t scan_scratch_bytes();
 void scan_exclusive(const int *in, int *out, const int *d_n, int max_n, int *extra_dst, const int *extra_base,
                     void *scratch, cudaStream_t s);
+// Single-pass form (one launch per scan) over a scratch of scan1p_bytes(max_n)
+// bytes that init() zeroes once; the scan leaves it zeroed.  range() scans
+// in[*d_lo .. *d_hi) (d_lo may be NULL: from 0) into out[0..len], out[len] =
+// total, bounded by min(bound, max_n); a look-back wait that runs out sets
+// ST_ETIMEOUT in *status.
+size_t scan1p_bytes(int max_n);
+struct Scan1P {
+    unsigned *ctr = nullptr;            // [0] tile tickets, [1] blocks done
+    unsigned long long *look = nullptr; // per tile: status (2 bits) | value (32 bits)
+    int max_n = 0;
+    void attach(void *mem, int max_n); // an already zeroed scratch
+    void init(void *mem, int max_n, cudaStream_t s);
+    void range(const int *in, int *out, const int *d_lo, const int *d_hi, int bound, int *extra_dst,
+               const int *extra_base, int *status, cudaStream_t s) const;
+    void exclusive(const int *in, int *out, const int *d_n, int bound, int *status, cudaStream_t s) const
+    {
+        range(in, out, nullptr, d_n, bound, nullptr, nullptr, status, s);
+    }
+};
 
 // ---- forward / adjoint (walk.cu) ----
 int accel(Tree *t, const int64_t *active, int64_t n_active, double *accel, double *phi, cudaStream_t s);

@@ -2510,7 +2510,8 @@ static int grid_for(int64_t n, int bt)
 
 // Per-call workspace carved from one grow-only allocation.
 struct Work {
-    int *flag, *pre, *tgt, *gflag, *gcnt, *goff, *ovf, *scr;
+    int *flag, *pre, *tgt, *gflag, *gcnt, *goff, *ovf;
+    Scan1P sc;
     int2 *gtab, *gstack;
     float4 *res_a;
     double *res_phi;
@@ -2537,14 +2538,16 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     const size_t n = (size_t)t->n;
     const int retry_warps = num_sms() * WALK_WARPS;
     const size_t NB = 24;
-    size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, (n + PSLOTS) * 4, scan_scratch_bytes(),
+    size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, (n + PSLOTS) * 4, scan1p_bytes((int)n),
                      n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8,
                      n * 4 * NCNT, n * 4, n * 4, (n + 1) * 4, (n + 1) * 4, n * 4,
                      (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8, 64 * 4, (n + PSLOTS) * 8,
                      (n + 1) * 8, (n + 1) * 8};
     size_t total = 0;
     for (size_t b : sz) total += align_up(b);
+    bool fresh = false;
     if (t->ws_bytes < total) {
+        fresh = true;
         t->lists_ok = false; // the list sizes lived in the old workspace
         if (t->ws) dev_free(t, t->ws, s);
         t->ws = dev_alloc(t, total, s);
@@ -2567,7 +2570,8 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     w.gcnt = (int *)ptr[4];
     w.goff = (int *)ptr[5];
     w.ovf = (int *)ptr[6];
-    w.scr = (int *)ptr[7];
+    w.sc.attach(ptr[7], (int)n);
+    if (fresh) SFG_CUDA_OK(cudaMemsetAsync(ptr[7], 0, scan1p_bytes((int)n), s)); // zero between scans from here on
     w.gtab = (int2 *)ptr[8];
     w.gstack = (int2 *)ptr[9];
     w.res_a = (float4 *)ptr[10];
@@ -2595,13 +2599,13 @@ static int form_groups(Tree *t, const int64_t *active, int64_t n_active, Work &w
     const int n = (int)t->n, BT = 256;
     SFG_CUDA_OK(cudaMemsetAsync(w.flag, 0, sizeof(int) * (size_t)n, s));
     SFG_CUDA_OK(cudaMemsetAsync(w.gflag, 0, sizeof(int) * (size_t)n, s));
-    t->n_launch += 1 + 3 + 1 + 1 + 3 + 1; // mark, scan, compact, marks, scan, table
+    t->n_launch += 6; // mark, scan, compact, marks, scan, table
     k_mark<<<grid_for(n_active, BT), BT, 0, s>>>(active, n_active, n, t->rank, w.flag, t->d_status);
-    scan_exclusive(w.flag, w.pre, t->d_n, n, nullptr, nullptr, w.scr, s);
+    w.sc.exclusive(w.flag, w.pre, t->d_n, n, t->d_status, s);
     k_compact<<<grid_for(n, BT), BT, 0, s>>>(w.flag, w.pre, n, w.tgt);
     k_group_marks<<<grid_for(t->nn, BT), BT, 0, s>>>(t->nfirst, t->ncount, t->nchild_first, t->nnchild, t->nn,
                                                      t->nclouds, w.pre, t->prm.group_size, w.gflag, w.gcnt);
-    scan_exclusive(w.gflag, w.goff, w.pre + n, n, nullptr, nullptr, w.scr, s);
+    w.sc.exclusive(w.gflag, w.goff, w.pre + n, n, t->d_status, s);
     k_group_table<<<grid_for(n, BT), BT, 0, s>>>(w.gflag, w.gcnt, w.goff, w.pre + n, w.gtab);
     *d_ngroups = nullptr;
     return SFG_OK;
@@ -2777,15 +2781,15 @@ static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s, i
     k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total);
     const long long warps = (long long)num_sms() * WALK_MINB * WALK_WARPS;
     k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total, warps, w.kcnt, w.is_split);
-    scan_exclusive(w.is_split, w.soff, d_ng, n, nullptr, nullptr, w.scr, s);
+    w.sc.exclusive(w.is_split, w.soff, d_ng, n, t->d_status, s);
     k_item_cap<<<grid_for(n, BT), BT, 0, s>>>(w.soff, d_ng, w.kcnt);
-    scan_exclusive(w.kcnt, w.ioff, d_ng, n, nullptr, nullptr, w.scr, s);
+    w.sc.exclusive(w.kcnt, w.ioff, d_ng, n, t->d_status, s);
     cudaMemsetAsync(w.gdone, 0, sizeof(int) * (size_t)n, s);
     cudaMemsetAsync(w.hist, 0, 32 * sizeof(int), s);
     k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, wt, w.hist);
     k_item_scan<<<1, 32, 0, s>>>(w.hist);
     k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, wt, w.hist, w.items);
-    t->n_launch += 1 + 3 + 3 + 3;
+    t->n_launch += 8; // total, counts, scan, cap, scan, hist, bin scan, fill
 }
 
 static void make_items(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
