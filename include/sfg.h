@@ -98,6 +98,9 @@ typedef struct sfg_stats {
     float vjp_walk_ms;    /* its adjoint evaluation launch, likewise */
     int64_t n_p2p_newton; /* of n_p2p: pairs from stored Newtonian range lists (opened leaves wholly
                              outside both softening supports; 0 without stored lists) */
+    int32_t list_walks;   /* walks the last stored-list build took: 1 = one pass (lists staged and
+                             placed as walked), 2 = sizes first, then the lists (the first build
+                             of the process, or one whose lists outgrew the sizing hint) */
 } sfg_stats;
 
 /* Fill *p with the defaults: G = 1, theta = 0.5, leaf_size = 16, group_size = 32,

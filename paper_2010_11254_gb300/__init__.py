@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("n_p2m", ctypes.c_int64), ("n_overflow", ctypes.c_int64), ("n_clouds", ctypes.c_int32),
                 ("n_launches", ctypes.c_int64),
                 ("build_ms", ctypes.c_float), ("fwd_ms", ctypes.c_float), ("fwd_walk_ms", ctypes.c_float),
-                ("vjp_ms", ctypes.c_float), ("vjp_walk_ms", ctypes.c_float), ("n_p2p_newton", ctypes.c_int64)]
+                ("vjp_ms", ctypes.c_float), ("vjp_walk_ms", ctypes.c_float), ("n_p2p_newton", ctypes.c_int64),
+                ("list_walks", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -256,6 +256,7 @@ int sfg_get_stats(sfg_tree *tree, sfg_stats *out)
     s.n_groups = (int64_t)(*(int *)&c[5]);
     s.n_targets = (int64_t)c[6];
     s.n_launches = t->n_launch;
+    s.list_walks = t->list_walks;
     float *ms[5] = {&s.build_ms, &s.fwd_ms, &s.fwd_walk_ms, &s.vjp_ms, &s.vjp_walk_ms};
     for (int ph = 0; ph < 5; ph++) {
         *ms[ph] = 0.f;

@@ -114,6 +114,10 @@ struct Tree {
     bool rel_on = false;
     int *d_flag = nullptr;       // device scratch word
     long long *d_lscan = nullptr; // list-offset scan scratch + totals
+    unsigned long long *d_lbump = nullptr; // one-pass list walk: reservations and flags
+    void *lstage = nullptr;                // one-pass list walk: per-warp staging
+    size_t lstage_bytes = 0;
+    int list_walks = 0;                    // walks of the last stored-list build (1 or 2)
     std::unordered_set<void *> live; // every device allocation still held
 };
 

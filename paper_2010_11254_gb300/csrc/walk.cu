@@ -28,6 +28,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "sfg_internal.cuh"
 
 namespace sfg {
@@ -40,7 +43,8 @@ constexpr int GSTK = 4096;     // spill stack capacity per warp of the retry lau
 constexpr int MODE_EVAL = 0, MODE_COUNT = 1, MODE_DUMP = 2, MODE_VJP = 3, MODE_EVAL64 = 4, MODE_LIST = 5,
               MODE_TIDAL = 6, // forward evaluation plus the tidal tensor (stored lists only)
               MODE_JERK = 7,  // forward evaluation plus the jerk (stored lists only)
-              MODE_TSTEP = 8; // sink two-body timestep minima only (stored lists only)
+              MODE_TSTEP = 8, // sink two-body timestep minima only (stored lists only)
+              MODE_LIST1 = 9; // one-pass list walk: lists staged per warp, then copied to reserved space
 // list sizes per group written by the counting walk: P2M nodes, softened P2P
 // ranges and particles, Newtonian P2P ranges and particles
 constexpr int NCNT = 5;
@@ -91,6 +95,21 @@ struct WalkParams {
     // relative opening criterion (off when gps == NULL): |g_prev| per sorted rank, alpha, G
     const double *gps;
     double ralpha, rG;
+    // one-pass list walk: per-warp staging (stg_cap_m P2M ids; stg_cap_r
+    // softened, then stg_cap_r Newtonian ranges), the warps of the main
+    // launch (the retry launch's warps follow them), the final buffers'
+    // capacities, and the reservations: [0] P2M entries [1] ranges [2] 1 if
+    // the final buffers were short [3] groups whose lists outgrew the
+    // staging (listed in rlist; their space is reserved, a list-writing
+    // walk of just those groups fills it) [4] [5] the largest P2M list and
+    // range list (softened or Newtonian) of a group
+    int *rlist;
+    int *stg_m;
+    int2 *stg_r;
+    int stg_cap_m, stg_cap_r, stg_main_warps;
+    long long lcap_m, lcap_r;
+    unsigned long long *lbump;
+    long long *lmo_w, *lro_w; // where each group's lists were placed (the lmo / lro arrays)
     unsigned long long *counters; // [0] p2p [1] p2m [2] overflowed groups [3] work [4] retry work
     int *ovf_list;
     int *status;
@@ -757,6 +776,8 @@ struct WalkState {
     double dax, day, daz;
     float c0, c1, c2, cf;
     long long off_m, off_p;
+    int *sm;      // one-pass list walk: this warp's staging
+    int2 *ss, *sn;
 };
 
 // Append accepted nodes (acc) and P2P ranges (lf) of this round to the lists.
@@ -770,7 +791,7 @@ __device__ __forceinline__ void append_lists(const WalkParams &P, WarpSmem &S, W
     W.tot_m += __popc(ba);
     W.tot_leaf += __popc(bl);
     W.tot_p += lc;
-    if (MODE == MODE_COUNT || MODE == MODE_LIST) {
+    if (MODE == MODE_COUNT || MODE == MODE_LIST || MODE == MODE_LIST1) {
         unsigned bn = __ballot_sync(FULL, nw);
         W.tot_ln += __popc(bn);
         W.tot_pn += __reduce_add_sync(FULL, nw ? cnt : 0);
@@ -781,6 +802,17 @@ __device__ __forceinline__ void append_lists(const WalkParams &P, WarpSmem &S, W
             if (acc && im < W.lim_m) P.lm[im] = node;
             if (lf && !nw && is < W.lim_s) P.lr[is] = make_int2(link, cnt);
             if (nw && in < W.lim_n) P.lr[in] = make_int2(link, cnt);
+            W.off_m += __popc(ba);
+            W.off_s += __popc(bs);
+            W.off_n += __popc(bn);
+        }
+        if (MODE == MODE_LIST1) {
+            // staged; what does not fit is counted only
+            unsigned bs = bl & ~bn;
+            long long im = W.off_m + __popc(ba & lt), is = W.off_s + __popc(bs & lt), in = W.off_n + __popc(bn & lt);
+            if (acc && im < W.lim_m) W.sm[im] = node;
+            if (lf && !nw && is < W.lim_s) W.ss[is] = make_int2(link, cnt);
+            if (nw && in < W.lim_n) W.sn[in] = make_int2(link, cnt);
             W.off_m += __popc(ba);
             W.off_s += __popc(bs);
             W.off_n += __popc(bn);
@@ -826,7 +858,7 @@ template <bool QUAD, int MODE>
 __device__ __forceinline__ void flush_tiles(const WalkParams &P, WarpSmem &S, WalkState &W, const Tgt &T, int lane,
                                             bool final, int kk, int K)
 {
-    if (MODE == MODE_COUNT || MODE == MODE_DUMP || MODE == MODE_LIST) return;
+    if (MODE == MODE_COUNT || MODE == MODE_DUMP || MODE == MODE_LIST || MODE == MODE_LIST1) return;
     const int lim = final ? 1 : 32;
     while (MODE == MODE_EVAL64 && W.nm >= lim) {
         int c = min(W.nm, 32);
@@ -884,15 +916,15 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 template <bool QUAD, int MODE, bool GSTACK>
 __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item,
-                                int lane, int &cloud_out);
+                                int lane, int wid, int &cloud_out);
 
 // One work item, plus the per-cloud completion time when timing is on.
 template <bool QUAD, int MODE, bool GSTACK>
 __device__ __forceinline__ void walk_group(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K,
-                                           int item, int lane)
+                                           int item, int lane, int wid)
 {
     int cloud = 0;
-    walk_group_body<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane, cloud);
+    walk_group_body<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane, wid, cloud);
     if (P.ctime && lane == 0) atomicMax(&P.ctime[cloud], global_ns());
 }
 
@@ -1035,9 +1067,52 @@ __device__ __forceinline__ void finish_targets(const WalkParams &P, const Tgt &T
     }
 }
 
+// One-pass list walk, end of a group: its list sizes, space reserved in the
+// final buffers (every group adds its exact sizes, so the totals size a
+// second attempt), and the staged lists copied there if they were staged
+// whole and the space is inside the buffers.
+__device__ void commit_staged(const WalkParams &P, const WalkState &W, int g, int lane)
+{
+    const int ns = W.tot_leaf - W.tot_ln, nn = W.tot_ln;
+    long long bm = 0, br = 0;
+    int ok = 0;
+    if (lane == 0) {
+        int *c = P.dbg_counts + NCNT * (size_t)g;
+        c[0] = W.tot_m;
+        c[1] = ns;
+        c[2] = W.tot_p - W.tot_pn;
+        c[3] = nn;
+        c[4] = W.tot_pn;
+        bm = (long long)atomicAdd(&P.lbump[0], (unsigned long long)W.tot_m);
+        br = (long long)atomicAdd(&P.lbump[1], (unsigned long long)W.tot_leaf);
+        atomicMax(&P.lbump[4], (unsigned long long)W.tot_m);
+        atomicMax(&P.lbump[5], (unsigned long long)max(ns, nn));
+        const bool staged = W.tot_m <= P.stg_cap_m && ns <= P.stg_cap_r && nn <= P.stg_cap_r;
+        const bool room = bm + W.tot_m <= P.lcap_m && br + W.tot_leaf <= P.lcap_r;
+        ok = staged && room;
+        if (room) {
+            P.lmo_w[g] = bm;
+            P.lro_w[g] = br;
+            if (!staged) P.rlist[atomicAdd(&P.lbump[3], 1ull)] = g;
+        } else {
+            atomicOr(&P.lbump[2], 1ull);
+        }
+    }
+    ok = __shfl_sync(FULL, ok, 0);
+    __syncwarp(); // the lanes' staging writes are visible to the copy
+    if (ok) {
+        bm = __shfl_sync(FULL, bm, 0);
+        br = __shfl_sync(FULL, br, 0);
+        for (int i = lane; i < W.tot_m; i += 32) P.lm[bm + i] = W.sm[i];
+        for (int i = lane; i < ns; i += 32) P.lr[br + i] = W.ss[i];
+        for (int i = lane; i < nn; i += 32) P.lr[br + ns + i] = W.sn[i];
+    }
+    __syncwarp(); // the copy has read the staging before the next group writes it
+}
+
 template <bool QUAD, int MODE, bool GSTACK>
 __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, int g, int kk, int K, int item,
-                                int lane, int &cloud_out)
+                                int lane, int wid, int &cloud_out)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int cap = GSTACK ? GSTK : STK;
@@ -1075,6 +1150,13 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
         W.lim_m = W.off_m + c[0];
         W.lim_s = W.off_n;
         W.lim_n = W.off_n + c[3];
+    }
+    if (MODE == MODE_LIST1) {
+        W.sm = P.stg_m + (size_t)wid * P.stg_cap_m;
+        W.ss = P.stg_r + (size_t)wid * 2 * P.stg_cap_r;
+        W.sn = W.ss + P.stg_cap_r;
+        W.lim_m = P.stg_cap_m;
+        W.lim_s = W.lim_n = P.stg_cap_r;
     }
 
     if (lane == 0) stack[0] = make_int2(cloud, 1);
@@ -1135,6 +1217,10 @@ __device__ void walk_group_body(const WalkParams &P, WarpSmem &S, int2 *stack, i
             c[3] = W.tot_ln;
             c[4] = W.tot_pn;
         }
+        return;
+    }
+    if (MODE == MODE_LIST1) {
+        commit_staged(P, W, g, lane);
         return;
     }
     if (MODE == MODE_DUMP || MODE == MODE_LIST) return;
@@ -2251,8 +2337,10 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams 
     WarpSmem &S = sm[w];
     int2 *stack = GSTACK ? P.gstack + (size_t)(blockIdx.x * WALK_WARPS + w) * GSTK : S.stack;
     constexpr bool ITEMS = MODE == MODE_EVAL || MODE == MODE_VJP || MODE == MODE_EVAL64;
+    // a list-writing walk over the listed groups only (those a one-pass walk could not stage)
+    const bool RLIST = MODE == MODE_LIST && P.rlist != nullptr;
     const int ngroups = *P.d_ngroups;
-    const int nwork = GSTACK ? (int)P.counters[2] : (ITEMS ? P.ioff[ngroups] : ngroups);
+    const int nwork = GSTACK ? (int)P.counters[2] : (ITEMS ? P.ioff[ngroups] : (RLIST ? (int)P.lbump[3] : ngroups));
     if (P.ctime && lane == 0 && !GSTACK) atomicMin(&P.ctime[P.nclouds], global_ns());
     while (true) {
         int w_i = 0;
@@ -2260,14 +2348,15 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams 
         w_i = __shfl_sync(FULL, w_i, 0);
         if (w_i >= nwork) break;
         int item = GSTACK ? P.ovf_list[w_i] : w_i;
-        int g = item, kk = 0, K = 1;
+        int g = RLIST ? P.rlist[item] : item, kk = 0, K = 1;
         if (ITEMS) {
             int2 it = P.items[item];
             g = it.x;
             kk = it.y;
             K = P.kcnt[g];
         }
-        walk_group<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane);
+        walk_group<QUAD, MODE, GSTACK>(P, S, stack, g, kk, K, item, lane,
+                                       (GSTACK ? P.stg_main_warps : 0) + blockIdx.x * WALK_WARPS + w);
     }
 }
 
@@ -2675,6 +2764,13 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.lro = w.lro;
     P.lm = t->lm;
     P.lr = t->lr;
+    P.stg_m = nullptr;
+    P.stg_r = nullptr;
+    P.stg_cap_m = P.stg_cap_r = P.stg_main_warps = 0;
+    P.lcap_m = P.lcap_r = 0;
+    P.lbump = nullptr;
+    P.lmo_w = P.lro_w = nullptr;
+    P.rlist = nullptr;
 }
 
 template <int MODE>
@@ -2683,7 +2779,8 @@ static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
     t->n_launch += 2;
     // the list-only walks (no evaluation, fewer registers) are latency-bound:
     // two more resident blocks per SM keep more groups in flight
-    const int blocks = num_sms() * (MODE == MODE_COUNT || MODE == MODE_LIST ? WALK_MINB + 2 : WALK_MINB);
+    const int blocks =
+        num_sms() * (MODE == MODE_COUNT || MODE == MODE_LIST || MODE == MODE_LIST1 ? WALK_MINB + 2 : WALK_MINB);
     const int retry_blocks = num_sms();
     if (t->prm.quadrupole) {
         k_walk<true, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
@@ -2819,17 +2916,112 @@ static int grow_buffer(Tree *t, void **buf, long long *cap, long long need, size
     return SFG_OK;
 }
 
-// Walk every group twice: count its lists, then write them (P2M node ids,
-// softened and Newtonian P2P ranges) into the tree's grow-only buffers,
-// sized from the counts after one synchronization.
-static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+// Process-wide sizing hints of the one-pass list walk: list entries per
+// active row in the last lists built (the final buffers are sized from them,
+// with a margin) and the per-warp staging capacities (the largest lists of
+// a group in the last one-pass walk, with a margin, within bounds).
+struct ListHint {
+    double m_per = 0.0, r_per = 0.0;
+    int stg_m = 4096, stg_r = 1024;
+};
+static std::mutex g_hint_mu;
+static ListHint g_hint;
+constexpr int STG_MIN_M = 1024, STG_MIN_R = 256, STG_MAX_M = 1 << 16, STG_MAX_R = 1 << 14;
+
+static void update_hint(long long tot_m, long long tot_r, int64_t n_active, long long max_m, long long max_r)
+{
+    std::lock_guard<std::mutex> lk(g_hint_mu);
+    const double na = (double)std::max<int64_t>(n_active, 1);
+    g_hint.m_per = (double)tot_m / na;
+    g_hint.r_per = (double)tot_r / na;
+    if (max_m >= 0) {
+        g_hint.stg_m = (int)std::min<long long>(std::max<long long>(max_m + max_m / 4 + 32, STG_MIN_M), STG_MAX_M);
+        g_hint.stg_r = (int)std::min<long long>(std::max<long long>(max_r + max_r / 4 + 32, STG_MIN_R), STG_MAX_R);
+    }
+}
+
+// Lists of every group (P2M node ids, softened and Newtonian P2P ranges) in
+// the tree's grow-only buffers.  One walk stages each group's lists per warp
+// and copies them to space it reserves; one synchronization then reads the
+// reservations.  Groups whose lists outgrew the staging have their space
+// reserved all the same, and a list-writing walk of just those groups fills
+// it (the next call's staging fits this call's largest lists).  If
+// the buffers, sized from the hint, were short, the walk's exact sizes
+// place every group's lists contiguously and a second walk writes them.
+// Without a hint (the first lists of the process) a counting walk gives the
+// sizes instead of the one-pass walk.
+static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t n_active)
 {
     t->lists_ok = false;
-    count_lists(t, w, P, s);
+    ListHint h;
+    {
+        std::lock_guard<std::mutex> lk(g_hint_mu);
+        h = g_hint;
+    }
     if (!t->d_lscan) {
         t->d_lscan = (long long *)dev_alloc(t, sizeof(long long) * (2 * LS_NB + 2), s);
         if (!t->d_lscan) return SFG_ENOMEM;
     }
+    if (!t->d_lbump) {
+        t->d_lbump = (unsigned long long *)dev_alloc(t, 6 * sizeof(unsigned long long), s);
+        if (!t->d_lbump) return SFG_ENOMEM;
+    }
+    const double na = (double)std::max<int64_t>(n_active, 1);
+    bool counted = false;
+    if (h.m_per > 0.0) {
+        const int main_warps = num_sms() * (WALK_MINB + 2) * WALK_WARPS;
+        const int warps = main_warps + num_sms() * WALK_WARPS;
+        const size_t stg_m_bytes = align_up((size_t)warps * h.stg_m * sizeof(int));
+        const size_t stg_r_bytes = align_up((size_t)warps * 2 * h.stg_r * sizeof(int2));
+        const size_t stg_bytes = stg_m_bytes + stg_r_bytes + sizeof(int) * (size_t)t->n;
+        if (t->lstage_bytes < stg_bytes) {
+            if (t->lstage) dev_free(t, t->lstage, s);
+            t->lstage = dev_alloc(t, stg_bytes, s);
+            t->lstage_bytes = t->lstage ? stg_bytes : 0;
+            if (!t->lstage) return SFG_ENOMEM;
+        }
+        int rc = grow_buffer(t, (void **)&t->lm, &t->lm_cap, (long long)(h.m_per * na * 1.15) + 4096, sizeof(int), s);
+        if (rc) return rc;
+        rc = grow_buffer(t, (void **)&t->lr, &t->lr_cap, (long long)(h.r_per * na * 1.15) + 1024, sizeof(int2), s);
+        if (rc) return rc;
+        P.lm = t->lm;
+        P.lr = t->lr;
+        P.lcap_m = t->lm_cap;
+        P.lcap_r = t->lr_cap;
+        P.stg_m = (int *)t->lstage;
+        P.stg_r = (int2 *)((char *)t->lstage + stg_m_bytes);
+        P.rlist = (int *)((char *)t->lstage + stg_m_bytes + stg_r_bytes);
+        P.stg_cap_m = h.stg_m;
+        P.stg_cap_r = h.stg_r;
+        P.stg_main_warps = main_warps;
+        P.lbump = t->d_lbump;
+        P.lmo_w = w.lmo;
+        P.lro_w = w.lro;
+        SFG_CUDA_OK(cudaMemsetAsync(t->d_lbump, 0, 6 * sizeof(unsigned long long), s));
+        SFG_CUDA_OK(cudaMemsetAsync(w.cnt, 0, sizeof(int) * NCNT * (size_t)t->n, s));
+        SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
+        P.dbg_counts = w.cnt;
+        launch_walk<MODE_LIST1>(t, P, s);
+        P.dbg_counts = nullptr;
+        unsigned long long b[6] = {0, 0, 0, 0, 0, 0};
+        SFG_CUDA_OK(cudaMemcpyAsync(b, t->d_lbump, sizeof(b), cudaMemcpyDeviceToHost, s));
+        SFG_CUDA_OK(cudaStreamSynchronize(s));
+        update_hint((long long)b[0], (long long)b[1], n_active, (long long)b[4], (long long)b[5]);
+        if (b[2] == 0) {
+            if (b[3] > 0) {
+                // the groups that outgrew the staging, into their reserved space
+                SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
+                launch_walk<MODE_LIST>(t, P, s);
+            }
+            P.rlist = nullptr;
+            t->list_walks = 1;
+            SFG_CUDA_OK(cudaGetLastError());
+            return SFG_OK;
+        }
+        P.rlist = nullptr;
+        counted = true; // the sizes in w.cnt are exact
+    }
+    if (!counted) count_lists(t, w, P, s);
     long long *tot_d = t->d_lscan + 2 * LS_NB;
     k_lscan_reduce<<<LS_NB, 256, 0, s>>>(w.cnt, P.d_ngroups, t->d_lscan);
     k_lscan_top<<<1, 32, 0, s>>>(t->d_lscan, P.d_ngroups, w.lmo, w.lro, tot_d);
@@ -2838,6 +3030,7 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
     long long tot[2] = {0, 0};
     SFG_CUDA_OK(cudaMemcpyAsync(tot, tot_d, sizeof(tot), cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
+    if (!counted) update_hint(tot[0], tot[1], n_active, -1, -1);
     int rc = grow_buffer(t, (void **)&t->lm, &t->lm_cap, tot[0], sizeof(int), s);
     if (rc) return rc;
     rc = grow_buffer(t, (void **)&t->lr, &t->lr_cap, tot[1], sizeof(int2), s);
@@ -2846,6 +3039,7 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
     P.lr = t->lr;
     SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
     launch_walk<MODE_LIST>(t, P, s);
+    t->list_walks = 2;
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
 }
@@ -2920,7 +3114,7 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
     }
     const bool lists = !f64 && use_lists(t, s);
     if (lists) {
-        rc = build_lists(t, w, P, s);
+        rc = build_lists(t, w, P, s, n_active);
         if (rc) return rc;
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
@@ -2992,7 +3186,7 @@ int accel_tidal(Tree *t, const int64_t *active, int64_t n_active, double *acc, d
     rc = lists_match(t, active, n_active, s, match);
     if (rc) return rc;
     if (!match) {
-        rc = build_lists(t, w, P, s);
+        rc = build_lists(t, w, P, s, n_active);
         if (rc) return rc;
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
@@ -3106,7 +3300,7 @@ static int prepare_vel(Tree *t, const double *vel, const int64_t *active, int64_
     rc = lists_match(t, active, n_active, s, match);
     if (rc) return rc;
     if (!match) {
-        rc = build_lists(t, w, P, s);
+        rc = build_lists(t, w, P, s, n_active);
         if (rc) return rc;
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
@@ -3414,7 +3608,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         P.gnode = gnode;
         if (lists) {
             if (!match) {
-                rc = build_lists(t, w, P, s);
+                rc = build_lists(t, w, P, s, n_active);
                 if (rc) return rc;
                 rc = remember_active(t, active, n_active, s);
                 if (rc) return rc;
