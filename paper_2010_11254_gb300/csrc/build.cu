@@ -842,6 +842,7 @@ struct MomArgs {
     double *nS; // [nn][6] second moment about the centre of mass (scratch of the reduction)
     float4 *pw;
     int4 *pc;
+    int32_t *pleaf;
     const int *leaves;
     int nn;
 };
@@ -977,6 +978,7 @@ __device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
         if (A.sink[k]) hs = -hs;
         A.pw[k] = make_float4(f32_rn(d[0]), f32_rn(d[1]), f32_rn(d[2]), f32_rn(m));
         A.pc[k] = make_int4(ci[0], ci[1], ci[2], __float_as_int(hs));
+        A.pleaf[k] = node;
     }
     double com[3], Q[6];
     moments_finish(M, s, S, cen, com, Q);
@@ -1257,6 +1259,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->sink_s, uint8_t, n);
     ALLOC(t->pw, float4, n);
     ALLOC(t->pc, int4, n);
+    ALLOC(t->pleaf, int32_t, n);
     if (C > 1) ALLOC(t->pcloud, int32_t, n);
     k_pack<<<grid_for(n, BT), BT, 0, s>>>(pos, mass, soft, is_sink, n, v0, t->order, t->rank, t->pos_s, t->mass_s,
                                           t->soft_s, t->sink_s, cloud_of, t->pcloud);
@@ -1375,6 +1378,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.nS = nS;
     A.pw = t->pw;
     A.pc = t->pc;
+    A.pleaf = t->pleaf;
     A.leaves = leaves;
     A.nn = nn;
     k_leaf_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);

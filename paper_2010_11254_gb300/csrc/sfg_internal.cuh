@@ -75,6 +75,7 @@ struct Tree {
     uint8_t *sink_s = nullptr;
     float4 *pw = nullptr;
     int4 *pc = nullptr;
+    int32_t *pleaf = nullptr; // sorted rank -> its leaf
     // nodes
     int32_t *nfirst = nullptr, *ncount = nullptr, *nparent = nullptr, *nchild_first = nullptr,
             *nnchild = nullptr, *nlevel = nullptr;

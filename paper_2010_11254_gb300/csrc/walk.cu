@@ -3516,34 +3516,75 @@ __global__ void __launch_bounds__(256)
 // stored FP32 offsets of member and centre of mass against the leaf centre)
 // and added to the FP64 particle gradients; the node gradients stay FP64
 // and gM enters in FP64.
-__global__ void k_gleaf(const double *gnode, const float4 *E0, const float4 *pw, const int32_t *nfirst,
-                        const int32_t *ncount, const int32_t *nnchild, int nn, double *gpart)
+// The leaves' node gradients in FP32 for the members' pass: (v, tr S), S[0..3],
+// (S[4], S[5], g_M as two words): 48 B per leaf.
+__global__ void k_gleaf_prep(const double *gnode, const int32_t *nnchild, int nn, float4 *gl)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
         if (nnchild[i] != 0) continue;
         const double *g = gnode + 10 * (size_t)i;
-        const double g0 = g[0];
-        const float v0 = (float)g[1], v1 = (float)g[2], v2 = (float)g[3];
-        const float S0 = (float)g[4], S1 = (float)g[5], S2 = (float)g[6], S3 = (float)g[7], S4 = (float)g[8],
-                    S5 = (float)g[9];
-        const float tr = S0 + S1 + S2;
-        const float4 c = E0[i];
-        for (int k = nfirst[i]; k < nfirst[i] + ncount[i]; k++) {
-            const float4 x = pw[k];
-            const float s0 = x.x - c.x, s1 = x.y - c.y, s2 = x.z - c.z;
-            const float Ss0 = fmaf(S0, s0, fmaf(S3, s1, S4 * s2));
-            const float Ss1 = fmaf(S3, s0, fmaf(S1, s1, S5 * s2));
-            const float Ss2 = fmaf(S4, s0, fmaf(S5, s1, S2 * s2));
-            const float ss = fmaf(s0, s0, fmaf(s1, s1, s2 * s2));
-            const float sSs = fmaf(s0, Ss0, fmaf(s1, Ss1, s2 * Ss2));
-            const float tm = fmaf(v0, s0, fmaf(v1, s1, fmaf(v2, s2, fmaf(3.f, sSs, -ss * tr))));
-            const float m = x.w;
-            double *o = gpart + 4 * (size_t)k;
-            o[3] += g0 + (double)tm;
-            o[0] += (double)(m * fmaf(6.f, Ss0, fmaf(-2.f * tr, s0, v0)));
-            o[1] += (double)(m * fmaf(6.f, Ss1, fmaf(-2.f * tr, s1, v1)));
-            o[2] += (double)(m * fmaf(6.f, Ss2, fmaf(-2.f * tr, s2, v2)));
+        const float S0 = (float)g[4], S1 = (float)g[5], S2 = (float)g[6];
+        const long long gm = __double_as_longlong(g[0]);
+        gl[3 * (size_t)i] = make_float4((float)g[1], (float)g[2], (float)g[3], S0 + S1 + S2);
+        gl[3 * (size_t)i + 1] = make_float4(S0, S1, S2, (float)g[7]);
+        gl[3 * (size_t)i + 2] =
+            make_float4((float)g[8], (float)g[9], __int_as_float((int)gm), __int_as_float((int)(gm >> 32)));
+    }
+}
+
+// Exact FP32 -> FP64 conversion of a normal or zero float (every result of
+// the flush-to-zero FP32 arithmetic here), on the integer pipes; infinities
+// and NaN take the hardware conversion.
+__device__ __forceinline__ double f64_of(float x)
+{
+    const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu;
+    if (e == 255u) return (double)x;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// Per particle (sorted rank k): its leaf's centre-of-mass and quadrupole
+// gradient terms added to its pair gradients, times G, written in input
+// order.  With s = x - com (member offset from the leaf's centre of mass):
+// d/dx += m (v + 6 S s - 2 tr(S) s), d/dm += g_M + v.s + 3 s.S s - tr(S) s.s.
+__global__ void k_gleaf_out(const float4 *gl, const float4 *E0, const float4 *pw, const int32_t *pleaf,
+                            const double *gpart, const int32_t *order, int n, double G, double *d_pos, double *d_mass)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = pleaf[k];
+        const float4 a = gl[3 * (size_t)i], b = gl[3 * (size_t)i + 1], c = gl[3 * (size_t)i + 2];
+        const float v0 = a.x, v1 = a.y, v2 = a.z, tr = a.w;
+        const float S0 = b.x, S1 = b.y, S2 = b.z, S3 = b.w, S4 = c.x, S5 = c.y;
+        const double g0 = __longlong_as_double(((long long)__float_as_int(c.w) << 32) |
+                                               (long long)(unsigned)__float_as_int(c.z));
+        const float4 e = E0[i], x = pw[k];
+        const float s0 = x.x - e.x, s1 = x.y - e.y, s2 = x.z - e.z;
+        const float Ss0 = fmaf(S0, s0, fmaf(S3, s1, S4 * s2));
+        const float Ss1 = fmaf(S3, s0, fmaf(S1, s1, S5 * s2));
+        const float Ss2 = fmaf(S4, s0, fmaf(S5, s1, S2 * s2));
+        const float ss = fmaf(s0, s0, fmaf(s1, s1, s2 * s2));
+        const float sSs = fmaf(s0, Ss0, fmaf(s1, Ss1, s2 * Ss2));
+        const float tm = fmaf(v0, s0, fmaf(v1, s1, fmaf(v2, s2, fmaf(3.f, sSs, -ss * tr))));
+        const float m = x.w;
+        const double2 p01 = *reinterpret_cast<const double2 *>(gpart + 4 * (size_t)k);
+        const double2 p23 = *reinterpret_cast<const double2 *>(gpart + 4 * (size_t)k + 2);
+        double o0 = p01.x + f64_of(m * fmaf(6.f, Ss0, fmaf(-2.f * tr, s0, v0)));
+        double o1 = p01.y + f64_of(m * fmaf(6.f, Ss1, fmaf(-2.f * tr, s1, v1)));
+        double o2 = p23.x + f64_of(m * fmaf(6.f, Ss2, fmaf(-2.f * tr, s2, v2)));
+        double o3 = p23.y + (g0 + f64_of(tm));
+        if (G != 1.0) {
+            o0 *= G;
+            o1 *= G;
+            o2 *= G;
+            o3 *= G;
         }
+        const int r = order[k];
+        d_pos[3 * (size_t)r] = o0;
+        d_pos[3 * (size_t)r + 1] = o1;
+        d_pos[3 * (size_t)r + 2] = o2;
+        d_mass[r] = o3;
     }
 }
 
@@ -3577,9 +3618,10 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
     int rc = prepare(t, active, n_active, w, P, s, match && t->lists_grp_gen == t->grp_gen);
     if (rc) return rc;
     if (!t->lists_ok) match = false; // a new workspace: the list sizes were dropped with the old one
-    // adjoint workspace: cotd [n][4] f64, cot [n] float4, gpart [n][4] f64, gnode [nn][10] f64
+    // adjoint workspace: cotd [n][4] f64, cot [n] float4, gpart [n][4] f64, gnode [nn][10] f64,
+    // gl [nn][3] float4
     size_t need = align_up(32 * (size_t)n) + align_up(16 * (size_t)n) + align_up(32 * (size_t)n) +
-                  align_up(80 * (size_t)nn);
+                  align_up(80 * (size_t)nn) + align_up(48 * (size_t)nn);
     if (t->ws2_bytes < need) {
         if (t->ws2) dev_free(t, t->ws2, s);
         t->ws2 = dev_alloc(t, need, s);
@@ -3597,6 +3639,8 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
     double *gpart = (double *)p;
     p += align_up(32 * (size_t)n);
     double *gnode = (double *)p;
+    p += align_up(80 * (size_t)nn);
+    float4 *gl = (float4 *)p;
     SFG_CUDA_OK(cudaMemsetAsync(cotd, 0, 32 * (size_t)n, s));
     SFG_CUDA_OK(cudaMemsetAsync(gpart, 0, 32 * (size_t)n, s));
     SFG_CUDA_OK(cudaMemsetAsync(gnode, 0, 80 * (size_t)nn, s));
@@ -3644,9 +3688,13 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
                 t->n_launch += 1;
             }
         }
-        k_gleaf<<<grid_for(nn, 128), 128, 0, s>>>(gnode, t->E0, t->pw, t->nfirst, t->ncount, t->nnchild, nn, gpart);
+        k_gleaf_prep<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nnchild, nn, gl);
+        k_gleaf_out<<<grid_for(n, BT), BT, 0, s>>>(gl, t->E0, t->pw, t->pleaf, gpart, t->order, n, t->prm.G, d_pos,
+                                                   d_mass);
+        t->n_launch += 1;
+    } else {
+        k_unpermute<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->order, n, t->prm.G, d_pos, d_mass);
     }
-    k_unpermute<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->order, n, t->prm.G, d_pos, d_mass);
     t->n_launch += 1;
     ph_end(t, PH_VJP, s);
     SFG_CUDA_OK(cudaGetLastError());
