@@ -54,7 +54,8 @@ FLOP_VJP_P2M_QUAD = 139
 # DRAM bytes per launch of the evaluation kernels on the default workload
 # (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture), valid only
 # for the walk source (sha256 of walk.cu) and launch shape they were taken on.
-WALK_TRAFFIC = {"sha256": None, "leaf_size": None, "group_size": None, "fwd": None, "vjp": None}
+WALK_TRAFFIC = {"sha256": "c0ae0c604df56ecd290b997760527e8f694c0bec59dc3835bb32da6d0f9563e1",
+                "leaf_size": 32, "group_size": 16, "fwd": 473442304, "vjp": 1287380480}
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576
