@@ -16,12 +16,12 @@
 //      level 21 is split into its non-empty octants (binary search of the
 //      child digit in the node's sorted key range); node ids are breadth-first;
 //   7. moments, bottom-up: leaves sum their members in sorted order (one
-//      lane per leaf, leaves taken by member count), then the internal
-//      levels, deepest first, combine their children in octant order
-//      (parallel-axis theorem; one launch per level, the small top levels
-//      in one block).  The operation order is fixed and this file is
-//      compiled without FMA contraction, so the FP64 moments are
-//      reproducible bit for bit.
+//      lane per leaf, leaves taken by member count; on large clouds from
+//      chunks staged in shared memory), then the internal levels, deepest
+//      first, combine their children in octant order (parallel-axis
+//      theorem; one launch per level, the small top levels in one block).
+//      The operation order is fixed and this file is compiled without FMA
+//      contraction, so the FP64 moments are reproducible bit for bit.
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <stdint.h>
@@ -843,7 +843,6 @@ struct MomArgs {
     float4 *pw;
     int4 *pc;
     int32_t *pleaf;
-    const int *leaves;
     int nn;
 };
 
@@ -939,7 +938,23 @@ __device__ inline void moments_finish(double M, const double s[3], double S[6], 
     Q[5] = 3.0 * S[5];
 }
 
-__device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
+// Member data of a leaf: from the chunk staged in shared memory where it
+// holds them (ranks [c0, lim)), else from global memory.
+struct LeafSrc {
+    const MomArgs &A;
+    const double *sxyz, *smass, *ssoft;
+    const uint64_t *skey;
+    const uint8_t *ssink;
+    int c0, lim;
+    __device__ bool in(int k) const { return k >= c0 && k < lim; }
+    __device__ uint64_t key(int k) const { return in(k) ? skey[k - c0] : A.key[k]; }
+    __device__ double x(int k, int a) const { return in(k) ? sxyz[3 * (k - c0) + a] : A.pos[3 * (size_t)k + a]; }
+    __device__ double mass(int k) const { return in(k) ? smass[k - c0] : A.mass[k]; }
+    __device__ double soft(int k) const { return in(k) ? ssoft[k - c0] : A.soft[k]; }
+    __device__ bool sink(int k) const { return (in(k) ? ssink[k - c0] : A.sink[k]) != 0; }
+};
+
+__device__ void leaf_moments(const MomArgs &A, const LeafSrc &D, const Frame &fr, int node)
 {
     const int f = A.nfirst[node], c = A.ncount[node], level = A.nlevel[node];
     uint32_t lo[3] = {SFG_GRID_MAX, SFG_GRID_MAX, SFG_GRID_MAX}, hi[3] = {0, 0, 0};
@@ -947,15 +962,15 @@ __device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
     double cen[3];
     {
         // every member shares the cell prefix: the first one gives the centre
-        uint64_t key = A.key[f];
+        uint64_t key = D.key(f);
         uint32_t q[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
         node_centre(fr, q, level, ci, cen);
     }
     double M = 0.0, s[3] = {0.0, 0.0, 0.0}, S[6] = {0, 0, 0, 0, 0, 0}, hmax = 0.0;
     for (int k = f; k < f + c; k++) {
-        double m = A.mass[k];
+        double m = D.mass(k);
         double d[3], md[3];
-        for (int a = 0; a < 3; a++) d[a] = A.pos[3 * (size_t)k + a] - cen[a];
+        for (int a = 0; a < 3; a++) d[a] = D.x(k, a) - cen[a];
         M = M + m;
         for (int a = 0; a < 3; a++) md[a] = m * d[a];
         for (int a = 0; a < 3; a++) s[a] = s[a] + md[a];
@@ -965,17 +980,17 @@ __device__ void leaf_moments(const MomArgs &A, const Frame &fr, int node)
         S[3] = __fma_rn(md[0], d[1], S[3]);
         S[4] = __fma_rn(md[0], d[2], S[4]);
         S[5] = __fma_rn(md[1], d[2], S[5]);
-        uint64_t key = A.key[k];
+        uint64_t key = D.key(k);
         uint32_t q[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
         for (int a = 0; a < 3; a++) {
             lo[a] = q[a] < lo[a] ? q[a] : lo[a];
             hi[a] = q[a] > hi[a] ? q[a] : hi[a];
         }
-        double h = A.soft[k];
+        double h = D.soft(k);
         hmax = max_nonneg(hmax, h);
         // particle record of the walk: FP32 offset from the leaf centre
         float hs = f32_rn(h);
-        if (A.sink[k]) hs = -hs;
+        if (D.sink(k)) hs = -hs;
         A.pw[k] = make_float4(f32_rn(d[0]), f32_rn(d[1]), f32_rn(d[2]), f32_rn(m));
         A.pc[k] = make_int4(ci[0], ci[1], ci[2], __float_as_int(hs));
         A.pleaf[k] = node;
@@ -1026,15 +1041,98 @@ __device__ void internal_moments(const MomArgs &A, const Frame &fr, int node)
     write_records(A, fr, node, level, false, cf, nc, lo, hi, M, com, Q, S, hmax, cen, ci);
 }
 
-// Leaves of every level (one thread per leaf), then internal nodes one level
-// at a time from the deepest (one thread per node; its children are final).
-// (A node's FP64 reduction runs on one lane, so the internal levels keep
-// whole warps busy only when each level is its own pass.)
-__global__ void k_leaf_moments(MomArgs A)
+// Leaves: a lane sums one leaf in member order, and a warp runs as long as
+// its largest leaf, so a warp's lanes take leaves of about the same size.
+// Below LM_STAGED_MIN particles (the particle arrays about L2-resident) one
+// launch takes every leaf from a list ordered by member count.  Above it,
+// where those scattered member reads go to DRAM, blocks take chunks of
+// LM_CH sorted ranks: the chunk's particle data (and the next LM_EXT ranks,
+// where its last leaves end) is staged in shared memory with coalesced
+// loads, and its leaves -- those starting in the chunk -- are taken largest
+// first.  Then internal nodes one level at a time from the deepest (one
+// thread per node; its children are final).
+constexpr int LM_CH = 2048, LM_EXT = 64, LM_SPAN = LM_CH + LM_EXT, LM_BT = 256, LM_BINS = 64; // 2 blocks per SM
+constexpr size_t LM_SMEM = (size_t)LM_SPAN * (3 * 8 + 8 + 8 + 8 + 1);
+constexpr int64_t LM_STAGED_MIN = 1 << 22;
+
+__global__ void k_leaf_moments(MomArgs A, const int *leaves)
 {
+    const LeafSrc D{A, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nn; i += gridDim.x * blockDim.x) {
-        int node = A.leaves[i];
-        if (node >= 0) leaf_moments(A, A.fr[A.ncloud[node]], node);
+        const int node = leaves[i];
+        if (node >= 0) leaf_moments(A, D, A.fr[A.ncloud[node]], node);
+    }
+}
+
+// lstart[rank] = the leaf whose first member is at that rank (else -1).
+__global__ void k_leaf_starts_at(const int32_t *nnchild, const int32_t *nfirst, int nn, int *lstart)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+        if (nnchild[i] == 0) lstart[nfirst[i]] = i;
+}
+
+__global__ void __launch_bounds__(LM_BT) k_leaf_moments_staged(MomArgs A, const int *lstart, int n)
+{
+    extern __shared__ __align__(16) unsigned char lm_smem[];
+    double *sxyz = (double *)lm_smem;
+    double *smass = sxyz + 3 * LM_SPAN;
+    double *ssoft = smass + LM_SPAN;
+    uint64_t *skey = (uint64_t *)(ssoft + LM_SPAN);
+    uint8_t *ssink = (uint8_t *)(skey + LM_SPAN);
+    __shared__ int slist[LM_CH];
+    __shared__ int hist[LM_BINS], nleaf;
+    for (int c0 = blockIdx.x * LM_CH; c0 < n; c0 += gridDim.x * LM_CH) {
+        const int lim = min(n, c0 + LM_SPAN);
+        const int span = lim - c0;
+        for (int q = threadIdx.x; q < 3 * span; q += LM_BT) sxyz[q] = A.pos[3 * (size_t)c0 + q];
+        for (int q = threadIdx.x; q < span; q += LM_BT) {
+            smass[q] = A.mass[c0 + q];
+            ssoft[q] = A.soft[c0 + q];
+            skey[q] = A.key[c0 + q];
+            ssink[q] = A.sink[c0 + q];
+        }
+        if (threadIdx.x < LM_BINS) hist[threadIdx.x] = 0;
+        __syncthreads();
+        // the chunk's leaves by member count (bin 0 = the largest)
+        constexpr int PER = LM_CH / LM_BT;
+        int id[PER], bin[PER];
+#pragma unroll
+        for (int r = 0; r < PER; r++) {
+            const int k = c0 + r * LM_BT + threadIdx.x;
+            id[r] = k < n ? lstart[k] : -1;
+            bin[r] = 0;
+            if (id[r] >= 0) {
+                bin[r] = LM_BINS - min(max(A.ncount[id[r]], 1), LM_BINS);
+                atomicAdd(&hist[bin[r]], 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int a = hist[lane], b = hist[lane + 32], ia = a, ib = b;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+                if (lane >= o) {
+                    ia += ta;
+                    ib += tb;
+                }
+            }
+            const int tot_a = __shfl_sync(0xffffffffu, ia, 31);
+            hist[lane] = ia - a;
+            hist[lane + 32] = tot_a + ib - b;
+            if (lane == 31) nleaf = tot_a + ib;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; r++)
+            if (id[r] >= 0) slist[atomicAdd(&hist[bin[r]], 1)] = id[r];
+        __syncthreads();
+        const LeafSrc D{A, sxyz, smass, ssoft, skey, ssink, c0, lim};
+        for (int q = threadIdx.x; q < nleaf; q += LM_BT) {
+            const int node = slist[q];
+            leaf_moments(A, D, A.fr[A.ncloud[node]], node);
+        }
+        __syncthreads();
     }
 }
 
@@ -1337,19 +1435,26 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     ALLOC(t->ncom, double, 3 * (size_t)nn);
     ALLOC(t->nQ, double, 6 * (size_t)nn);
     ALLOC(t->nhmax, double, nn);
-    int *leaves;
-    unsigned *lhist, *lcur;
+    const bool staged = n >= LM_STAGED_MIN;
+    int *lidx = nullptr; // staged: leaf starting at each rank; else the leaves by member count
+    unsigned *lhist = nullptr;
     double *nS;
     ALLOC(nS, double, 6 * (size_t)nn);
-    ALLOC(leaves, int, nn);
-    ALLOC(lhist, unsigned, 2 * LB_BINS);
-    lcur = lhist + LB_BINS;
-    SFG_CUDA_OK(cudaMemsetAsync(leaves, 0xff, sizeof(int) * (size_t)nn, s));
-    SFG_CUDA_OK(cudaMemsetAsync(lhist, 0, sizeof(unsigned) * LB_BINS, s));
-    k_leaf_hist<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->ncount, nn, lhist);
-    k_leaf_starts<<<1, 32, 0, s>>>(lhist, lcur);
-    k_leaf_scatter<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->ncount, nn, lcur, leaves);
-    t->n_launch += 3;
+    if (staged) {
+        ALLOC(lidx, int, n);
+        SFG_CUDA_OK(cudaMemsetAsync(lidx, 0xff, sizeof(int) * (size_t)n, s));
+        k_leaf_starts_at<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->nfirst, nn, lidx);
+        t->n_launch += 1;
+    } else {
+        ALLOC(lidx, int, nn);
+        ALLOC(lhist, unsigned, 2 * LB_BINS);
+        SFG_CUDA_OK(cudaMemsetAsync(lidx, 0xff, sizeof(int) * (size_t)nn, s));
+        SFG_CUDA_OK(cudaMemsetAsync(lhist, 0, sizeof(unsigned) * LB_BINS, s));
+        k_leaf_hist<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->ncount, nn, lhist);
+        k_leaf_starts<<<1, 32, 0, s>>>(lhist, lhist + LB_BINS);
+        k_leaf_scatter<<<grid_for(nn, BT), BT, 0, s>>>(t->nnchild, t->ncount, nn, lhist + LB_BINS, lidx);
+        t->n_launch += 3;
+    }
     MomArgs A;
     A.key = t->key;
     A.pos = t->pos_s;
@@ -1379,9 +1484,15 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     A.pw = t->pw;
     A.pc = t->pc;
     A.pleaf = t->pleaf;
-    A.leaves = leaves;
     A.nn = nn;
-    k_leaf_moments<<<grid_for(nn, 128), 128, 0, s>>>(A);
+    if (staged) {
+        // the staged chunk needs more than the default 48 KB of shared memory
+        SFG_CUDA_OK(cudaFuncSetAttribute(k_leaf_moments_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LM_SMEM));
+        const int chunks = (int)((n + LM_CH - 1) / LM_CH);
+        k_leaf_moments_staged<<<std::min(chunks, 2 * num_sms()), LM_BT, LM_SMEM, s>>>(A, lidx, (int)n);
+    } else {
+        k_leaf_moments<<<grid_for(nn, 128), 128, 0, s>>>(A, lidx);
+    }
     t->n_launch += 1;
     // levels 0..top hold few nodes each: one block takes them in one launch
     int top = -1;
@@ -1400,8 +1511,8 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         t->n_launch += 1;
     }
     dev_free(t, nS, s);
-    dev_free(t, lhist, s);
-    dev_free(t, leaves, s);
+    dev_free(t, lidx, s);
+    if (lhist) dev_free(t, lhist, s);
     t->frames_h.resize(C);
     SFG_CUDA_OK(cudaMemcpyAsync(t->frames_h.data(), t->d_frame, sizeof(Frame) * C, cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));

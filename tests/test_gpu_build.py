@@ -77,9 +77,19 @@ def test_build_clumpy_with_sinks():
 
 
 def test_build_sizes_spanning_tiles():
-    # sizes around the radix-sort tile (4096) and scan chunking, with a ragged tail
-    for n in [4095, 4097, 12289, 70001]:
+    # sizes around the radix-sort and scan tiles (2048) and the leaf chunks, with a ragged tail
+    for n in [2047, 2049, 4095, 4097, 12289, 70001]:
         _compare_build(gen.uniform_cloud(n, seed=n, n_sink=n % 7), 16)
+
+
+@pytest.mark.parametrize("leaf_size", [16, 100])
+def test_build_large_staged_leaves(leaf_size):
+    """From 2^22 particles on, the leaf moments read chunks of sorted ranks
+    staged in shared memory; a leaf that starts near a chunk's end and runs
+    past the staged margin (leaf size 100 > the 64-rank margin) reads the
+    rest from global memory.  Same bit-exact moments and records."""
+    n = (1 << 22) + 4099
+    _compare_build(gen.uniform_cloud(n, seed=leaf_size, n_sink=9), leaf_size)
 
 
 def test_build_node_capacity_retry():
