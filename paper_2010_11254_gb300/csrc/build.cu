@@ -503,8 +503,14 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
                   int *status)
 {
     __shared__ int wcnt[RS_WARPS][256];
-    __shared__ unsigned start[256];
+    __shared__ unsigned start[256]; // global rank of the tile's first key of each digit
+    __shared__ int toff[256];       // tile rank of the tile's first key of each digit
+    __shared__ int sh[32];
     __shared__ int s_tile;
+    // the tile reordered by digit, then written out in digit runs (coalesced)
+    __shared__ uint64_t sk[OS_TILE];
+    __shared__ uint32_t sv[OS_TILE];
+    __shared__ uint8_t sd[OS_TILE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
     for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
@@ -534,7 +540,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
     __syncthreads();
     {
         // thread t owns digit t: exclusive prefix over the warps, the tile's
-        // count, then the count of all earlier tiles by look-back
+        // count, its offset in the tile, then the count of all earlier tiles
+        // by look-back
         const int d = threadIdx.x;
         unsigned run = 0;
         for (int ww = 0; ww < RS_WARPS; ww++) {
@@ -542,6 +549,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
             wcnt[ww][d] = (int)run;
             run += (unsigned)c;
         }
+        int tot;
+        toff[d] = block_incl_scan((int)run, sh, &tot) - (int)run;
         unsigned long long *mine = look + (size_t)tile * 256 + d;
         unsigned excl = 0;
         if (tile == 0) {
@@ -571,10 +580,19 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
 #pragma unroll
     for (int r = 0; r < OS_ITEMS; r++) {
         if (dg[r] < 256) {
-            const unsigned p = start[dg[r]] + (unsigned)wcnt[w][dg[r]] + (unsigned)loc[r];
-            kout[p] = k[r];
-            vout[p] = v[r];
+            const int p = toff[dg[r]] + wcnt[w][dg[r]] + loc[r];
+            sk[p] = k[r];
+            sv[p] = v[r];
+            sd[p] = (uint8_t)dg[r];
         }
+    }
+    __syncthreads();
+    const int cnt = min(OS_TILE, n - tile * OS_TILE);
+    for (int q = threadIdx.x; q < cnt; q += RS_WARPS * 32) {
+        const int d = sd[q];
+        const unsigned p = start[d] + (unsigned)(q - toff[d]);
+        kout[p] = sk[q];
+        vout[p] = sv[q];
     }
 }
 
