@@ -287,16 +287,22 @@ __global__ void k_validate_minmax(const double *pos, const double *mass, const d
     unsigned long long *mm = mm_all + 6 * (size_t)c;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
     bool bad = false;
+    // checks on the bit patterns (the FP64 pipe is slow on this part):
+    // finite = exponent field below all ones; m >= 0 = sign clear or -0; h > 0
+    // = sign clear and not +0
+    constexpr unsigned long long EXP = 0x7ff0000000000000ull, SIGN = 0x8000000000000000ull;
     for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
         for (int a = 0; a < 3; a++) {
             double x = pos[3 * (size_t)i + a];
-            if (!isfinite(x)) bad = true;
+            if ((__double_as_longlong(x) & EXP) == EXP) bad = true;
             unsigned long long u = ord_of(x);
             lo[a] = u < lo[a] ? u : lo[a];
             hi[a] = u > hi[a] ? u : hi[a];
         }
-        double m = mass[i], h = soft[i];
-        if (!(m >= 0.0) || !isfinite(m) || !(h > 0.0) || !isfinite(h)) bad = true;
+        const unsigned long long mb = (unsigned long long)__double_as_longlong(mass[i]);
+        const unsigned long long hb = (unsigned long long)__double_as_longlong(soft[i]);
+        if ((mb & EXP) == EXP || ((mb & SIGN) && mb != SIGN)) bad = true;
+        if ((hb & EXP) == EXP || (hb & SIGN) || hb == 0ull) bad = true;
     }
     for (int a = 0; a < 3; a++) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -1154,10 +1160,65 @@ __global__ void __launch_bounds__(LM_BT) k_leaf_moments_staged(MomArgs A, const 
     }
 }
 
-__global__ void k_internal_moments(MomArgs A, int b, int e)
+// Node order of the internal passes: within every level, internal nodes by
+// child count (8 first), then the leaves.  A lane combines one node's
+// children, so a warp's lanes take nodes of the same child count; in
+// breadth-first order leaves and internal nodes interleave (clumpy clouds:
+// about a quarter of the lanes busy).  A node's sums do not depend on its
+// slot, and every level keeps its slice [lvl_off[l], lvl_off[l + 1]).
+constexpr int NB_BINS = (SFG_LMAX + 1) * 9;
+
+__device__ __forceinline__ int node_bin(int level, int nch) { return level * 9 + (8 - min(max(nch, 0), 8)); }
+
+__global__ void k_node_hist(const int32_t *nlevel, const int32_t *nnchild, int nn, unsigned *hist)
 {
-    for (int node = b + blockIdx.x * blockDim.x + threadIdx.x; node < e; node += gridDim.x * blockDim.x)
+    __shared__ unsigned h[NB_BINS];
+    for (int b = threadIdx.x; b < NB_BINS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[node_bin(nlevel[i], nnchild[i])], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < NB_BINS; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+__global__ void k_node_starts(const unsigned *hist, unsigned *cur)
+{
+    unsigned run = 0;
+    for (int b = 0; b < NB_BINS; b++) {
+        cur[b] = run;
+        run += hist[b];
+    }
+}
+
+__global__ void k_node_scatter(const int32_t *nlevel, const int32_t *nnchild, int nn, unsigned *cur, int *perm)
+{
+    __shared__ unsigned h[NB_BINS], base[NB_BINS];
+    for (int c0 = blockIdx.x * blockDim.x; c0 < nn; c0 += gridDim.x * blockDim.x) {
+        for (int b = threadIdx.x; b < NB_BINS; b += blockDim.x) h[b] = 0;
+        __syncthreads();
+        const int i = c0 + threadIdx.x;
+        int bin = -1;
+        unsigned r = 0;
+        if (i < nn) {
+            bin = node_bin(nlevel[i], nnchild[i]);
+            r = atomicAdd(&h[bin], 1u);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < NB_BINS; b += blockDim.x)
+            if (h[b]) base[b] = atomicAdd(&cur[b], h[b]);
+        __syncthreads();
+        if (bin >= 0) perm[base[bin] + r] = i;
+        __syncthreads();
+    }
+}
+
+__global__ void k_internal_moments(MomArgs A, const int *perm, int b, int e)
+{
+    for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+        const int node = perm[i];
         if (A.nnchild[node] != 0) internal_moments(A, A.fr[A.ncloud[node]], node);
+    }
 }
 
 // Nodes per level taken by the single-block pass.  A node's combine is ~200
@@ -1171,11 +1232,13 @@ struct LevelOffsets {
     int off[SFG_LMAX + 3];
 };
 
-__global__ void __launch_bounds__(256) k_internal_moments_top(MomArgs A, LevelOffsets L, int top)
+__global__ void __launch_bounds__(256) k_internal_moments_top(MomArgs A, const int *perm, LevelOffsets L, int top)
 {
     for (int l = top; l >= 0; l--) {
-        for (int node = L.off[l] + threadIdx.x; node < L.off[l + 1]; node += blockDim.x)
+        for (int i = L.off[l] + threadIdx.x; i < L.off[l + 1]; i += blockDim.x) {
+            const int node = perm[i];
             if (A.nnchild[node] != 0) internal_moments(A, A.fr[A.ncloud[node]], node);
+        }
         __syncthreads();
     }
 }
@@ -1512,6 +1575,15 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         k_leaf_moments<<<grid_for(nn, 128), 128, 0, s>>>(A, lidx);
     }
     t->n_launch += 1;
+    int *perm = nullptr;
+    unsigned *nbin = nullptr;
+    ALLOC(perm, int, nn);
+    ALLOC(nbin, unsigned, 2 * NB_BINS);
+    SFG_CUDA_OK(cudaMemsetAsync(nbin, 0, sizeof(unsigned) * NB_BINS, s));
+    k_node_hist<<<grid_for(nn, BT), BT, 0, s>>>(t->nlevel, t->nnchild, nn, nbin);
+    k_node_starts<<<1, 1, 0, s>>>(nbin, nbin + NB_BINS);
+    k_node_scatter<<<grid_for(nn, BT), BT, 0, s>>>(t->nlevel, t->nnchild, nn, nbin + NB_BINS, perm);
+    t->n_launch += 3;
     // levels 0..top hold few nodes each: one block takes them in one launch
     int top = -1;
     while (top + 1 < t->depth && t->lvl_off[top + 2] - t->lvl_off[top + 1] <= SMALL_LEVEL) top++;
@@ -1519,16 +1591,18 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         int b = t->lvl_off[l], e = t->lvl_off[l + 1];
         // one warp per block on the smaller levels, so that they spread over the SMs
         const int bs = e - b <= num_sms() * 128 ? 32 : 128;
-        k_internal_moments<<<(e - b + bs - 1) / bs, bs, 0, s>>>(A, b, e);
+        k_internal_moments<<<(e - b + bs - 1) / bs, bs, 0, s>>>(A, perm, b, e);
         t->n_launch += 1;
     }
     if (top >= 0) {
         LevelOffsets L;
         for (int l = 0; l < SFG_LMAX + 3; l++) L.off[l] = t->lvl_off[l];
-        k_internal_moments_top<<<1, SMALL_LEVEL, 0, s>>>(A, L, top);
+        k_internal_moments_top<<<1, SMALL_LEVEL, 0, s>>>(A, perm, L, top);
         t->n_launch += 1;
     }
     dev_free(t, nS, s);
+    dev_free(t, perm, s);
+    dev_free(t, nbin, s);
     dev_free(t, lidx, s);
     if (lhist) dev_free(t, lhist, s);
     t->frames_h.resize(C);

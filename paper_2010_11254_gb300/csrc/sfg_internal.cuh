@@ -237,12 +237,28 @@ __host__ __device__ inline uint64_t morton3(uint32_t qx, uint32_t qy, uint32_t q
     return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
 }
 
+// Cell of coordinate x: floor((x - x0) scale) clamped to [0, 2^21 - 1].
+// scale = 2^21 / L0 is a power of two, so the product is exact and its floor
+// is read off the bits of the (rounded) difference with the exponent moved
+// by log2(scale): one FP64 operation, the rest on the integer pipes.  A
+// subnormal difference takes the FP64 product.
 __device__ inline uint32_t cell_of(double x, double x0, double scale)
 {
-    double s = __dmul_rn(__dsub_rn(x, x0), scale);
-    if (!(s > 0.0)) return 0u;
-    if (s >= 2097152.0) return SFG_GRID_MAX;
-    return (uint32_t)s;
+    const double t = __dsub_rn(x, x0);
+    const long long tb = __double_as_longlong(t);
+    if (tb <= 0) return 0u; // t <= 0 (the sign bit or +0)
+    const int ex = (int)((tb >> 52) & 0x7ff);
+    if (ex == 0x7ff) return (tb & 0xfffffffffffffll) ? 0u : SFG_GRID_MAX; // NaN: 0, +inf: clamped
+    if (ex == 0) {
+        const double s = __dmul_rn(t, scale);
+        return s >= 2097152.0 ? SFG_GRID_MAX : (uint32_t)s;
+    }
+    const int se = (int)((__double_as_longlong(scale) >> 52) & 0x7ff) - 1023;
+    const int e = ex - 1023 + se; // exponent of the product
+    if (e < 0) return 0u;
+    if (e >= 21) return SFG_GRID_MAX;
+    const unsigned long long m = (unsigned long long)(tb & 0xfffffffffffffll) | (1ull << 52);
+    return (uint32_t)(m >> (52 - e));
 }
 
 __device__ inline unsigned long long hq_of(double h, double scale)
