@@ -28,6 +28,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "sfg_internal.cuh"
@@ -245,6 +246,10 @@ void Scan1P::range(const int *in, int *out, const int *d_lo, const int *d_hi, in
     k_scan_1p<<<grid, SP_BT, 0, s>>>(in, out, d_lo, d_hi, std::min(bound, max_n), extra_dst, extra_base, ctr, look,
                                      status);
 }
+
+// Depth of the last tree built in this process: the octree enqueues that
+// many levels before its first look at the level sizes.
+static std::atomic<int> g_depth_hint{SFG_LMAX};
 
 int num_sms()
 {
@@ -1472,20 +1477,40 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
         t->n_launch += 1 + (SFG_LMAX + 1) * 3; // roots; per level: count, scan, write
         // grid-stride over a level (its size is only known on the device)
         const int og = std::min(grid_for(cap, BT), num_sms() * 4);
-        for (int level = 0; level <= SFG_LMAX; level++) {
-            k_oct_count<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
-                                          t->ncount, tmp, bnd, t->d_status);
-            sc.range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
-                     t->d_lvl + level + 1, t->d_status, s);
-            k_oct_write<<<og, BT, 0, s>>>(bnd, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
-                                                         t->ncount, t->nparent, t->nchild_first, t->nnchild,
-                                                         t->nlevel, t->ncloud, tmpo, t->d_status);
-        }
+        auto levels = [&](int l0, int l1) {
+            for (int level = l0; level < l1; level++) {
+                k_oct_count<<<og, BT, 0, s>>>(t->key, ks, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst,
+                                              t->ncount, tmp, bnd, t->d_status);
+                sc.range(tmp, tmpo, t->d_lvl + level, t->d_lvl + level + 1, cap, t->d_lvl + level + 2,
+                         t->d_lvl + level + 1, t->d_status, s);
+                k_oct_write<<<og, BT, 0, s>>>(bnd, t->d_lvl, level, t->prm.leaf_size, cap, t->nfirst, t->ncount,
+                                              t->nparent, t->nchild_first, t->nnchild, t->nlevel, t->ncloud, tmpo,
+                                              t->d_status);
+            }
+        };
+        // the levels the last tree needed (and two more) first; then the rest
+        // only if the tree goes deeper (their launches find empty levels)
+        const int l1 = std::min(SFG_LMAX + 1, g_depth_hint.load() + 2);
+        levels(0, l1);
         int st = 0;
         SFG_CUDA_OK(cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         SFG_CUDA_OK(cudaMemcpyAsync(t->lvl_off, t->d_lvl, sizeof(int) * (SFG_LMAX + 3), cudaMemcpyDeviceToHost, s));
         SFG_CUDA_OK(cudaStreamSynchronize(s));
         SFG_CUDA_OK(cudaGetLastError());
+        if (l1 <= SFG_LMAX && !(st & (ST_NODECAP | ST_EINVAL))) {
+            if (t->lvl_off[l1 + 1] > t->lvl_off[l1]) {
+                levels(l1, SFG_LMAX + 1);
+                SFG_CUDA_OK(cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+                SFG_CUDA_OK(
+                    cudaMemcpyAsync(t->lvl_off, t->d_lvl, sizeof(int) * (SFG_LMAX + 3), cudaMemcpyDeviceToHost, s));
+                SFG_CUDA_OK(cudaStreamSynchronize(s));
+                SFG_CUDA_OK(cudaGetLastError());
+            } else {
+                // level l1 is empty, and so is every deeper one
+                t->n_launch -= (SFG_LMAX + 1 - l1) * 3;
+                for (int l = l1 + 2; l <= SFG_LMAX + 2; l++) t->lvl_off[l] = t->lvl_off[l1 + 1];
+            }
+        }
         dev_free(t, tmp, s);
         dev_free(t, tmpo, s);
         dev_free(t, bnd, s);
@@ -1504,6 +1529,7 @@ int build_tree(Tree *t, const double *pos, const double *mass, const double *sof
     for (int l = 0; l <= SFG_LMAX; l++)
         if (t->lvl_off[l + 1] > t->lvl_off[l]) t->depth = l;
     t->n_levels = t->depth + 1;
+    g_depth_hint.store(t->depth);
 
     ALLOC(t->W0, int4, nn);
     ALLOC(t->W1, int4, nn);
