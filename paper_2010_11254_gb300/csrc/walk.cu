@@ -2329,8 +2329,15 @@ __global__ void k_cmp_idx(const int64_t *a, const int64_t *b, int64_t n, int *fl
         if (a[k] != b[k]) *flag = 1;
 }
 
+// The list-only walks (no evaluation) are latency-bound: two more resident
+// blocks per SM keep more groups in flight.
+__host__ __device__ constexpr int walk_minb(int mode)
+{
+    return mode == MODE_COUNT || mode == MODE_LIST || mode == MODE_LIST1 ? WALK_MINB + 2 : WALK_MINB;
+}
+
 template <bool QUAD, int MODE, bool GSTACK>
-__global__ void __launch_bounds__(WALK_WARPS * 32, WALK_MINB) k_walk(WalkParams P)
+__global__ void __launch_bounds__(WALK_WARPS * 32, walk_minb(MODE)) k_walk(WalkParams P)
 {
     __shared__ WarpSmem sm[WALK_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -2777,10 +2784,7 @@ template <int MODE>
 static void launch_walk(Tree *t, WalkParams &P, cudaStream_t s)
 {
     t->n_launch += 2;
-    // the list-only walks (no evaluation, fewer registers) are latency-bound:
-    // two more resident blocks per SM keep more groups in flight
-    const int blocks =
-        num_sms() * (MODE == MODE_COUNT || MODE == MODE_LIST || MODE == MODE_LIST1 ? WALK_MINB + 2 : WALK_MINB);
+    const int blocks = num_sms() * walk_minb(MODE);
     const int retry_blocks = num_sms();
     if (t->prm.quadrupole) {
         k_walk<true, MODE, false><<<blocks, WALK_WARPS * 32, 0, s>>>(P);
