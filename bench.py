@@ -54,8 +54,8 @@ FLOP_VJP_P2M_QUAD = 139
 # DRAM bytes per launch of the evaluation kernels on the default workload
 # (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture), valid only
 # for the walk source (sha256 of walk.cu) and launch shape they were taken on.
-WALK_TRAFFIC = {"sha256": "c0ae0c604df56ecd290b997760527e8f694c0bec59dc3835bb32da6d0f9563e1",
-                "leaf_size": 32, "group_size": 16, "fwd": 473442304, "vjp": 1287380480}
+WALK_TRAFFIC = {"sha256": "219d8f26358dfcdf614afae6aa2e838c484c1484854ab6b89c30ab6e043cc275",
+                "leaf_size": 32, "group_size": 16, "fwd": 496040704, "vjp": 1385587200}
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576
