@@ -280,6 +280,16 @@ const char *sfg_status_string(int status);
  * unrelated calls before they start, so SFG_ECUDA names an error of their own. */
 const char *sfg_last_cuda_error(void);
 
+/* ---- measurement ----
+ * FP32 fused multiply-add throughput of the current device, measured: a
+ * launch of FMA-only threads (8 independent chains each, 4 blocks of 256
+ * threads per SM), timed with CUDA events on `stream` after a warm-up
+ * launch.  The roofline of the evaluation kernels (bound by the FP32 pipes)
+ * is taken against it.  *tflops receives 2 x FMAs / time in TFLOP/s and, if
+ * ms is not NULL, *ms the timed launch's milliseconds.  Synchronizes the
+ * stream.  SFG_EINVAL for a NULL tflops, SFG_ENOMEM, SFG_ECUDA. */
+int sfg_fp32_peak(double *tflops, double *ms, void *stream);
+
 /* ---- inspection (tests and tools; copies to HOST memory, synchronizing) ----
  * field ids and layouts:
  *   SFG_FIELD_KEYS      uint64 [n]        sorted Morton keys

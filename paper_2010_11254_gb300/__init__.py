@@ -96,6 +96,8 @@ def _load():
         lib.sfg_accel_tidal.restype = i32
         lib.sfg_tidal_timestep.argtypes = [vp, i64, ctypes.c_double, vp, vp]
         lib.sfg_tidal_timestep.restype = i32
+        lib.sfg_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+        lib.sfg_fp32_peak.restype = i32
         lib.sfg_accel_jerk.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
         lib.sfg_accel_jerk.restype = i32
         lib.sfg_sink_timestep.argtypes = [vp, vp, vp, i64, ctypes.c_double, vp, vp]
@@ -360,6 +362,17 @@ def tidal_timestep(tidal: torch.Tensor, eta: float) -> torch.Tensor:
         rc = _load().sfg_tidal_timestep(tidal.data_ptr(), n, float(eta), dt.data_ptr(), _stream(tidal.device))
     _check(rc, "sfg_tidal_timestep")
     return dt
+
+
+def fp32_peak(device=None) -> dict:
+    """Measured FP32 FMA throughput of the device (sfg_fp32_peak): TFLOP/s and
+    the timed launch's milliseconds."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        rc = _load().sfg_fp32_peak(ctypes.byref(tf), ctypes.byref(ms), _stream(dev))
+    _check(rc, "sfg_fp32_peak")
+    return {"tflops": tf.value, "ms": ms.value}
 
 
 def gravity(pos, mass, soft, is_sink=None, active=None, **kw):

@@ -91,6 +91,69 @@ void sfg_default_params(sfg_params *p)
 
 const char *sfg_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
 
+// FMA-only probe: 8 independent chains per thread cover the FMA latency, so
+// the launch runs at the FP32 pipes' issue rate; the sums are stored so that
+// none of the chains is dropped.
+constexpr int PK_UNROLL = 16, PK_CHAINS = 8, PK_BT = 256;
+
+__global__ void __launch_bounds__(PK_BT) k_ffma_peak(const float *ab, int iters, float *out)
+{
+    const float a = ab[0], b = ab[1];
+    float x[PK_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; c++) x[c] = (float)(threadIdx.x + c) * 1e-3f;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < PK_UNROLL; u++) {
+#pragma unroll
+            for (int c = 0; c < PK_CHAINS; c++) x[c] = fmaf(x[c], a, b);
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; c++) sum += x[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+int sfg_fp32_peak(double *tflops, double *ms, void *stream)
+{
+    if (!tflops) return SFG_EINVAL;
+    cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    SFG_CUDA_OK(cudaGetDevice(&dev));
+    SFG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 4 * (sms > 0 ? sms : 1), iters = 8192;
+    float *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, sizeof(float) * (2 + (size_t)blocks * PK_BT), s) != cudaSuccess) {
+        cudaGetLastError();
+        return SFG_ENOMEM;
+    }
+    const float ab[2] = {0.9999999f, 1e-7f};
+    int rc = SFG_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float t = 0.f;
+    if (cudaMemcpyAsync(buf, ab, sizeof(ab), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError());
+    } else {
+        k_ffma_peak<<<blocks, PK_BT, 0, s>>>(buf, iters / 4, buf + 2); // warm-up
+        cudaEventRecord(e0, s);
+        k_ffma_peak<<<blocks, PK_BT, 0, s>>>(buf, iters, buf + 2);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess || t <= 0.f)
+            rc = cuda_fail(cudaGetLastError());
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(buf, s);
+    if (rc) return rc;
+    const double flops = 2.0 * (double)blocks * PK_BT * (double)iters * PK_UNROLL * PK_CHAINS;
+    *tflops = flops / ((double)t * 1e-3) / 1e12;
+    if (ms) *ms = (double)t;
+    return SFG_OK;
+}
+
 const char *sfg_status_string(int st)
 {
     switch (st) {

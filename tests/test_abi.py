@@ -56,6 +56,8 @@ def test_host_side_argument_checks(lib):
         q = sfg.default_params()
         setattr(q, field, bad)
         assert lib.sfg_build(fake, fake, fake, None, 10, ctypes.byref(q), None, ctypes.byref(out)) == sfg.SFG_EINVAL
+    lib.sfg_fp32_peak.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.sfg_fp32_peak(None, None, None) == sfg.SFG_EINVAL
     lib.sfg_accel.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p]
     assert lib.sfg_accel(None, None, 1, fake, None, None) == sfg.SFG_EINVAL
