@@ -563,7 +563,6 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
             tree = sfg.Tree(dv[0], dv[1], dv[2], dv[3], **kw)
             acc, phi = tree.accel(dv[4])
             g_pos, g_mass = tree.accel_vjp(dv[4], dv[5], dv[6])
-            tree.close()
             done = torch.cuda.Event()
             done.record(stream)
             last_use[sl] = done
@@ -574,6 +573,7 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
                 for h, d in zip(h_out, (acc, phi, g_pos, g_mass)):
                     d.record_stream(copy_s)
                     h.copy_(d, non_blocking=True)
+            tree.close()  # synchronizes the compute stream: after the copies are queued
         stream.wait_stream(copy_s)
         e1.record(stream)
         e1.synchronize()
