@@ -55,8 +55,8 @@ FLOP_VJP_P2M_QUAD = 139
 # DRAM bytes per launch of the evaluation kernels on the default workload
 # (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture), valid only
 # for the walk source (sha256 of walk.cu) and launch shape they were taken on.
-WALK_TRAFFIC = {"sha256": "219d8f26358dfcdf614afae6aa2e838c484c1484854ab6b89c30ab6e043cc275",
-                "leaf_size": 32, "group_size": 16, "fwd": 496040704, "vjp": 1385587200}
+WALK_TRAFFIC = {"sha256": "b2744f99249a44a9ec661e44de1d7a68d1530745e9ad1e974ead840068a638a5",
+                "leaf_size": 32, "group_size": 16, "fwd": 501262848, "vjp": 1417757440}
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576

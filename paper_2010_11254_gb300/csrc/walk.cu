@@ -1310,33 +1310,6 @@ __device__ __forceinline__ int ring_take(const WalkParams &P, const SM &S, int c
     return j;
 }
 
-// Newtonian tile: positions and masses only (and the particle id for the adjoint).
-template <class SM>
-__device__ __forceinline__ void stage_p2p_newt(const WalkParams &P, SM &S, int cnt, int &qh, int &qoff, const Tgt &T,
-                                               int lane)
-{
-    int j = ring_take(P, S, cnt, qh, qoff, lane);
-    if (lane < cnt && (j < 0 || j >= P.npart)) { // a corrupt range: skipped, status set
-        atomicOr(P.status, ST_ETIMEOUT);
-        j = -1;
-    }
-    if (lane < cnt) {
-        if (j >= 0) {
-            float4 a = P.pw[j];
-            int4 b = P.pc[j];
-            float px = fmaf((float)(b.x - T.cg[0]), T.s22, a.x);
-            float py = fmaf((float)(b.y - T.cg[1]), T.s22, a.y);
-            float pz = fmaf((float)(b.z - T.cg[2]), T.s22, a.z);
-            S.tP[lane] = make_float4(px, py, pz, a.w);
-            S.tN[lane] = j;
-        } else {
-            S.tP[lane] = make_float4(3e18f, 0.f, 0.f, 0.f); // massless and far: no contribution
-            S.tN[lane] = -1;
-        }
-    }
-    __syncwarp();
-}
-
 template <class SM>
 __device__ __forceinline__ void fwd_newt_step(const SM &S, int k, const Tgt &T, float &ax, float &ay, float &az,
                                               float &pt)
@@ -1869,7 +1842,7 @@ __device__ __forceinline__ void ts_tile(const SM &S, int cnt, const Tgt &T, floa
 // The evaluation kernel copies the next tile's source records into
 // S.raw with asynchronous 16-byte copies (cp.async) while it evaluates the
 // current tile, then converts them in place of the synchronous staging
-// (same layouts as stage_p2p / stage_p2p_newt / stage_p2m).  Each lane
+// (same layouts as stage_p2p / stage_p2m).  Each lane
 // copies, waits for and converts only its own slot.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
@@ -2972,22 +2945,27 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
     }
     const double na = (double)std::max<int64_t>(n_active, 1);
     bool counted = false;
-    if (h.m_per > 0.0) {
-        const int main_warps = num_sms() * (WALK_MINB + 2) * WALK_WARPS;
-        const int warps = main_warps + num_sms() * WALK_WARPS;
-        const size_t stg_m_bytes = align_up((size_t)warps * h.stg_m * sizeof(int));
-        const size_t stg_r_bytes = align_up((size_t)warps * 2 * h.stg_r * sizeof(int2));
+    const int main_warps = num_sms() * walk_minb(MODE_LIST1) * WALK_WARPS;
+    const int warps = main_warps + num_sms() * WALK_WARPS;
+    const size_t stg_m_bytes = align_up((size_t)warps * h.stg_m * sizeof(int));
+    const size_t stg_r_bytes = align_up((size_t)warps * 2 * h.stg_r * sizeof(int2));
+    bool one_pass = h.m_per > 0.0;
+    if (one_pass) {
         const size_t stg_bytes = stg_m_bytes + stg_r_bytes + sizeof(int) * (size_t)t->n;
         if (t->lstage_bytes < stg_bytes) {
             if (t->lstage) dev_free(t, t->lstage, s);
             t->lstage = dev_alloc(t, stg_bytes, s);
             t->lstage_bytes = t->lstage ? stg_bytes : 0;
-            if (!t->lstage) return SFG_ENOMEM;
         }
-        int rc = grow_buffer(t, (void **)&t->lm, &t->lm_cap, (long long)(h.m_per * na * 1.15) + 4096, sizeof(int), s);
-        if (rc) return rc;
-        rc = grow_buffer(t, (void **)&t->lr, &t->lr_cap, (long long)(h.r_per * na * 1.15) + 1024, sizeof(int2), s);
-        if (rc) return rc;
+        // where the staging or the buffers sized from the hint do not fit in
+        // memory, the sizes-first path below allocates exactly what it needs
+        one_pass = t->lstage != nullptr &&
+                   grow_buffer(t, (void **)&t->lm, &t->lm_cap, (long long)(h.m_per * na * 1.15) + 4096, sizeof(int),
+                               s) == SFG_OK &&
+                   grow_buffer(t, (void **)&t->lr, &t->lr_cap, (long long)(h.r_per * na * 1.15) + 1024, sizeof(int2),
+                               s) == SFG_OK;
+    }
+    if (one_pass) {
         P.lm = t->lm;
         P.lr = t->lr;
         P.lcap_m = t->lm_cap;
