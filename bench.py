@@ -8,15 +8,16 @@ cotangents.  Metric: active-particle gravity evaluations per second
 (= active particles / step time), with the walk kernel's FP32 throughput
 against the GB300 FP32 ALU peak.
 
-Default workload: the clumpy GMC-like cloud -- 2^21 equal-mass cells in 512
-Plummer clumps (70 % of the mass) + 30 % uniform in the unit sphere, 32nd-
-neighbour softening, 256 sinks (log-normal masses, softening 1e-3), theta =
-0.5, quadrupoles, a random 10 % active subset.  Inputs are resident in HBM
-when the timed region starts; L2 (129 MB) is flushed before every timed step
-by writing a 512 MB buffer.
+Default workload (paper-20M): the paper-scale clumpy GMC-like cloud --
+2e7 equal-mass cells, 70 % of the mass in 2048 Plummer clumps and 30 %
+uniform in the unit sphere, 32nd-neighbour softening, 1024 sinks
+(log-normal masses, softening 1e-3), theta = 0.5, quadrupoles, a random 10 %
+active subset.  clumpy-2M is the same recipe at 2^21 cells, 512 clumps and
+256 sinks.  Inputs are resident in HBM when the timed region starts; L2 (129
+MB) is flushed before every timed step by writing a 512 MB buffer.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload clumpy-2M|paper-20M] [--active-frac F]
+                    [--workload paper-20M|clumpy-2M|ensemble-256] [--active-frac F]
     python bench.py --opening-curve     # accuracy vs cost of the opening rules
 
 Multi-GPU (torchrun): every rank solves its own independent cloud (seed +
@@ -41,22 +42,25 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # FP32 operations per interaction, counted from the evaluation source
-# (walk.cu: fwd_newt_step for every P2P pair, fwd_p2m_step with quadrupole /
-# monopole); FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The deferred evaluation of
-# the pairs inside a softening support is extra work and not counted.
-FLOP_P2P = 19
-FLOP_P2M_QUAD = 55
-FLOP_P2M_MONO = 19
-# Adjoint (walk.cu: vjp_p2p_newt for every P2P pair, vjp_p2m_tile with
-# quadrupole), same counting rule; the source-side rotation shuffles and the
-# deferred softened pairs are not counted.
-FLOP_VJP_P2P = 42
-FLOP_VJP_P2M_QUAD = 139
-# DRAM bytes per launch of the evaluation kernels on the default workload
-# (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture), valid only
-# for the walk source (sha256 of walk.cu) and launch shape they were taken on.
-WALK_TRAFFIC = {"sha256": "b2744f99249a44a9ec661e44de1d7a68d1530745e9ad1e974ead840068a638a5",
-                "leaf_size": 32, "group_size": 16, "fwd": 501262848, "vjp": 1417757440}
+# (eval_chunks.cuh: chunk_fwd_parts for every P2P pair, chunk_fwd_nodes with
+# quadrupole / monopole); FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The deferred
+# evaluation of the pairs inside a softening support, padding slots and
+# absent targets are extra work and not counted.
+FLOP_P2P = 20
+FLOP_P2M_QUAD = 53
+FLOP_P2M_MONO = 20
+# Adjoint (eval_chunks.cuh: chunk_vjp_parts for every P2P pair,
+# chunk_vjp_nodes with quadrupole), same counting rule; the source-side
+# rotation shuffles and the deferred softened pairs are not counted.
+FLOP_VJP_P2P = 44
+FLOP_VJP_P2M_QUAD = 137
+# DRAM bytes per launch of the evaluation kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture), valid only for the evaluation
+# sources (sha256 over walk.cu and eval_chunks.cuh), workload and launch shape
+# they were taken on; otherwise the line reports null.
+EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16,
+                "fwd": None, "vjp": None}
+EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576
@@ -66,6 +70,15 @@ WORKLOADS = {
     "paper-20M": dict(n_gas=20_000_000, n_clumps=2048, n_sink=1024, theta=0.5, active=0.1, seed_id=5),
     "clumpy-256K": dict(n_gas=1 << 18, n_clumps=128, n_sink=64, theta=0.5, active=0.1, seed_id=2),
 }
+
+
+def eval_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in EVAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_11254_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def load_peaks():
@@ -227,26 +240,34 @@ def aggregate(local_ms: float, units_per_rank: int, world: int, dist=None, devic
 
 
 def run_reference(args, wl, rank, world):
-    """--impl reference: the CPU oracle on this workload (rank 0 only)."""
+    """--impl reference: the CPU oracle on this workload (rank 0 only).  One
+    step is a bounded sample of the workload: the oracle tree over every
+    particle, then walk + field + adjoint of a random sample of the active
+    rows; ms_per_step is that step's wall time, and the value is the
+    evals/s of a whole step extrapolated from it per active row."""
     if rank != 0:
         return
     c, act, ca, cp, frac = make_inputs(wl, 0, args.active_frac)
-    for _ in range(args.warmup):
-        cpu_baseline(wl, c, act, ca, cp, sample=1024, seed=1)
+    sample = 1024
+    for k in range(args.warmup):
+        cpu_baseline(wl, c, act, ca, cp, sample=64, seed=1 + k)
     vals, wall = [], []
+    r = None
     for k in range(args.steps):
         t0 = time.perf_counter()
-        r = cpu_baseline(wl, c, act, ca, cp, sample=2048, seed=10 + k)
+        r = cpu_baseline(wl, c, act, ca, cp, sample=sample, seed=10 + k)
         wall.append(time.perf_counter() - t0)
         vals.append(r["value"])
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": "active-particle gravity evaluations per second (build + field + adjoint)",
             "value": v, "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * act.size / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1e3 * statistics.mean(wall), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n_particles": int(c.n), "n_active": int(act.size),
                        "active_frac": frac, "theta": wl["theta"]},
-            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": v},
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"],
+                             "sample": r["sample"] + "; ms_per_step is the wall time of one such sampled step",
+                             "value": v, "est_full_step_s": round(statistics.median(act.size / x for x in vals), 3)},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -622,17 +643,15 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
     sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak, peak_text, _ = fp32_peak(sfg, sms, sm_max)
-    import hashlib
-    src = os.path.join(ROOT, "paper_2010_11254_gb300", "csrc", "walk.cu")
-    same_src = WALK_TRAFFIC["sha256"] == hashlib.sha256(open(src, "rb").read()).hexdigest()
+    same_src = EVAL_TRAFFIC["sha256"] is not None and EVAL_TRAFFIC["sha256"] == eval_sources_sha256()
 
     def roof(kernel, flops, ms, traffic_key, model):
         a = flops / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": kernel, "achieved": round(a, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(a / peak, 4),
-                "traffic": WALK_TRAFFIC[traffic_key] if (same_src and args.workload == "clumpy-2M"
-                                                          and (leaf, group) == (WALK_TRAFFIC["leaf_size"],
-                                                                                WALK_TRAFFIC["group_size"])) else None,
+                "traffic": EVAL_TRAFFIC[traffic_key] if (same_src and args.workload == EVAL_TRAFFIC["workload"]
+                                                          and (leaf, group) == (EVAL_TRAFFIC["leaf_size"],
+                                                                                EVAL_TRAFFIC["group_size"])) else None,
                 "peak_source": peak_text,
                 "flops_per_launch": int(flops), "launch_ms": round(ms, 4), "flop_model": model}
 
@@ -744,11 +763,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="clumpy-2M", choices=sorted(WORKLOADS) + ["ensemble-256"])
+    ap.add_argument("--workload", default="paper-20M", choices=sorted(WORKLOADS) + ["ensemble-256"])
     ap.add_argument("--active-frac", type=float, default=None)
     ap.add_argument("--active-fracs", default=None,
                     help="comma-separated active fractions: one line each on the same cloud")
-    ap.add_argument("--error-sample", type=int, default=1000,
+    ap.add_argument("--error-sample", type=int, default=10000,
                     help="active rows checked against the FP64 direct sum")
     ap.add_argument("--store-lists", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -61,9 +61,11 @@ typedef struct sfg_params {
     int quadrupole;  /* 1: monopole + quadrupole node fields; 0: monopole only (Sec. 2.2) */
     int precision;   /* 0: FP32 pair/multipole arithmetic on node-centred offsets, FP64
                         frame/moments/potential sums; 1: all-FP64 evaluation */
-    int store_lists; /* 1: walk once per call into stored interaction lists (two walks:
-                        count, then write), evaluate from them, and let the adjoint reuse
-                        the forward's lists when called with the same active set;
+    int store_lists; /* 1: walk once per call into stored interaction lists (one walk that
+                        stages each group's lists and places them, or, when they outgrow the
+                        sizing hint, a sizes-first walk and a list-writing walk), evaluate
+                        from them, and let the adjoint reuse the forward's lists when
+                        called with the same active set;
                         0: every evaluation walks the tree itself.  Ignored (0) with
                         precision = 1 and while the stream is captured into a CUDA graph
                         (sizing the lists synchronizes the stream once). */
@@ -219,6 +221,32 @@ int sfg_accel_jerk(sfg_tree *tree, const double *vel, const int64_t *active_idx,
 int sfg_sink_timestep(sfg_tree *tree, const double *vel, const int64_t *active_idx, int64_t n_active, double eta,
                       double *dt, void *stream);
 
+/* One step of the modified 4th-order Hermite integrator for sink particles
+ * (Sec. 2.3, the predictor and corrector equations), with both field and
+ * jerk evaluations done by the library on a tree of the n particles alone
+ * (the paper's sinks-only pass; every particle is treated as a sink, so
+ * every pair takes one kernel of support max(S_i, S_j), Sec. 2.2.1):
+ *   a0, j0 at (pos, vel);
+ *   x_p = pos + dt vel + dt^2/2 a0 + dt^3/6 j0,  v_p = vel + dt a0 + dt^2/2 j0;
+ *   a1, j1 at (x_p, v_p);
+ *   vel_out = vel + dt/2 (a1 + a0) + dt^2/12 (j0 - j1),
+ *   pos_out = pos + dt/2 (vel_out + vel) + dt^2/12 (a0 - a1)
+ * (the velocity is corrected first and the position uses it).  Field and
+ * jerk are as sfg_accel_jerk computes them (FP32 terms, FP64 sums and
+ * outputs); the predictor and corrector run in FP64.
+ *   pos, vel  [n][3] float64, device: the state at the start of the step
+ *   mass, soft [n] float64, device: masses and softening radii S_*
+ *   params    as for sfg_build (G, theta, leaf and group size; precision must be 0), or NULL
+ *   dt        the step (finite; the caller chooses it, e.g. from sfg_sink_timestep)
+ *   pos_out, vel_out [n][3] float64, device, overwritten (may not alias pos or vel)
+ * Builds two trees and frees them; allocates its temporaries with
+ * cudaMallocAsync on `stream` and synchronizes it.  Errors: SFG_EINVAL (NULL
+ * pointer, n <= 0 or >= 2^31, dt not finite, bad params, or an error the
+ * device reported for the inputs), SFG_ENOMEM, SFG_ECUDA, SFG_EOVERFLOW,
+ * SFG_ETIMEOUT. */
+int sfg_hermite_step(const double *pos, const double *vel, const double *mass, const double *soft, int64_t n,
+                     const sfg_params *params, double dt, double *pos_out, double *vel_out, void *stream);
+
 /* Tidal timestep constraint of Sec. 2.3:
  *   dt[k] = sqrt(eta) * (|T_k|^2 / 6)^(-1/4),
  * |T| the Frobenius norm of the symmetric tensor given by its six components
@@ -343,10 +371,12 @@ int sfg_debug_lists(sfg_tree *tree, const int64_t *active_idx, int64_t n_active,
  * sfg_sort_keys_static computes what sfg_build computes first -- the frame,
  * the 63-bit Morton keys and their stable sort -- for n <= SFG_STATIC_MAX_N
  * particles without allocating anything:
- *   pos       [n][3] float64, device, finite (not checked)
+ *   pos       [n][3] float64, device, finite, with a largest per-axis extent
+ *             that is 0 or a normal double below 2^1023 (not checked: other
+ *             inputs give unspecified keys, where sfg_build reports SFG_EINVAL)
  *   key_out   [n] uint64, device: the sorted keys (as SFG_FIELD_KEYS)
  *   order_out [n] int32, device: sorted rank -> original index (as SFG_FIELD_ORDER)
- * Temporary buffers live in one fixed array of about 6.5 MB that every GPU
+ * Temporary buffers live in one fixed array of 6,556,928 bytes (6.25 MiB) that every GPU
  * loading the library holds until the process exits.  The first call on a
  * device looks up that array's device address (make it before any stream
  * capture); later calls reuse it.  All calls share the array, so calls that

@@ -106,6 +106,9 @@ def _load():
                                          ctypes.c_int64, _i64p, _f64p]
         lib.sfgo_jerk_group.restype = ctypes.c_int
         lib.sfgo_jerk_group.argtypes = [_vp, _f64p, ctypes.c_double, _i64p, ctypes.c_int64, _f64p]
+        lib.sfgo_hermite_step.restype = None
+        lib.sfgo_hermite_step.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, ctypes.c_double, ctypes.c_double,
+                                          _f64p, _f64p]
         lib.sfgo_direct_tstep.restype = None
         lib.sfgo_direct_tstep.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int64, _i64p, _f64p]
@@ -210,6 +213,24 @@ def direct_tstep(pos, vel, mass, soft, eta: float, targets=None, G: float = 1.0)
     _load().sfgo_direct_tstep(n, _p(pos, _f64p), _p(vel, _f64p), _p(mass, _f64p), _p(soft, _f64p), float(G),
                               float(eta), tg.size, _p(tg, _i64p), _p(dt, _f64p))
     return dt
+
+
+def hermite_step(pos, vel, mass, soft, dt: float, G: float = 1.0):
+    """One modified Hermite step of sink particles (Sec. 2.3, predictor and
+    corrector; two FP64 direct field + jerk evaluations, every particle a
+    sink).  Returns (pos1, vel1), each [n][3]."""
+    pos, vel, mass, soft = _f64(pos), _f64(vel), _f64(mass), _f64(soft)
+    n = pos.shape[0]
+    x1 = np.zeros((n, 3))
+    v1 = np.zeros((n, 3))
+    _load().sfgo_hermite_step(n, _p(pos, _f64p), _p(vel, _f64p), _p(mass, _f64p), _p(soft, _f64p), float(G),
+                              float(dt), _p(x1, _f64p), _p(v1, _f64p))
+    return x1, v1
+
+
+def two_body_dt(pos, vel, mass, soft, eta: float, G: float = 1.0) -> float:
+    """Smallest sink two-body timestep of Sec. 2.3 over all particles (direct)."""
+    return float(direct_tstep(pos, vel, mass, soft, eta, G=G).min())
 
 
 def tidal_dt(tidal, eta: float):

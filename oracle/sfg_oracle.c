@@ -20,6 +20,8 @@
  *           pair, Sec. 2.2.1);
  *       (b) per group of <= G targets, the exact integer, conservative form the
  *           GPU path uses (decisions on integer cell boxes; same decisions here);
+ *   - the modified 4th-order Hermite step of sink particles (Sec. 2.3,
+ *     predictor and corrector) on FP64 direct sinks-only fields and jerks;
  *   - the analytic vector-Jacobian product of the group-form tree with the
  *     interaction lists frozen (tidal tensor of the same softened kernel, Sec. 2.2),
  *     and a frozen-list re-evaluation used for finite differences.
@@ -208,6 +210,66 @@ void sfgo_direct_jerk(int64_t n, const double *pos, const double *vel, const dou
         }
         for (int a = 0; a < 3; a++) jerk[3 * t + a] = G * J[a];
     }
+}
+
+/* Field and jerk of every particle from every other, all treated as sinks
+ * (the sinks-only pass of Sec. 2.3, summed directly in FP64). */
+static void sink_field_jerk(int64_t n, const double *pos, const double *vel, const double *mass, const double *soft,
+                            double G, double *acc, double *jerk)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double A[3] = {0, 0, 0}, J[3] = {0, 0, 0};
+        for (int64_t k = 0; k < n; k++) {
+            if (k == i)
+                continue;
+            double d[3], w[3];
+            for (int a = 0; a < 3; a++) {
+                d[a] = pos[3 * k + a] - pos[3 * i + a];
+                w[a] = vel[3 * k + a] - vel[3 * i + a];
+            }
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double K, P, Kr;
+            pair_law(r, soft[i], soft[k], 1, 1, &K, &P, &Kr);
+            for (int a = 0; a < 3; a++) A[a] += mass[k] * K * d[a];
+            pair_jerk(mass[k], K, Kr, d, w, J);
+        }
+        for (int a = 0; a < 3; a++) {
+            acc[3 * i + a] = G * A[a];
+            jerk[3 * i + a] = G * J[a];
+        }
+    }
+}
+
+/* One step of the modified 4th-order Hermite integrator for sink particles
+ * (Sec. 2.3, the predictor and corrector equations).  The field a0 and jerk
+ * j0 are evaluated at the start (x0, v0); the prediction is
+ *   x_p = x0 + dt v0 + dt^2/2 a0 + dt^3/6 j0,   v_p = v0 + dt a0 + dt^2/2 j0;
+ * the field and jerk are evaluated again at (x_p, v_p), giving a1, j1; the
+ * correction updates the velocity first and the position from it:
+ *   v1 = v0 + dt/2 (a1 + a0) + dt^2/12 (j0 - j1),
+ *   x1 = x0 + dt/2 (v1 + v0) + dt^2/12 (a0 - a1).
+ * pos, vel [n][3] (the start), pos1, vel1 [n][3] (the end). */
+void sfgo_hermite_step(int64_t n, const double *pos, const double *vel, const double *mass, const double *soft,
+                       double G, double dt, double *pos1, double *vel1)
+{
+    size_t b = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
+    double *a0 = malloc(b), *j0 = malloc(b), *a1 = malloc(b), *j1 = malloc(b), *xp = malloc(b), *vp = malloc(b);
+    sink_field_jerk(n, pos, vel, mass, soft, G, a0, j0);
+    for (int64_t q = 0; q < 3 * n; q++) {
+        xp[q] = pos[q] + dt * vel[q] + (dt * dt / 2.0) * a0[q] + (dt * dt * dt / 6.0) * j0[q];
+        vp[q] = vel[q] + dt * a0[q] + (dt * dt / 2.0) * j0[q];
+    }
+    sink_field_jerk(n, xp, vp, mass, soft, G, a1, j1);
+    for (int64_t q = 0; q < 3 * n; q++) {
+        vel1[q] = vel[q] + (dt / 2.0) * (a1[q] + a0[q]) + (dt * dt / 12.0) * (j0[q] - j1[q]);
+        pos1[q] = pos[q] + (dt / 2.0) * (vel1[q] + vel[q]) + (dt * dt / 12.0) * (a0[q] - a1[q]);
+    }
+    free(a0);
+    free(j0);
+    free(a1);
+    free(j1);
+    free(xp);
+    free(vp);
 }
 
 /* Tidal timestep of Sec. 2.3, Eq. for Delta t_tidal: sqrt(eta) (|T|^2 / 6)^(-1/4)

@@ -102,6 +102,8 @@ def _load():
         lib.sfg_accel_jerk.restype = i32
         lib.sfg_sink_timestep.argtypes = [vp, vp, vp, i64, ctypes.c_double, vp, vp]
         lib.sfg_sink_timestep.restype = i32
+        lib.sfg_hermite_step.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp]
+        lib.sfg_hermite_step.restype = i32
         lib.sfg_set_relative_criterion.argtypes = [vp, vp, ctypes.c_double, vp]
         lib.sfg_set_relative_criterion.restype = i32
         lib.sfg_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -203,8 +205,18 @@ class Tree:
 
     def accel(self, active=None, out=None):
         a, na = self._active(active)
-        acc = torch.empty((na, 3), dtype=torch.float64, device=self.device) if out is None else out[0]
-        phi = torch.empty(na, dtype=torch.float64, device=self.device) if out is None else out[1]
+        if out is None:
+            acc = torch.empty((na, 3), dtype=torch.float64, device=self.device)
+            phi = torch.empty(na, dtype=torch.float64, device=self.device)
+        else:
+            acc, phi = out
+            if not (isinstance(acc, torch.Tensor) and acc.is_cuda and acc.dtype == torch.float64
+                    and acc.is_contiguous() and tuple(acc.shape) == (na, 3)):
+                raise ValueError(f"out[0] must be a contiguous CUDA float64 tensor of shape [{na}, 3]")
+            if phi is not None and not (isinstance(phi, torch.Tensor) and phi.is_cuda
+                                        and phi.dtype == torch.float64 and phi.is_contiguous()
+                                        and tuple(phi.shape) == (na,)):
+                raise ValueError(f"out[1] must be None or a contiguous CUDA float64 tensor of shape [{na}]")
         with torch.cuda.device(self.device):
             rc = _load().sfg_accel(self._h, None if a is None else a.data_ptr(), na, acc.data_ptr(),
                                    phi.data_ptr() if phi is not None else None, _stream(self.device))
@@ -261,8 +273,12 @@ class Tree:
     def accel_vjp(self, active, cot_a, cot_phi=None):
         a, na = self._active(active)
         cot_a = _dev(cot_a, torch.float64, "cot_a")
+        if tuple(cot_a.shape) != (na, 3):
+            raise ValueError(f"cot_a must be [{na}, 3] (one row per active index)")
         if cot_phi is not None:
             cot_phi = _dev(cot_phi, torch.float64, "cot_phi")
+            if tuple(cot_phi.shape) != (na,):
+                raise ValueError(f"cot_phi must be [{na}] (one entry per active index)")
         d_pos = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
         d_mass = torch.empty(self.n, dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
@@ -339,17 +355,19 @@ class _Gravity(torch.autograd.Function):
     def forward(ctx, pos, mass, soft, is_sink, active, kw):
         tree = Tree(pos.detach(), mass.detach(), soft.detach(), is_sink, **kw)
         acc, phi = tree.accel(active)
+        tree.check()  # an out-of-range active index raises here instead of leaving rows unwritten
         ctx.tree = tree
         ctx.active = active
         return acc, phi
 
     @staticmethod
     def backward(ctx, g_acc, g_phi):
+        # the tree lives as long as the autograd graph holds ctx, so that a
+        # second backward (retain_graph=True) reuses it
         tree = ctx.tree
         g_acc = torch.zeros_like(g_acc) if g_acc is None else g_acc.contiguous()
         g_phi = None if g_phi is None else g_phi.contiguous()
         d_pos, d_mass = tree.accel_vjp(ctx.active, g_acc, g_phi)
-        tree.close()
         return d_pos, d_mass, None, None, None, None
 
 
@@ -362,6 +380,30 @@ def tidal_timestep(tidal: torch.Tensor, eta: float) -> torch.Tensor:
         rc = _load().sfg_tidal_timestep(tidal.data_ptr(), n, float(eta), dt.data_ptr(), _stream(tidal.device))
     _check(rc, "sfg_tidal_timestep")
     return dt
+
+
+def hermite_step(pos, vel, mass, soft, dt: float, *, G: float = 1.0, theta: float = 0.5, leaf_size: int = 16,
+                 group_size: int = 32, quadrupole: bool = True):
+    """One modified Hermite step of sink particles (sfg_hermite_step, Sec. 2.3):
+    returns (pos1, vel1) [n][3]; both field + jerk evaluations run in the
+    library on a tree of these particles alone."""
+    pos = _dev(pos, torch.float64, "pos")
+    vel = _dev(vel, torch.float64, "vel")
+    mass = _dev(mass, torch.float64, "mass")
+    soft = _dev(soft, torch.float64, "soft")
+    n = pos.shape[0]
+    if pos.dim() != 2 or pos.shape[1] != 3 or tuple(vel.shape) != (n, 3):
+        raise ValueError("pos and vel must be [n, 3]")
+    if mass.shape != (n,) or soft.shape != (n,):
+        raise ValueError("mass and soft must be [n]")
+    prm = default_params(G=G, theta=theta, leaf_size=leaf_size, group_size=group_size, quadrupole=quadrupole)
+    x1 = torch.empty_like(pos)
+    v1 = torch.empty_like(vel)
+    with torch.cuda.device(pos.device):
+        rc = _load().sfg_hermite_step(pos.data_ptr(), vel.data_ptr(), mass.data_ptr(), soft.data_ptr(), n,
+                                      ctypes.byref(prm), float(dt), x1.data_ptr(), v1.data_ptr(), _stream(pos.device))
+    _check(rc, "sfg_hermite_step")
+    return x1, v1
 
 
 def fp32_peak(device=None) -> dict:
@@ -380,4 +422,5 @@ def gravity(pos, mass, soft, is_sink=None, active=None, **kw):
     return _Gravity.apply(pos, mass, soft, is_sink, active, kw)
 
 
-__all__ = ["Tree", "gravity", "Params", "Stats", "SfgError", "default_params", "library_path"]
+__all__ = ["Tree", "gravity", "hermite_step", "tidal_timestep", "fp32_peak", "Params", "Stats", "SfgError",
+           "default_params", "library_path"]

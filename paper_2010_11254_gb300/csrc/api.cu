@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sfg_internal.cuh"
@@ -71,6 +72,44 @@ static void release(sfg_tree *T)
     for (void *p : ptrs) dev_free(t, p, t->stream);
     cudaStreamSynchronize(t->stream);
     delete T;
+}
+
+// Modified Hermite step of sink particles (Sec. 2.3): prediction from the
+// start of the step, and the correction from both evaluations (velocity
+// first; the position uses the corrected velocity).  Elementwise over the
+// 3 n components.
+__global__ void k_hermite_predict(int64_t n3, double dt, const double *x0, const double *v0, const double *a0,
+                                  const double *j0, double *xp, double *vp)
+{
+    const double h2 = dt * dt / 2.0, h3 = dt * dt * dt / 6.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n3; q += (int64_t)gridDim.x * blockDim.x) {
+        xp[q] = x0[q] + dt * v0[q] + h2 * a0[q] + h3 * j0[q];
+        vp[q] = v0[q] + dt * a0[q] + h2 * j0[q];
+    }
+}
+
+__global__ void k_hermite_correct(int64_t n3, double dt, const double *x0, const double *v0, const double *a0,
+                                  const double *j0, const double *a1, const double *j1, double *x1, double *v1)
+{
+    const double h1 = dt / 2.0, h12 = dt * dt / 12.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n3; q += (int64_t)gridDim.x * blockDim.x) {
+        const double v = v0[q] + h1 * (a1[q] + a0[q]) + h12 * (j0[q] - j1[q]);
+        x1[q] = x0[q] + h1 * (v + v0[q]) + h12 * (a0[q] - a1[q]);
+        v1[q] = v;
+    }
+}
+
+// Field and jerk of every particle of a sinks-only tree at (x, v).
+static int sink_pass(const double *x, const double *v, const double *mass, const double *soft, const uint8_t *ones,
+                     int64_t n, const sfg_params *p, cudaStream_t s, double *acc, double *jerk)
+{
+    sfg_tree *T = nullptr;
+    int rc = sfg_build(x, mass, soft, ones, n, p, (void *)s, &T);
+    if (rc != SFG_OK) return rc;
+    rc = sfg_accel_jerk(T, v, nullptr, n, acc, nullptr, jerk, (void *)s);
+    const int st = rc == SFG_OK ? sfg_get_status(T) : rc;
+    sfg_free(T);
+    return st;
 }
 
 extern "C" {
@@ -285,6 +324,40 @@ int sfg_tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, v
     if (n < 0 || (n > 0 && (!tidal || !dt)) || !(eta > 0.0) || !std::isfinite(eta)) return SFG_EINVAL;
     cudaGetLastError();
     return sfg::tidal_timestep(tidal, n, eta, dt, (cudaStream_t)stream);
+}
+
+int sfg_hermite_step(const double *pos, const double *vel, const double *mass, const double *soft, int64_t n,
+                     const sfg_params *params, double dt, double *pos_out, double *vel_out, void *stream)
+{
+    if (!pos || !vel || !mass || !soft || !pos_out || !vel_out || n <= 0 || n >= 0x7fffffffLL ||
+        !std::isfinite(dt))
+        return SFG_EINVAL;
+    cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b3 = sizeof(double) * 3 * (size_t)n;
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, 6 * b3 + (size_t)n, s) != cudaSuccess) {
+        cudaGetLastError();
+        return SFG_ENOMEM;
+    }
+    double *a0 = (double *)buf, *j0 = a0 + 3 * n, *a1 = j0 + 3 * n, *j1 = a1 + 3 * n, *xp = j1 + 3 * n,
+           *vp = xp + 3 * n;
+    uint8_t *ones = (uint8_t *)(vp + 3 * n);
+    const int64_t n3 = 3 * n;
+    const int BT = 256, grid = (int)std::min<int64_t>((n3 + BT - 1) / BT, 4096);
+    int rc = cudaMemsetAsync(ones, 1, (size_t)n, s) == cudaSuccess ? SFG_OK : cuda_fail(cudaGetLastError());
+    if (rc == SFG_OK) rc = sink_pass(pos, vel, mass, soft, ones, n, params, s, a0, j0);
+    if (rc == SFG_OK) {
+        k_hermite_predict<<<grid, BT, 0, s>>>(n3, dt, pos, vel, a0, j0, xp, vp);
+        rc = sink_pass(xp, vp, mass, soft, ones, n, params, s, a1, j1);
+    }
+    if (rc == SFG_OK) {
+        k_hermite_correct<<<grid, BT, 0, s>>>(n3, dt, pos, vel, a0, j0, a1, j1, pos_out, vel_out);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    cudaFreeAsync(buf, s);
+    return rc;
 }
 
 int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,

@@ -1662,6 +1662,7 @@ constexpr size_t ST_OFF_VALS = st_al(ST_OFF_KEYS + (size_t)SFG_STATIC_MAX_N * 8)
 constexpr size_t ST_BYTES = st_al(ST_OFF_VALS + (size_t)SFG_STATIC_MAX_N * 4);
 static_assert(ST_OFF_KEYS % 256 == 0 && ST_OFF_VALS % 256 == 0 && ST_OFF_HIST % 256 == 0, "scratch alignment");
 static_assert(sizeof(Frame) <= 256 && SCAN_NB * 4 <= 4096, "scratch layout");
+static_assert(ST_BYTES == 6556928, "the array size stated in sfg.h");
 
 static __device__ __align__(256) unsigned char g_sort_scratch[ST_BYTES];
 
@@ -1723,6 +1724,7 @@ extern "C" int sfg_sort_keys_static(const double *pos, int64_t n, uint64_t *key_
     using namespace sfg;
     if (!pos || !key_out || !order_out || n <= 0) return SFG_EINVAL;
     if (n > SFG_STATIC_MAX_N) return SFG_EINVAL;
+    cudaGetLastError(); // a launch error reported at the end is this call's own
     unsigned char *base = nullptr;
     int rc = static_scratch(&base);
     if (rc != SFG_OK) return rc;
@@ -1737,9 +1739,12 @@ extern "C" int sfg_sort_keys_static(const double *pos, int64_t n, uint64_t *key_
     uint64_t *kb = (uint64_t *)(base + ST_OFF_KEYS);
     uint32_t *vb = (uint32_t *)(base + ST_OFF_VALS);
     const int nb = (nn + RS_TILE - 1) / RS_TILE;
-    int *scratch_status = hn + 1; // k_frame reports an unsupported extent here; positions must be finite
+    // k_frame flags an unsupported extent (subnormal or beyond 2^1023) here;
+    // the call does not read it back, so such inputs give unspecified keys
+    int *scratch_status = hn + 1;
     int64_t *range = (int64_t *)(base + ST_OFF_RANGE);
     k_set_range<<<1, 1, 0, s>>>(range, n);
+    k_set_int<<<1, 1, 0, s>>>(scratch_status, 0);
     k_minmax_init<<<1, 32, 0, s>>>(mm, 1);
     k_minmax_pos<<<grid_for(nn, BT), BT, 0, s>>>(pos, nn, mm);
     k_frame<<<1, 1, 0, s>>>(mm, fr, 1, scratch_status);

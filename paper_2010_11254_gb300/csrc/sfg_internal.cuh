@@ -103,6 +103,8 @@ struct Tree {
     int *lm = nullptr;
     int2 *lr = nullptr;
     long long lm_cap = 0, lr_cap = 0;
+    int *lp = nullptr; // the P2P ranges expanded to sorted particle ranks
+    long long lp_cap = 0;
     int64_t *la = nullptr; // copy of that active index array
     int64_t la_cap = 0, la_n = -1;
     bool la_all = false;   // it was NULL (every particle)

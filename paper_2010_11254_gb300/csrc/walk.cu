@@ -132,6 +132,9 @@ struct WalkParams {
     const long long *lmo, *lro;
     int *lm;
     int2 *lr;
+    // the P2P ranges expanded to sorted particle ranks: first entry per group, entries
+    const long long *lpo;
+    const int *lp;
     // adjoint
     const float4 *cot; // per distinct target: (cot_a, cot_phi)
     double *gpart;     // [n][4] sorted: d_pos, d_mass
@@ -159,6 +162,19 @@ struct Tgt {
     double rel_ag, rel_L0, rel_cell2;
     float rel_agf, rel_GL0f, rel_cell2f; // FP32 roundings of alpha min|g|, G L0^2, cell^2
 };
+
+// Exact FP32 -> FP64 conversion of a normal or zero float (every result of
+// the flush-to-zero FP32 arithmetic here), on the integer pipes; infinities
+// and NaN take the hardware conversion.
+__device__ __forceinline__ double f64_of(float x)
+{
+    const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu;
+    if (e == 255u) return (double)x;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
 
 // ------------------------------------------------------------ kernels ----
 // Softened kernel of support h at separation r (u = r/h < 1 here):
@@ -1085,6 +1101,7 @@ __device__ void commit_staged(const WalkParams &P, const WalkState &W, int g, in
         c[4] = W.tot_pn;
         bm = (long long)atomicAdd(&P.lbump[0], (unsigned long long)W.tot_m);
         br = (long long)atomicAdd(&P.lbump[1], (unsigned long long)W.tot_leaf);
+        atomicAdd(&P.lbump[6], (unsigned long long)W.tot_p);
         atomicMax(&P.lbump[4], (unsigned long long)W.tot_m);
         atomicMax(&P.lbump[5], (unsigned long long)max(ns, nn));
         const bool staged = W.tot_m <= P.stg_cap_m && ns <= P.stg_cap_r && nn <= P.stg_cap_r;
@@ -2165,6 +2182,8 @@ __device__ __forceinline__ int eval_item(const WalkParams &P, EvalSmem &S, int g
     return cloud;
 }
 
+#include "eval_chunks.cuh"
+
 // Persistent warps take work items (longest first) from an atomic counter.
 // resident blocks per SM of the evaluation kernel (the tidal mode carries
 // seven more accumulators per lane)
@@ -2215,36 +2234,41 @@ __global__ void k_lscan_reduce(const int *cnt, const int *d_ng, long long *bsum)
     const int ng = *d_ng;
     const int chunk = (ng + LS_NB - 1) / LS_NB;
     const int b0 = min(ng, (int)blockIdx.x * chunk), b1 = min(ng, b0 + chunk);
-    long long sm = 0, sr = 0;
+    long long sm = 0, sr = 0, sp = 0;
     for (int g = b0 + threadIdx.x; g < b1; g += blockDim.x) {
         const int *c = cnt + NCNT * (size_t)g;
         sm += c[0];
         sr += c[1] + c[3];
+        sp += (long long)c[2] + c[4];
     }
     sm = block_sum64(sm, sh);
     sr = block_sum64(sr, sh);
+    sp = block_sum64(sp, sh);
     if (threadIdx.x == 0) {
         bsum[blockIdx.x] = sm;
         bsum[LS_NB + blockIdx.x] = sr;
+        bsum[2 * LS_NB + blockIdx.x] = sp;
     }
 }
 
 __global__ void k_lscan_top(long long *bsum, const int *d_ng, long long *lmo, long long *lro, long long *tot)
 {
     if (threadIdx.x != 0) return;
-    long long rm = 0, rr = 0;
+    long long rm = 0, rr = 0, rp = 0;
     for (int b = 0; b < LS_NB; b++) {
         long long m = bsum[b], r = bsum[LS_NB + b];
         bsum[b] = rm;
         bsum[LS_NB + b] = rr;
         rm += m;
         rr += r;
+        rp += bsum[2 * LS_NB + b];
     }
     const int ng = *d_ng;
     lmo[ng] = rm;
     lro[ng] = rr;
     tot[0] = rm;
     tot[1] = rr;
+    tot[2] = rp;
 }
 
 __global__ void k_lscan_down(const int *cnt, const int *d_ng, const long long *bsum, long long *lmo, long long *lro)
@@ -2595,6 +2619,7 @@ struct Work {
     double ralpha, rG;
     int *cnt, *kcnt, *is_split, *soff, *ioff, *gdone, *hist; // cnt: NCNT list sizes per group
     long long *lmo, *lro; // stored lists: first P2M entry / first P2P range of every group (exclusive scans)
+    long long *lpo;       // expanded P2P lists: first particle entry of every group
     int2 *items;
     float4 *part_a;
     double *part_phi;
@@ -2606,12 +2631,12 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
 {
     const size_t n = (size_t)t->n;
     const int retry_warps = num_sms() * WALK_WARPS;
-    const size_t NB = 24;
+    const size_t NB = 25;
     size_t sz[NB] = {n * 4, (n + 1) * 4, n * 4, n * 4, n * 4, (n + 1) * 4, (n + PSLOTS) * 4, scan1p_bytes((int)n),
                      n * 8, (size_t)retry_warps * GSTK * 8, n * 16, n * 8,
                      n * 4 * NCNT, n * 4, n * 4, (n + 1) * 4, (n + 1) * 4, n * 4,
                      (size_t)PSLOTS * 32 * 16, (size_t)PSLOTS * 32 * 8, 64 * 4, (n + PSLOTS) * 8,
-                     (n + 1) * 8, (n + 1) * 8};
+                     (n + 1) * 8, (n + 1) * 8, (n + 1) * 8};
     size_t total = 0;
     for (size_t b : sz) total += align_up(b);
     bool fresh = false;
@@ -2657,6 +2682,7 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     w.items = (int2 *)ptr[21];
     w.lmo = (long long *)ptr[22];
     w.lro = (long long *)ptr[23];
+    w.lpo = (long long *)ptr[24];
     return SFG_OK;
 }
 
@@ -2744,6 +2770,8 @@ static void fill_params(Tree *t, Work &w, WalkParams &P)
     P.lro = w.lro;
     P.lm = t->lm;
     P.lr = t->lr;
+    P.lp = t->lp;
+    P.lpo = w.lpo;
     P.stg_m = nullptr;
     P.stg_r = nullptr;
     P.stg_cap_m = P.stg_cap_r = P.stg_main_warps = 0;
@@ -2903,6 +2931,7 @@ struct ListHint {
 };
 static std::mutex g_hint_mu;
 static ListHint g_hint;
+constexpr int LBUMP = 8; // list reservations and totals ([6]: P2P particle entries, [7]: expansion cursor)
 constexpr int STG_MIN_M = 1024, STG_MIN_R = 256, STG_MAX_M = 1 << 16, STG_MAX_R = 1 << 14;
 
 static void update_hint(long long tot_m, long long tot_r, int64_t n_active, long long max_m, long long max_r)
@@ -2927,6 +2956,65 @@ static void update_hint(long long tot_m, long long tot_r, int64_t n_active, long
 // place every group's lists contiguously and a second walk writes them.
 // Without a hint (the first lists of the process) a counting walk gives the
 // sizes instead of the one-pass walk.
+// Expanded P2P lists: every group's softened, then Newtonian, particle
+// ranges written out as sorted particle ranks (one warp per group, at an
+// offset reserved with one atomic), so that the evaluation stages a source
+// with one index load.
+__global__ void k_expand_p2p(const int *cnt, const long long *lro, const int2 *lr, const int *d_ng, int *lp,
+                             long long *lpo, unsigned long long *bump, long long cap, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+    const int ng = *d_ng;
+    for (int g = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); g < ng; g += nw) {
+        const int *c = cnt + NCNT * (size_t)g;
+        const int nr = c[1] + c[3];
+        const long long np = (long long)c[2] + c[4];
+        long long off = 0;
+        if (lane == 0) off = (long long)atomicAdd(bump, (unsigned long long)np);
+        off = __shfl_sync(FULL, off, 0);
+        if (lane == 0) lpo[g] = off;
+        if (off + np > cap) {
+            if (lane == 0) atomicOr(status, ST_ETIMEOUT);
+            continue;
+        }
+        const int2 *rr = lr + lro[g];
+        long long pos = off;
+        for (int b = 0; b < nr; b += 32) {
+            const int k = b + lane;
+            const int2 r = k < nr ? rr[k] : make_int2(0, 0);
+            int inc = r.y;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const long long start = pos + inc - r.y;
+            const int nb = min(32, nr - b);
+            for (int q = 0; q < nb; q++) {
+                const int first = __shfl_sync(FULL, r.x, q), n_q = __shfl_sync(FULL, r.y, q);
+                const long long st = __shfl_sync(FULL, start, q);
+                for (int e = lane; e < n_q; e += 32) lp[st + e] = first + e;
+            }
+            pos += __shfl_sync(FULL, inc, 31);
+        }
+    }
+}
+
+// Expand the stored P2P ranges (np_total particle entries over all groups).
+static int expand_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, long long np_total)
+{
+    int rc = grow_buffer(t, (void **)&t->lp, &t->lp_cap, std::max(np_total, 1ll), sizeof(int), s);
+    if (rc) return rc;
+    SFG_CUDA_OK(cudaMemsetAsync(t->d_lbump + LBUMP - 1, 0, sizeof(unsigned long long), s));
+    k_expand_p2p<<<num_sms() * 8, 256, 0, s>>>(w.cnt, w.lro, t->lr, P.d_ngroups, t->lp, w.lpo,
+                                               t->d_lbump + LBUMP - 1, t->lp_cap, t->d_status);
+    t->n_launch += 1;
+    P.lp = t->lp;
+    P.lpo = w.lpo;
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
+}
+
 static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t n_active)
 {
     t->lists_ok = false;
@@ -2936,11 +3024,11 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
         h = g_hint;
     }
     if (!t->d_lscan) {
-        t->d_lscan = (long long *)dev_alloc(t, sizeof(long long) * (2 * LS_NB + 2), s);
+        t->d_lscan = (long long *)dev_alloc(t, sizeof(long long) * (3 * LS_NB + 3), s);
         if (!t->d_lscan) return SFG_ENOMEM;
     }
     if (!t->d_lbump) {
-        t->d_lbump = (unsigned long long *)dev_alloc(t, 6 * sizeof(unsigned long long), s);
+        t->d_lbump = (unsigned long long *)dev_alloc(t, LBUMP * sizeof(unsigned long long), s);
         if (!t->d_lbump) return SFG_ENOMEM;
     }
     const double na = (double)std::max<int64_t>(n_active, 1);
@@ -2979,13 +3067,13 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
         P.lbump = t->d_lbump;
         P.lmo_w = w.lmo;
         P.lro_w = w.lro;
-        SFG_CUDA_OK(cudaMemsetAsync(t->d_lbump, 0, 6 * sizeof(unsigned long long), s));
+        SFG_CUDA_OK(cudaMemsetAsync(t->d_lbump, 0, LBUMP * sizeof(unsigned long long), s));
         SFG_CUDA_OK(cudaMemsetAsync(w.cnt, 0, sizeof(int) * NCNT * (size_t)t->n, s));
         SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
         P.dbg_counts = w.cnt;
         launch_walk<MODE_LIST1>(t, P, s);
         P.dbg_counts = nullptr;
-        unsigned long long b[6] = {0, 0, 0, 0, 0, 0};
+        unsigned long long b[LBUMP] = {0};
         SFG_CUDA_OK(cudaMemcpyAsync(b, t->d_lbump, sizeof(b), cudaMemcpyDeviceToHost, s));
         SFG_CUDA_OK(cudaStreamSynchronize(s));
         update_hint((long long)b[0], (long long)b[1], n_active, (long long)b[4], (long long)b[5]);
@@ -2997,19 +3085,18 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
             }
             P.rlist = nullptr;
             t->list_walks = 1;
-            SFG_CUDA_OK(cudaGetLastError());
-            return SFG_OK;
+            return expand_lists(t, w, P, s, (long long)b[6]);
         }
         P.rlist = nullptr;
         counted = true; // the sizes in w.cnt are exact
     }
     if (!counted) count_lists(t, w, P, s);
-    long long *tot_d = t->d_lscan + 2 * LS_NB;
+    long long *tot_d = t->d_lscan + 3 * LS_NB;
     k_lscan_reduce<<<LS_NB, 256, 0, s>>>(w.cnt, P.d_ngroups, t->d_lscan);
     k_lscan_top<<<1, 32, 0, s>>>(t->d_lscan, P.d_ngroups, w.lmo, w.lro, tot_d);
     k_lscan_down<<<LS_NB, 256, 0, s>>>(w.cnt, P.d_ngroups, t->d_lscan, w.lmo, w.lro);
     t->n_launch += 3;
-    long long tot[2] = {0, 0};
+    long long tot[3] = {0, 0, 0};
     SFG_CUDA_OK(cudaMemcpyAsync(tot, tot_d, sizeof(tot), cudaMemcpyDeviceToHost, s));
     SFG_CUDA_OK(cudaStreamSynchronize(s));
     if (!counted) update_hint(tot[0], tot[1], n_active, -1, -1);
@@ -3022,8 +3109,7 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
     SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
     launch_walk<MODE_LIST>(t, P, s);
     t->list_walks = 2;
-    SFG_CUDA_OK(cudaGetLastError());
-    return SFG_OK;
+    return expand_lists(t, w, P, s, tot[2]);
 }
 
 // Record the active set the stored lists belong to (and that the groups now
@@ -3069,12 +3155,32 @@ static int lists_match(Tree *t, const int64_t *active, int64_t n_active, cudaStr
     return SFG_OK;
 }
 
+// Resident blocks per SM of a kernel at its launch shape (looked up once).
+template <class F>
+static int resident_blocks(F kernel, int threads)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
 template <int MODE>
 static void launch_eval(Tree *t, WalkParams &P, cudaStream_t s)
 {
-    const int blocks = num_sms() * eval_minb(MODE);
-    if (t->prm.quadrupole) k_eval<true, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
-    else k_eval<false, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
+    if constexpr (MODE == MODE_EVAL || MODE == MODE_VJP) {
+        // forward and adjoint: source chunks, several targets per lane
+        static const int bq = resident_blocks(k_eval_chunks<true, MODE>, CK_WARPS * 32);
+        static const int bm = resident_blocks(k_eval_chunks<false, MODE>, CK_WARPS * 32);
+        if (t->prm.quadrupole) k_eval_chunks<true, MODE><<<num_sms() * bq, CK_WARPS * 32, 0, s>>>(P);
+        else k_eval_chunks<false, MODE><<<num_sms() * bm, CK_WARPS * 32, 0, s>>>(P);
+    } else {
+        const int blocks = num_sms() * eval_minb(MODE);
+        if (t->prm.quadrupole) k_eval<true, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
+        else k_eval<false, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
+    }
     t->n_launch += 1;
 }
 
@@ -3514,18 +3620,6 @@ __global__ void k_gleaf_prep(const double *gnode, const int32_t *nnchild, int nn
     }
 }
 
-// Exact FP32 -> FP64 conversion of a normal or zero float (every result of
-// the flush-to-zero FP32 arithmetic here), on the integer pipes; infinities
-// and NaN take the hardware conversion.
-__device__ __forceinline__ double f64_of(float x)
-{
-    const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu;
-    if (e == 255u) return (double)x;
-    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    if (e == 0u) return __longlong_as_double((long long)sign);
-    return __longlong_as_double(
-        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
-}
 
 // Per particle (sorted rank k): its leaf's centre-of-mass and quadrupole
 // gradient terms added to its pair gradients, times G, written in input

@@ -147,3 +147,52 @@ def test_autograd_function_matches_direct_calls():
     d_pos, d_mass = _gpu_vjp(c, act.cpu().numpy(), ca, cp, 0.6)
     np.testing.assert_allclose(gp.cpu().numpy(), d_pos, rtol=0, atol=1e-6 * np.abs(d_pos).max())
     np.testing.assert_allclose(gm.cpu().numpy(), d_mass, rtol=0, atol=1e-6 * np.abs(d_mass).max())
+
+
+def test_vjp_adjoint_workload_full_size():
+    """The adjoint workload at its stated size: the uniform recipe with 2^20
+    cells and 128 sinks, every particle active, N(0,1) cotangents, theta 0.5.
+    (1) The GPU VJP of all rows against the oracle's analytic FP64 VJP;
+    (2) the GPU VJP of 4096 sampled rows against FP64 central differences
+    (step 1e-6) of the oracle's frozen-list field of the same rows, at 64
+    sampled particle coordinates and 16 masses."""
+    c = gen.adjoint_cloud(1 << 20, n_sink=128, seed=gen.CONFIG_SEED[3])
+    rows = np.arange(c.n)
+    ca, cp = gen.cotangents(c.n, seed=gen.CONFIG_SEED[3] + 7)
+    g_pos, g_mass = _gpu_vjp(c, rows, ca, cp, 0.5)
+    o = oracle_tree(c, 16)
+    o.walk(rows, 32, 0.5)
+    o_pos, o_mass = o.vjp(rows, ca, cp)
+    _close(g_pos, o_pos)
+    _close(g_mass, o_mass)
+    # finite differences on a row sample (the frozen-list loss of 4096 rows)
+    rng = np.random.default_rng(11)
+    sub = np.sort(rng.choice(c.n, 4096, replace=False))
+    s_pos, s_mass = _gpu_vjp(c, sub, ca[sub], cp[sub], 0.5)
+    o.walk(sub, 32, 0.5)
+    h = 1e-6
+    scale = np.abs(s_pos).max()
+
+    def loss(p, m):
+        a, ph = o.eval_frozen(p, m, sub)
+        return float((a * ca[sub]).sum() + (ph * cp[sub]).sum())
+
+    # half the probes on the sampled rows themselves, half anywhere
+    pick = np.concatenate([rng.choice(sub, 32, replace=False), rng.choice(c.n, 32, replace=False)])
+    for k in pick:
+        ax = int(rng.integers(0, 3))
+        pp = c.pos.copy()
+        pp[k, ax] += h
+        lp = loss(pp, c.mass)
+        pp[k, ax] -= 2 * h
+        lm = loss(pp, c.mass)
+        assert abs((lp - lm) / (2 * h) - s_pos[k, ax]) <= VJP_TOL * scale
+    mscale = np.abs(s_mass).max()
+    for k in pick[::4]:
+        mm = c.mass.copy()
+        hm = 1e-6 * c.mass[k]
+        mm[k] += hm
+        lp = loss(c.pos, mm)
+        mm[k] -= 2 * hm
+        lm = loss(c.pos, mm)
+        assert abs((lp - lm) / (2 * hm) - s_mass[k]) <= VJP_TOL * mscale

@@ -50,6 +50,26 @@ def test_static_key_sort_matches_build_on_two_calls():
         tree.close()
 
 
+def test_static_key_sort_at_the_array_capacity():
+    """n = SFG_STATIC_MAX_N fills every region of the fixed array exactly."""
+    import torch
+    sfg, sort_static = _lib()
+    c = gen.uniform_cloud(SFG_STATIC_MAX_N, seed=23, n_sink=0)
+    pos = torch.from_numpy(c.pos).cuda()
+    tree = sfg.Tree(pos, torch.from_numpy(c.mass).cuda(), torch.from_numpy(c.soft).cuda())
+    want_k, want_o = tree.export(sfg.FIELD_KEYS), tree.export(sfg.FIELD_ORDER)
+    tree.close()
+    for _ in range(2):
+        keys = torch.empty(c.n, dtype=torch.int64, device="cuda")
+        order = torch.empty(c.n, dtype=torch.int32, device="cuda")
+        rc = sort_static(pos.data_ptr(), c.n, keys.data_ptr(), order.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert rc == sfg.SFG_OK
+        np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint64), want_k)
+        np.testing.assert_array_equal(order.cpu().numpy(), want_o)
+
+
 def test_static_key_sort_rejects_sizes_beyond_its_array():
     import torch
     sfg, sort_static = _lib()
