@@ -25,6 +25,11 @@
  *     passed the call.  sfg_build copies what the tree needs.  Outputs are
  *     allocated by the caller.
  *   - A tree must be used from one stream at a time (it keeps a workspace).
+ *   - CUDA graphs: a tree allocates its grow-only workspaces on the first call
+ *     of each kind (sfg_accel, sfg_accel_vjp, per-cloud timing) that needs
+ *     them.  Make one such call eagerly before capturing a stream into a
+ *     graph; a call that would allocate while its stream is being captured
+ *     returns SFG_EINVAL instead (the memory would belong to the graph).
  *   - Return value: SFG_OK or an SFG_E* status.  Nothing aborts or exits.
  *     Errors that only the device can see (non-finite inputs, an index out
  *     of range, a traversal buffer overflow that survived its retry) are
@@ -270,6 +275,23 @@ int sfg_tidal_timestep(const double *tidal, int64_t n, double eta, double *dt, v
  * Duplicate rows sum.  Errors as for sfg_accel. */
 int sfg_accel_vjp(sfg_tree *tree, const int64_t *active_idx, int64_t n_active, const double *cot_a,
                   const double *cot_phi, double *d_pos, double *d_mass, void *stream);
+
+/* Split the evaluation of one tree across `world` processes (one per GPU):
+ * later sfg_accel, sfg_accel_vjp, sfg_accel_tidal, sfg_accel_jerk and
+ * sfg_sink_timestep calls of this tree evaluate only share `rank` of the
+ * groups of their active set -- the contiguous run of groups
+ * [floor(ng rank / world), floor(ng (rank + 1) / world)) in Morton order,
+ * ng the call's group count -- so that every group is evaluated by exactly
+ * one process.  Rows of targets in other shares come out as zeros (+inf for
+ * sfg_sink_timestep), and the adjoint's d_pos, d_mass hold this share's
+ * part of the sums, so the sum over all processes of each output (one
+ * all-reduce) is the unsplit result.  The paper's runs split the tree work
+ * over MPI ranks by domain decomposition (Sec. 2.2); here every process
+ * holds the whole tree (built from the same particles) and the split is
+ * over groups of targets.  Interaction counts in sfg_get_stats cover this
+ * share.  (rank, world) = (0, 1) evaluates everything (the default).
+ * Errors: SFG_EINVAL (NULL tree, world < 1 or > 65536, rank outside [0, world)). */
+int sfg_set_group_share(sfg_tree *tree, int rank, int world);
 
 /* Turn per-phase CUDA-event timing of later calls on (1) or off (0).  Timing
  * records a few events per call on the call's stream; it does not synchronize. */

@@ -112,6 +112,8 @@ def _load():
         lib.sfg_cloud_times.restype = i32
         lib.sfg_set_timing.argtypes = [vp, i32]
         lib.sfg_set_timing.restype = i32
+        lib.sfg_set_group_share.argtypes = [vp, i32, i32]
+        lib.sfg_set_group_share.restype = i32
         lib.sfg_get_status.argtypes = [vp]
         lib.sfg_get_status.restype = i32
         lib.sfg_free.argtypes = [vp]
@@ -292,6 +294,11 @@ class Tree:
         s = Stats()
         _check(_load().sfg_get_stats(self._h, ctypes.byref(s)), "sfg_get_stats")
         return s.as_dict()
+
+    def set_group_share(self, rank: int, world: int):
+        """Evaluate only share `rank` of `world` of the groups in later calls
+        (sfg_set_group_share); (0, 1) evaluates everything."""
+        _check(_load().sfg_set_group_share(self._h, int(rank), int(world)), "sfg_set_group_share")
 
     def set_timing(self, on: bool = True):
         _check(_load().sfg_set_timing(self._h, int(bool(on))), "sfg_set_timing")

@@ -426,6 +426,14 @@ int sfg_cloud_times(sfg_tree *tree, float *fwd_ms, float *vjp_ms)
     return SFG_OK;
 }
 
+int sfg_set_group_share(sfg_tree *tree, int rank, int world)
+{
+    if (!tree || world < 1 || world > 65536 || rank < 0 || rank >= world) return SFG_EINVAL;
+    tree->t.share_rank = rank;
+    tree->t.share_world = world;
+    return SFG_OK;
+}
+
 int sfg_set_timing(sfg_tree *tree, int on)
 {
     if (!tree) return SFG_EINVAL;

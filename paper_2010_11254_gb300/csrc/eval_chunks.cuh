@@ -38,6 +38,26 @@ struct ChunkSmem {
     float4 tI[32];         // targets: h, 1/h, rank bits, sink flag
 };
 
+// Source-side adjoint sums are added to FP32 gradient buffers with vector
+// reductions (one 16- or 8-byte reduction for four or two values); every
+// source of a list is visited once per group, so each entry sums one
+// contribution per group that lists it (per particle, the groups whose P2P
+// lists hold it; per node, the groups that accept it).  The buffers are added
+// to the FP64 gradients before the node push-down.  Node gradients take 12
+// floats per node: gM, gcom[3] | gQ xx yy zz xy | gQ xz yz, -, - .
+constexpr int GN32 = 12;
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
 // Lane layout and group frame of one work item.
 struct ChunkGroup {
     int T, TL, R, A, tl, s, tfirst, cloud;
@@ -498,10 +518,12 @@ __device__ __forceinline__ void chunk_vjp_nodes(const WalkParams &P, const Chunk
         }
         const int id = G.active ? S.sN[base + G.tl] : -1;
         if (id >= 0) {
-            double *dst = P.gnode + 10 * (size_t)id;
-#pragma unroll
-            for (int q = 0; q < NA; q++)
-                if (acc[q] != 0.f) atomicAdd(dst + q, f64_of(acc[q]));
+            float *dst = P.gnode32 + GN32 * (size_t)id;
+            red_add_v4(dst, acc[0], acc[1], acc[2], acc[3]);
+            if (QUAD) {
+                red_add_v4(dst + 4, acc[4 % NA], acc[5 % NA], acc[6 % NA], acc[7 % NA]);
+                red_add_v2(dst + 8, acc[8 % NA], acc[9 % NA]);
+            }
         }
     }
 }
@@ -648,7 +670,7 @@ __device__ __forceinline__ void chunk_vjp_deferred(ChunkSmem &S, const ChunkGrou
     }
 }
 
-// FP64 atomics of the lane's block sums for the sources it holds.
+// The lane's block sums added to the gradients of the sources it holds.
 __device__ __forceinline__ void chunk_vjp_flush(const WalkParams &P, const ChunkSmem &S, const ChunkGroup &G,
                                                 const float (&a)[CK_M][4])
 {
@@ -656,12 +678,7 @@ __device__ __forceinline__ void chunk_vjp_flush(const WalkParams &P, const Chunk
 #pragma unroll
     for (int b = 0; b < CK_M; b++) {
         const int id = S.sN[(G.s * CK_M + b) * G.TL + G.tl];
-        if (id >= 0) {
-            double *dst = P.gpart + 4 * (size_t)id;
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (a[b][q] != 0.f) atomicAdd(dst + q, f64_of(a[b][q]));
-        }
+        if (id >= 0) red_add_v4(P.gpart32 + 4 * (size_t)id, a[b][0], a[b][1], a[b][2], a[b][3]);
     }
 }
 
@@ -727,7 +744,7 @@ __device__ __forceinline__ int chunk_item(const WalkParams &P, ChunkSmem &S, int
                 chunk_fwd_nodes<QUAD, NT>(S, G, X, ax, ay, az, pt);
 #pragma unroll
                 for (int i = 0; i < NT; i++) {
-                    ph[i] += f64_of(pt[i]);
+                    ph[i] += (double)pt[i];
                     pt[i] = 0.f;
                 }
             }
@@ -736,9 +753,10 @@ __device__ __forceinline__ int chunk_item(const WalkParams &P, ChunkSmem &S, int
     }
     // ---- P2P: the group's expanded list, softened particles then Newtonian ones;
     // ranks one chunk ahead of their records, which run one chunk ahead of the evaluation
-    const int *lp = P.lp + P.lpo[g];
+    const long long lpo = P.lpo[g]; // < 0: the expansion had no room (reported on the status word)
+    const int *lp = P.lp + (lpo < 0 ? 0 : lpo);
 #pragma unroll 1
-    for (int list = 0; list < 2; list++) {
+    for (int list = 0; list < (lpo < 0 ? 0 : 2); list++) {
         const bool soft = list == 0;
         const int *lq = soft ? lp : lp + nps;
         int e0, e1;
@@ -788,7 +806,7 @@ __device__ __forceinline__ int chunk_item(const WalkParams &P, ChunkSmem &S, int
                 }
 #pragma unroll
                 for (int i = 0; i < NT; i++) {
-                    ph[i] += f64_of(pt[i]);
+                    ph[i] += (double)pt[i];
                     pt[i] = 0.f;
                 }
             }
@@ -831,9 +849,9 @@ __device__ __forceinline__ int chunk_item(const WalkParams &P, ChunkSmem &S, int
     if (VJP) {
         if (own) {
             double *dst = P.gpart + 4 * (size_t)P.tgt[G.tfirst + lane];
-            atomicAdd(dst, f64_of(rx));
-            atomicAdd(dst + 1, f64_of(ry));
-            atomicAdd(dst + 2, f64_of(rz));
+            atomicAdd(dst, (double)rx);
+            atomicAdd(dst + 1, (double)ry);
+            atomicAdd(dst + 2, (double)rz);
         }
     } else if (K == 1) {
         if (own) {
@@ -882,8 +900,12 @@ __device__ __forceinline__ int chunk_item(const WalkParams &P, ChunkSmem &S, int
 }
 
 // Persistent warps take work items (longest first) from an atomic counter.
+// resident blocks per SM the register budget must allow: the adjoint keeps
+// more per-lane state (cotangents, source sums) than the forward
+constexpr int chunk_minb(int mode) { return mode == MODE_VJP ? 4 : 5; }
+
 template <bool QUAD, int MODE>
-__global__ void __launch_bounds__(CK_WARPS * 32, 4) k_eval_chunks(WalkParams P)
+__global__ void __launch_bounds__(CK_WARPS * 32, chunk_minb(MODE)) k_eval_chunks(WalkParams P)
 {
     __shared__ ChunkSmem sm[CK_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

@@ -104,7 +104,8 @@ struct Tree {
     int2 *lr = nullptr;
     long long lm_cap = 0, lr_cap = 0;
     int *lp = nullptr; // the P2P ranges expanded to sorted particle ranks
-    long long lp_cap = 0;
+    long long lp_cap = 0, lp_need = 0; // capacity; entries of the kept lists
+    bool lp_ready = false;             // lp holds the kept lists' expansion
     int64_t *la = nullptr; // copy of that active index array
     int64_t la_cap = 0, la_n = -1;
     bool la_all = false;   // it was NULL (every particle)
@@ -121,6 +122,8 @@ struct Tree {
     void *lstage = nullptr;                // one-pass list walk: per-warp staging
     size_t lstage_bytes = 0;
     int list_walks = 0;                    // walks of the last stored-list build (1 or 2)
+    // calls evaluate only the share of the groups of process share_rank of share_world
+    int share_rank = 0, share_world = 1;
     std::unordered_set<void *> live; // every device allocation still held
 };
 

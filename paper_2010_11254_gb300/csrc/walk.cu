@@ -139,6 +139,8 @@ struct WalkParams {
     const float4 *cot; // per distinct target: (cot_a, cot_phi)
     double *gpart;     // [n][4] sorted: d_pos, d_mass
     double *gnode;     // [nn][10]: gM, gcom[3], gQ sym[6]
+    float *gpart32;    // [n][4]: source-side sums of the chunked evaluation (added to gpart)
+    float *gnode32;    // [nn][12]: gM, gcom[3], gQ[6], -, - (added to gnode)
 };
 
 // Target-lane state of one group.
@@ -2384,12 +2386,22 @@ __device__ inline long long group_iters(const int *cnt, int tc, int g, int4 wt)
 }
 
 // Total estimated cost of all groups (one 64-bit atomic per warp).
-__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
-                             unsigned long long *total)
+// The share [g0, g1) of the groups a tree evaluates when its calls are split
+// across `world` processes (rank `rank` of them): contiguous runs of groups
+// in Morton order, by group count.
+__host__ __device__ inline void group_share(int ng, int rank, int world, int &g0, int &g1)
 {
-    int ng = *d_ngroups;
+    g0 = (int)((long long)ng * rank / world);
+    g1 = (int)((long long)ng * (rank + 1) / world);
+}
+
+__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
+                             unsigned long long *total, int2 share)
+{
+    int g0, g1;
+    group_share(*d_ngroups, share.x, share.y, g0, g1);
     unsigned long long acc = 0;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+    for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += gridDim.x * blockDim.x)
         acc += (unsigned long long)group_iters(cnt, gtab[g].y, g, wt);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
@@ -2401,12 +2413,19 @@ __global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngro
 // every item stays small next to a warp's share (longest-first scheduling
 // then balances the rest).
 __global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
-                              const unsigned long long *total, long long warps, int *kcnt, int *is_split)
+                              const unsigned long long *total, long long warps, int *kcnt, int *is_split,
+                              int2 share)
 {
-    int ng = *d_ngroups;
+    int ng = *d_ngroups, g0, g1;
+    group_share(ng, share.x, share.y, g0, g1);
     long long C = (long long)(*total / (unsigned long long)(SPLIT_PER_WARP * warps));
     if (C < SPLIT_ITERS) C = SPLIT_ITERS;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        if (g < g0 || g >= g1) { // another process's share: no items
+            kcnt[g] = 0;
+            is_split[g] = 0;
+            continue;
+        }
         long long iters = group_iters(cnt, gtab[g].y, g, wt);
         long long k = (iters + C - 1) / C;
         int K = (int)(k < 1 ? 1 : (k > KMAX ? KMAX : k));
@@ -2429,7 +2448,7 @@ __global__ void k_item_hist(const int *cnt, const int2 *gtab, const int *kcnt, c
 {
     int ng = *d_ngroups;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        atomicAdd(&hist[cost_bucket(cnt, gtab, kcnt, g, wt)], kcnt[g]);
+        if (kcnt[g] > 0) atomicAdd(&hist[cost_bucket(cnt, gtab, kcnt, g, wt)], kcnt[g]);
 }
 
 __global__ void k_item_scan(int *hist)
@@ -2450,6 +2469,7 @@ __global__ void k_item_fill(const int *cnt, const int2 *gtab, const int *kcnt, c
     int ng = *d_ngroups;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         int K = kcnt[g];
+        if (K == 0) continue;
         int base = atomicAdd(&cursor[cost_bucket(cnt, gtab, kcnt, g, wt)], K);
         for (int k = 0; k < K; k++) items[base + k] = make_int2(g, k);
     }
@@ -2641,6 +2661,9 @@ static int get_work(Tree *t, cudaStream_t s, Work &w)
     for (size_t b : sz) total += align_up(b);
     bool fresh = false;
     if (t->ws_bytes < total) {
+        // allocated while a stream is captured, the workspace would belong to
+        // the graph: one call of the tree must come before capture
+        if (capturing(s)) return SFG_EINVAL;
         fresh = true;
         t->lists_ok = false; // the list sizes lived in the old workspace
         if (t->ws) dev_free(t, t->ws, s);
@@ -2839,6 +2862,7 @@ static int cloud_timer_begin(Tree *t, int which, cudaStream_t s, WalkParams &P)
 {
     const int C = t->nclouds;
     if (!t->d_ctime) {
+        if (capturing(s)) return SFG_EINVAL; // see get_work
         t->d_ctime = (unsigned long long *)dev_alloc(t, 2 * sizeof(unsigned long long) * (size_t)(C + 1), s);
         if (!t->d_ctime) return SFG_ENOMEM;
     }
@@ -2880,14 +2904,20 @@ static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s, i
     cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s);
     unsigned long long *total = t->d_counters + 7;
     cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
-    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total);
+    const int2 share = make_int2(t->share_rank, t->share_world);
+    k_item_total<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total, share);
     const long long warps = (long long)num_sms() * WALK_MINB * WALK_WARPS;
-    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total, warps, w.kcnt, w.is_split);
+    k_item_counts<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, d_ng, wt, total, warps, w.kcnt, w.is_split,
+                                                  share);
     w.sc.exclusive(w.is_split, w.soff, d_ng, n, t->d_status, s);
     k_item_cap<<<grid_for(n, BT), BT, 0, s>>>(w.soff, d_ng, w.kcnt);
     w.sc.exclusive(w.kcnt, w.ioff, d_ng, n, t->d_status, s);
     cudaMemsetAsync(w.gdone, 0, sizeof(int) * (size_t)n, s);
     cudaMemsetAsync(w.hist, 0, 32 * sizeof(int), s);
+    if (t->share_world > 1) { // rows of other processes' groups come out as zeros
+        cudaMemsetAsync(w.res_a, 0, sizeof(float4) * (size_t)n, s);
+        cudaMemsetAsync(w.res_phi, 0, sizeof(double) * (size_t)n, s);
+    }
     k_item_hist<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, wt, w.hist);
     k_item_scan<<<1, 32, 0, s>>>(w.hist);
     k_item_fill<<<grid_for(n, BT), BT, 0, s>>>(w.cnt, w.gtab, w.kcnt, d_ng, wt, w.hist, w.items);
@@ -2957,60 +2987,117 @@ static void update_hint(long long tot_m, long long tot_r, int64_t n_active, long
 // Without a hint (the first lists of the process) a counting walk gives the
 // sizes instead of the one-pass walk.
 // Expanded P2P lists: every group's softened, then Newtonian, particle
-// ranges written out as sorted particle ranks (one warp per group, at an
-// offset reserved with one atomic), so that the evaluation stages a source
-// with one index load.
-__global__ void k_expand_p2p(const int *cnt, const long long *lro, const int2 *lr, const int *d_ng, int *lp,
-                             long long *lpo, unsigned long long *bump, long long cap, int *status)
+// ranges written out as sorted particle ranks, so that the evaluation stages
+// a source with one index load.  k_lp_offsets reserves each group's space
+// (one atomic per group); k_expand_p2p then fills it one work item per warp,
+// each item its share of both lists (the split that balances the
+// evaluation balances this pass too: a few groups in dense clumps hold lists
+// of thousands of ranges).
+__global__ void k_lp_offsets(const int *cnt, const int *d_ng, long long *lpo, unsigned long long *bump, long long cap,
+                             int *status)
 {
-    const int lane = threadIdx.x & 31;
-    const int nw = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
     const int ng = *d_ng;
-    for (int g = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); g < ng; g += nw) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         const int *c = cnt + NCNT * (size_t)g;
-        const int nr = c[1] + c[3];
         const long long np = (long long)c[2] + c[4];
-        long long off = 0;
-        if (lane == 0) off = (long long)atomicAdd(bump, (unsigned long long)np);
-        off = __shfl_sync(FULL, off, 0);
-        if (lane == 0) lpo[g] = off;
+        const long long off = (long long)atomicAdd(bump, (unsigned long long)np);
         if (off + np > cap) {
-            if (lane == 0) atomicOr(status, ST_ETIMEOUT);
-            continue;
-        }
-        const int2 *rr = lr + lro[g];
-        long long pos = off;
-        for (int b = 0; b < nr; b += 32) {
-            const int k = b + lane;
-            const int2 r = k < nr ? rr[k] : make_int2(0, 0);
-            int inc = r.y;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += v;
-            }
-            const long long start = pos + inc - r.y;
-            const int nb = min(32, nr - b);
-            for (int q = 0; q < nb; q++) {
-                const int first = __shfl_sync(FULL, r.x, q), n_q = __shfl_sync(FULL, r.y, q);
-                const long long st = __shfl_sync(FULL, start, q);
-                for (int e = lane; e < n_q; e += 32) lp[st + e] = first + e;
-            }
-            pos += __shfl_sync(FULL, inc, 31);
+            atomicOr(status, ST_ETIMEOUT);
+            lpo[g] = -1;
+        } else {
+            lpo[g] = off;
         }
     }
 }
 
-// Expand the stored P2P ranges (np_total particle entries over all groups).
-static int expand_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, long long np_total)
+// Write particles [e0, e1) of a range list (nr ranges) to dst[e0..e1).
+__device__ __forceinline__ void expand_share(const int2 *rr, int nr, int e0, int e1, int *dst, int lane, int *status)
 {
-    int rc = grow_buffer(t, (void **)&t->lp, &t->lp_cap, std::max(np_total, 1ll), sizeof(int), s);
+    if (e0 >= e1) return;
+    // the range holding particle e0 (warp-wide prefix search, 32 ranges at a time)
+    int r = -1, before = 0;
+    for (int base = 0; base < nr && r < 0; base += 32) {
+        const int idx = base + lane;
+        const int c = idx < nr ? rr[idx].y : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned hit = __ballot_sync(FULL, idx < nr && before + incl > e0);
+        if (hit) {
+            const int L = __ffs(hit) - 1;
+            r = base + L;
+            before += __shfl_sync(FULL, incl - c, L);
+        } else {
+            before += __shfl_sync(FULL, incl, 31);
+        }
+    }
+    if (r < 0) { // the stored sizes disagree with the ranges
+        if (lane == 0) atomicOr(status, ST_ETIMEOUT);
+        return;
+    }
+    // ranges r, r + 1, ... starting at particle 'before', 32 at a time
+    for (int base = r; base < nr && before < e1; base += 32) {
+        const int idx = base + lane;
+        const int2 q = idx < nr ? rr[idx] : make_int2(0, 0);
+        int incl = q.y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int start = before + incl - q.y; // list position of this lane's range
+        const int nb = min(32, nr - base);
+        for (int k = 0; k < nb; k++) {
+            const int st = __shfl_sync(FULL, start, k), first = __shfl_sync(FULL, q.x, k),
+                      cn = __shfl_sync(FULL, q.y, k);
+            if (st >= e1) break;
+            const int a = max(st, e0), b = min(st + cn, e1);
+            for (int e = a + lane; e < b; e += 32) dst[e] = first + (e - st);
+        }
+        before += __shfl_sync(FULL, incl, 31);
+    }
+}
+
+__global__ void k_expand_p2p(WalkParams P, const int2 *lr, int *lp)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+    const int nwork = P.ioff[*P.d_ngroups];
+    for (int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); w < nwork; w += nw) {
+        const int2 it = P.items[w];
+        const int g = it.x, kk = it.y, K = P.kcnt[g];
+        const long long off = P.lpo[g];
+        if (off < 0) continue; // no room (reported by k_lp_offsets)
+        const int *c = P.lcnt + NCNT * (size_t)g;
+        const int2 *rr = lr + P.lro[g];
+        int *dst = lp + off;
+        for (int list = 0; list < 2; list++) {
+            const int np = c[2 + 2 * list];
+            const int nt = (np + 31) >> 5;
+            const int t0 = (int)((long long)nt * kk / K), t1 = (int)((long long)nt * (kk + 1) / K);
+            if (t0 < t1)
+                expand_share(list == 0 ? rr : rr + c[1], c[1 + 2 * list], t0 * 32, min(np, t1 * 32),
+                             list == 0 ? dst : dst + c[2], lane, P.status);
+        }
+    }
+}
+
+// Expand the stored P2P ranges (np_total particle entries over all groups)
+// with the work items of the call.
+static int expand_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
+{
+    if (t->lp_ready) return SFG_OK;
+    int rc = grow_buffer(t, (void **)&t->lp, &t->lp_cap, std::max(t->lp_need, 1ll), sizeof(int), s);
     if (rc) return rc;
     SFG_CUDA_OK(cudaMemsetAsync(t->d_lbump + LBUMP - 1, 0, sizeof(unsigned long long), s));
-    k_expand_p2p<<<num_sms() * 8, 256, 0, s>>>(w.cnt, w.lro, t->lr, P.d_ngroups, t->lp, w.lpo,
-                                               t->d_lbump + LBUMP - 1, t->lp_cap, t->d_status);
-    t->n_launch += 1;
+    k_lp_offsets<<<grid_for(t->n, 256), 256, 0, s>>>(w.cnt, P.d_ngroups, w.lpo, t->d_lbump + LBUMP - 1,
+                                                      t->lp_cap, t->d_status);
     P.lp = t->lp;
     P.lpo = w.lpo;
+    k_expand_p2p<<<num_sms() * 8, 256, 0, s>>>(P, t->lr, t->lp);
+    t->n_launch += 2;
+    t->lp_ready = true;
     SFG_CUDA_OK(cudaGetLastError());
     return SFG_OK;
 }
@@ -3085,7 +3172,10 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
             }
             P.rlist = nullptr;
             t->list_walks = 1;
-            return expand_lists(t, w, P, s, (long long)b[6]);
+            t->lp_need = (long long)b[6];
+            t->lp_ready = false;
+            SFG_CUDA_OK(cudaGetLastError());
+            return SFG_OK;
         }
         P.rlist = nullptr;
         counted = true; // the sizes in w.cnt are exact
@@ -3109,7 +3199,10 @@ static int build_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int64_t 
     SFG_CUDA_OK(cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s));
     launch_walk<MODE_LIST>(t, P, s);
     t->list_walks = 2;
-    return expand_lists(t, w, P, s, tot[2]);
+    t->lp_need = tot[2];
+    t->lp_ready = false;
+    SFG_CUDA_OK(cudaGetLastError());
+    return SFG_OK;
 }
 
 // Record the active set the stored lists belong to (and that the groups now
@@ -3207,6 +3300,8 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
         items_from_counts(t, w, P, s, WT_EVAL);
+        rc = expand_lists(t, w, P, s);
+        if (rc) return rc;
     } else {
         t->lists_ok = false; // the counting walk below overwrites their sizes
         make_items(t, w, P, s);
@@ -3541,10 +3636,12 @@ __global__ void k_cot_pack(const double *cotd, const int *d_U, float4 *cot)
 // Node gradients (gM, g_com, g_Q sym) -> per-unit-mass form (gM, v = g_com / M,
 // g_Q).  A massless node's own centre-of-mass and quadrupole terms vanish
 // (its moments do not move to first order when a member's mass leaves zero).
-__global__ void k_gnode_unit(double *gnode, const double *nM, int nn)
+__global__ void k_gnode_unit(double *gnode, const float *gnode32, const double *nM, int nn)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
         double *g = gnode + 10 * (size_t)i;
+        const float *g32 = gnode32 + 12 * (size_t)i;
+        for (int a = 0; a < 10; a++) g[a] += (double)g32[a];
         double M = nM[i];
         if (M > 0.0) {
             for (int a = 1; a < 4; a++) g[a] /= M;
@@ -3626,7 +3723,8 @@ __global__ void k_gleaf_prep(const double *gnode, const int32_t *nnchild, int nn
 // order.  With s = x - com (member offset from the leaf's centre of mass):
 // d/dx += m (v + 6 S s - 2 tr(S) s), d/dm += g_M + v.s + 3 s.S s - tr(S) s.s.
 __global__ void k_gleaf_out(const float4 *gl, const float4 *E0, const float4 *pw, const int32_t *pleaf,
-                            const double *gpart, const int32_t *order, int n, double G, double *d_pos, double *d_mass)
+                            const double *gpart, const float4 *gpart32, const int32_t *order, int n, double G,
+                            double *d_pos, double *d_mass)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = pleaf[k];
@@ -3646,10 +3744,11 @@ __global__ void k_gleaf_out(const float4 *gl, const float4 *E0, const float4 *pw
         const float m = x.w;
         const double2 p01 = *reinterpret_cast<const double2 *>(gpart + 4 * (size_t)k);
         const double2 p23 = *reinterpret_cast<const double2 *>(gpart + 4 * (size_t)k + 2);
-        double o0 = p01.x + f64_of(m * fmaf(6.f, Ss0, fmaf(-2.f * tr, s0, v0)));
-        double o1 = p01.y + f64_of(m * fmaf(6.f, Ss1, fmaf(-2.f * tr, s1, v1)));
-        double o2 = p23.x + f64_of(m * fmaf(6.f, Ss2, fmaf(-2.f * tr, s2, v2)));
-        double o3 = p23.y + (g0 + f64_of(tm));
+        const float4 q = gpart32[k];
+        double o0 = (p01.x + f64_of(q.x)) + f64_of(m * fmaf(6.f, Ss0, fmaf(-2.f * tr, s0, v0)));
+        double o1 = (p01.y + f64_of(q.y)) + f64_of(m * fmaf(6.f, Ss1, fmaf(-2.f * tr, s1, v1)));
+        double o2 = (p23.x + f64_of(q.z)) + f64_of(m * fmaf(6.f, Ss2, fmaf(-2.f * tr, s2, v2)));
+        double o3 = (p23.y + f64_of(q.w)) + (g0 + f64_of(tm));
         if (G != 1.0) {
             o0 *= G;
             o1 *= G;
@@ -3695,10 +3794,13 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
     if (rc) return rc;
     if (!t->lists_ok) match = false; // a new workspace: the list sizes were dropped with the old one
     // adjoint workspace: cotd [n][4] f64, cot [n] float4, gpart [n][4] f64, gnode [nn][10] f64,
-    // gl [nn][3] float4
+    // gl [nn][3] float4, gpart32 [n][4] f32, gnode32 [nn][12] f32
     size_t need = align_up(32 * (size_t)n) + align_up(16 * (size_t)n) + align_up(32 * (size_t)n) +
-                  align_up(80 * (size_t)nn) + align_up(48 * (size_t)nn);
+                  align_up(80 * (size_t)nn) + align_up(48 * (size_t)nn) + align_up(16 * (size_t)n) +
+                  align_up(48 * (size_t)nn);
     if (t->ws2_bytes < need) {
+        // allocated while a stream is captured, the buffer would belong to the graph
+        if (capturing(s)) return SFG_EINVAL;
         if (t->ws2) dev_free(t, t->ws2, s);
         t->ws2 = dev_alloc(t, need, s);
         if (!t->ws2) {
@@ -3717,15 +3819,23 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
     double *gnode = (double *)p;
     p += align_up(80 * (size_t)nn);
     float4 *gl = (float4 *)p;
+    p += align_up(48 * (size_t)nn);
+    float *gpart32 = (float *)p;
+    p += align_up(16 * (size_t)n);
+    float *gnode32 = (float *)p;
     SFG_CUDA_OK(cudaMemsetAsync(cotd, 0, 32 * (size_t)n, s));
     SFG_CUDA_OK(cudaMemsetAsync(gpart, 0, 32 * (size_t)n, s));
     SFG_CUDA_OK(cudaMemsetAsync(gnode, 0, 80 * (size_t)nn, s));
+    SFG_CUDA_OK(cudaMemsetAsync(gpart32, 0, 16 * (size_t)n, s));
+    SFG_CUDA_OK(cudaMemsetAsync(gnode32, 0, 48 * (size_t)nn, s));
     if (n_active > 0) {
         k_cot_rows<<<grid_for(n_active, BT), BT, 0, s>>>(active, n_active, n, t->rank, w.pre, cot_a, cot_phi, cotd);
         k_cot_pack<<<grid_for(n, BT), BT, 0, s>>>(cotd, w.pre + n, cot);
         P.cot = cot;
         P.gpart = gpart;
         P.gnode = gnode;
+        P.gpart32 = gpart32;
+        P.gnode32 = gnode32;
         if (lists) {
             if (!match) {
                 rc = build_lists(t, w, P, s, n_active);
@@ -3734,6 +3844,8 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
                 if (rc) return rc;
             }
             items_from_counts(t, w, P, s, WT_VJP);
+            rc = expand_lists(t, w, P, s);
+            if (rc) return rc;
         } else {
             t->lists_ok = false;
             make_items(t, w, P, s);
@@ -3746,7 +3858,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
         if (lists) launch_eval<MODE_VJP>(t, P, s);
         else launch_walk<MODE_VJP>(t, P, s);
         ph_end(t, PH_VJP_WALK, s);
-        k_gnode_unit<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nM, nn);
+        k_gnode_unit<<<grid_for(nn, BT), BT, 0, s>>>(gnode, gnode32, t->nM, nn);
         t->n_launch += 4;
         // levels 1..top hold few nodes each: one block pushes them in one launch
         int top = 0;
@@ -3765,8 +3877,8 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
             }
         }
         k_gleaf_prep<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nnchild, nn, gl);
-        k_gleaf_out<<<grid_for(n, BT), BT, 0, s>>>(gl, t->E0, t->pw, t->pleaf, gpart, t->order, n, t->prm.G, d_pos,
-                                                   d_mass);
+        k_gleaf_out<<<grid_for(n, BT), BT, 0, s>>>(gl, t->E0, t->pw, t->pleaf, gpart, (const float4 *)gpart32,
+                                                   t->order, n, t->prm.G, d_pos, d_mass);
         t->n_launch += 1;
     } else {
         k_unpermute<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->order, n, t->prm.G, d_pos, d_mass);

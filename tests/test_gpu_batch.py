@@ -154,6 +154,28 @@ def test_cuda_graph_replay_equals_eager():
     t.close()
 
 
+def test_capture_before_any_eager_call_is_rejected():
+    """A tree allocates its workspace on its first call; a first call made
+    while the stream is being captured into a CUDA graph is refused with
+    SFG_EINVAL (the memory would belong to the graph), and eager calls work
+    afterwards."""
+    import torch
+    import paper_2010_11254_gb300 as sfg
+    c = gen.uniform_cloud(3000, seed=12)
+    pos, mass, soft, sink = (torch.from_numpy(x).cuda() for x in (c.pos, c.mass, c.soft, c.is_sink))
+    t = sfg.Tree(pos, mass, soft, sink, theta=0.6, store_lists=False)
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(sfg.SfgError) as e:
+        with torch.cuda.graph(g):
+            t.accel(None)
+    assert e.value.code == sfg.SFG_EINVAL
+    torch.cuda.synchronize()
+    a, p = t.accel(None)
+    t.check()
+    assert torch.isfinite(a).all()
+    t.close()
+
+
 def test_batch_many_clouds_small_leaves():
     """64 clouds (sizes 1 .. 5000, log-uniform) at leaf size 8 and group size
     16: per-cloud structure bit-exact and the field of every cloud equal to
