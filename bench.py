@@ -58,9 +58,9 @@ FLOP_VJP_P2M_QUAD = 137
 # dram__bytes_write.sum, one ncu capture), valid only for the evaluation
 # sources (sha256 over walk.cu and eval_chunks.cuh), workload and launch shape
 # they were taken on; otherwise the line reports null.
-EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16,
+EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 2,
                 "fwd": None, "vjp": None}
-EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh")
+EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh", "eval_chunks_body.inc")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
 BUILD_BYTES_PER_PARTICLE = 576
@@ -330,8 +330,8 @@ def run_ensemble(args, rank, world, dist, dev):
     pos, mass, soft, sink, ca, cp = (torch.from_numpy(x).to(dev) for x in cat + [ca_h, cp_h])
     theta = ENSEMBLE["theta"]
     tuned = autotune.tune(pos, mass, soft, sink, offsets=off, cot_a=ca, cot_phi=cp, theta=theta)
-    kw = dict(theta=theta, leaf_size=tuned["leaf_size"], group_size=tuned["group_size"], quadrupole=True,
-              offsets=off)
+    kw = dict(theta=theta, leaf_size=tuned["leaf_size"], group_size=tuned["group_size"],
+              list_depth=tuned.get("list_depth", 0), quadrupole=True, offsets=off)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
@@ -451,6 +451,7 @@ def run_ensemble(args, rank, world, dist, dev):
         "config": {"workload": "ensemble-256", "n_clouds": len(clouds), "n_particles": n,
                    "n_min": min(c.n for c in clouds), "n_max": max(c.n for c in clouds), "active": "all",
                    "theta": theta, "leaf_size": kw["leaf_size"], "group_size": kw["group_size"],
+                   "list_depth": kw["list_depth"],
                    "autotune": {"key": tuned["key"], "cached": tuned["cached"], "trials": tuned.get("trials")},
                    "l2": "flushed (512 MB write) before every timed step"},
         "phases_ms": {"build": round(st["build_ms"], 4), "fwd": round(st["fwd_ms"], 4),
@@ -517,15 +518,16 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     tuned = None
-    leaf, group = args.leaf_size, args.group_size
-    if leaf is None or group is None:
+    leaf, group, depth = args.leaf_size, args.group_size, args.list_depth
+    if leaf is None or group is None or depth is None:
         # launch shape from the autotuner (untimed; cached per GPU and workload class)
         from paper_2010_11254_gb300 import autotune
         tuned = autotune.tune(d_pos, d_mass, d_soft, d_sink, active=d_act, cot_a=d_ca, cot_phi=d_cp,
                               theta=wl["theta"])
         leaf = tuned["leaf_size"] if leaf is None else leaf
         group = tuned["group_size"] if group is None else group
-    kw = dict(theta=wl["theta"], leaf_size=leaf, group_size=group, quadrupole=True,
+        depth = tuned.get("list_depth", 0) if depth is None else depth
+    kw = dict(theta=wl["theta"], leaf_size=leaf, group_size=group, list_depth=depth, quadrupole=True,
               precision=args.precision, store_lists=bool(args.store_lists))
     lists = bool(args.store_lists) and args.precision == 0
     kname = "k_eval" if lists else "k_walk"
@@ -650,8 +652,9 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         return {"bound": "alu", "kernel": kernel, "achieved": round(a, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(a / peak, 4),
                 "traffic": EVAL_TRAFFIC[traffic_key] if (same_src and args.workload == EVAL_TRAFFIC["workload"]
-                                                          and (leaf, group) == (EVAL_TRAFFIC["leaf_size"],
-                                                                                EVAL_TRAFFIC["group_size"])) else None,
+                                                          and (leaf, group, depth or 2) == (
+                                                              EVAL_TRAFFIC["leaf_size"], EVAL_TRAFFIC["group_size"],
+                                                              EVAL_TRAFFIC["list_depth"])) else None,
                 "peak_source": peak_text,
                 "flops_per_launch": int(flops), "launch_ms": round(ms, 4), "flop_model": model}
 
@@ -671,7 +674,7 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         "dtype": "f32+f64" if args.precision == 0 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
                    "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"],
-                   "leaf_size": leaf, "group_size": group, "quadrupole": True,
+                   "leaf_size": leaf, "group_size": group, "list_depth": depth or 2, "quadrupole": True,
                    "precision": args.precision, "store_lists": bool(args.store_lists),
                    "autotune": None if tuned is None else {"key": tuned["key"], "cached": tuned["cached"],
                                                             "trials": tuned.get("trials")},
@@ -773,6 +776,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--leaf-size", type=int, default=None, help="default: the autotuner's choice")
     ap.add_argument("--group-size", type=int, default=None, help="default: the autotuner's choice")
+    ap.add_argument("--list-depth", type=int, default=None, choices=[1, 2, 4],
+                    help="evaluation chunk depth (sources staged per lane); default: the autotuner's choice")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     ap.add_argument("--opening-curve", action="store_true",

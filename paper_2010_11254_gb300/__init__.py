@@ -161,7 +161,7 @@ class Tree:
 
     def __init__(self, pos, mass, soft, is_sink=None, *, G: float = 1.0, theta: float = 0.5, leaf_size: int = 16,
                  group_size: int = 32, quadrupole: bool = True, precision: int = 0, store_lists: bool = True,
-                 offsets=None):
+                 list_depth: int = 0, offsets=None):
         """offsets (host sequence of n_clouds + 1 ints) builds one forest over an
         ensemble of independent clouds (sfg_build_batch).  store_lists: evaluate
         from interaction lists stored by one walk (the adjoint reuses the
@@ -182,7 +182,8 @@ class Tree:
         self.device = pos.device
         self.n = n
         self.params = default_params(G=G, theta=theta, leaf_size=leaf_size, group_size=group_size,
-                                     quadrupole=quadrupole, precision=precision, store_lists=store_lists)
+                                     quadrupole=quadrupole, precision=precision, store_lists=store_lists,
+                                     list_depth=list_depth)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             if offsets is None:

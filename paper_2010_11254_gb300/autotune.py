@@ -1,14 +1,15 @@
 """Autotuner for the launch-shape parameters of a workload.
 
 The tree's leaf size (N_leaf) and group size (targets sharing one walk) trade
-walk length against list length; the best pair depends on the particle
-distribution, the active fraction and the GPU.  ``tune`` builds the tree with
-each candidate pair on the caller's own data, times one forward + adjoint
-(CUDA events, after one warm-up), and returns the fastest pair.  Results are
-cached in a JSON file keyed by GPU name and a coarse workload class, so a
-repeated workload pays the search once.  The interaction-list buffers are
-fixed by design (tiles of 32 sources, 64-entry lists per warp), so there is
-no list depth to tune.
+walk length against list length, and the list-buffer depth (the sources
+each active lane stages per chunk of the evaluation: 1, 2 or 4) trades the
+per-chunk costs against shared memory per warp; the best choice depends on
+the particle distribution, the active fraction and the GPU.  ``tune`` builds
+the tree with each candidate on the caller's own data, times one forward +
+adjoint (CUDA events, after one warm-up), and returns the fastest: first
+over (leaf size, group size) at depth 2, then over the depths at the best
+pair.  Results are cached in a JSON file keyed by GPU name and a coarse
+workload class, so a repeated workload pays the search once.
 """
 from __future__ import annotations
 
@@ -19,6 +20,8 @@ import os
 import torch
 
 DEFAULT_CANDIDATES = ((8, 16), (8, 32), (16, 16), (16, 32), (32, 16), (32, 32))
+DEPTHS = (1, 2, 4)
+KEY_VERSION = "v2"  # cache entries carry the list depth
 
 
 def _cache_path() -> str:
@@ -29,7 +32,7 @@ def workload_key(n: int, n_clouds: int, n_active: int, theta: float) -> str:
     name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
     frac = max(n_active, 1) / max(n, 1)
     return (f"{name}|n=2^{round(math.log2(max(n, 1)))}|clouds=2^{round(math.log2(max(n_clouds, 1)))}"
-            f"|active=2^{round(math.log2(frac))}|theta={theta:g}")
+            f"|active=2^{round(math.log2(frac))}|theta={theta:g}|{KEY_VERSION}")
 
 
 def _load_cache(path: str) -> dict:
@@ -41,8 +44,9 @@ def _load_cache(path: str) -> dict:
 
 
 def tune(pos, mass, soft, is_sink=None, *, offsets=None, active=None, cot_a=None, cot_phi=None, theta=0.5,
-         candidates=DEFAULT_CANDIDATES, use_cache: bool = True, cache_path: str | None = None) -> dict:
-    """Fastest (leaf_size, group_size) for this workload: {"leaf_size", "group_size", "ms", "key", "trials"}."""
+         candidates=DEFAULT_CANDIDATES, depths=DEPTHS, use_cache: bool = True, cache_path: str | None = None) -> dict:
+    """Fastest (leaf_size, group_size, list_depth) for this workload:
+    {"leaf_size", "group_size", "list_depth", "ms", "key", "trials"}."""
     from . import Tree
     n = pos.shape[0]
     n_active = n if active is None else active.numel()
@@ -56,13 +60,15 @@ def tune(pos, mass, soft, is_sink=None, *, offsets=None, active=None, cot_a=None
         cot_a = torch.ones((n_active, 3), dtype=torch.float64, device=pos.device)
     trials = []
     stream = torch.cuda.current_stream(pos.device)
-    for leaf, group in candidates:
+
+    def trial(leaf, group, depth):
         best = float("inf")
         for rep in range(2):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            t = Tree(pos, mass, soft, is_sink, theta=theta, leaf_size=leaf, group_size=group, offsets=offsets)
+            t = Tree(pos, mass, soft, is_sink, theta=theta, leaf_size=leaf, group_size=group, list_depth=depth,
+                     offsets=offsets)
             t.accel(active)
             t.accel_vjp(active, cot_a, cot_phi)
             e1.record(stream)
@@ -70,9 +76,19 @@ def tune(pos, mass, soft, is_sink=None, *, offsets=None, active=None, cot_a=None
             t.close()
             if rep:  # the first pass warms up allocations and caches
                 best = min(best, e0.elapsed_time(e1))
-        trials.append({"leaf_size": leaf, "group_size": group, "ms": best})
+        trials.append({"leaf_size": leaf, "group_size": group, "list_depth": depth, "ms": best})
+        return trials[-1]
+
+    first = 2 if 2 in depths else depths[0]
+    for leaf, group in candidates:
+        trial(leaf, group, first)
     win = min(trials, key=lambda r: r["ms"])
-    out = {"leaf_size": win["leaf_size"], "group_size": win["group_size"], "ms": win["ms"], "trials": trials}
+    for depth in depths:
+        if depth != first:
+            trial(win["leaf_size"], win["group_size"], depth)
+    win = min(trials, key=lambda r: r["ms"])
+    out = {"leaf_size": win["leaf_size"], "group_size": win["group_size"], "list_depth": win["list_depth"],
+           "ms": win["ms"], "trials": trials}
     if use_cache:
         cache[key] = out
         try:

@@ -223,6 +223,7 @@ static int build_forest(const double *pos, const double *mass, const double *sof
     else sfg_default_params(&p);
     if (!(isfinite(p.G)) || !(p.theta >= 0.0) || !isfinite(p.theta) || p.leaf_size < 1 || p.leaf_size > 256 ||
         p.group_size < 1 || p.group_size > 32 || (p.quadrupole != 0 && p.quadrupole != 1) ||
+        (p.list_depth != 0 && p.list_depth != 1 && p.list_depth != 2 && p.list_depth != 4) ||
         (p.precision != 0 && p.precision != 1) || (p.alloc && !p.free))
         return SFG_EINVAL;
     cudaGetLastError();

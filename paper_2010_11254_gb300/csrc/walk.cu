@@ -29,6 +29,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "sfg_internal.cuh"
@@ -3037,7 +3038,9 @@ __device__ __forceinline__ void expand_share(const int2 *rr, int nr, int e0, int
         if (lane == 0) atomicOr(status, ST_ETIMEOUT);
         return;
     }
-    // ranges r, r + 1, ... starting at particle 'before', 32 at a time
+    // ranges r, r + 1, ... starting at particle 'before', 32 at a time: each
+    // lane writes every 32nd output of the batch's span and finds its range by
+    // a binary search over the batch's list positions
     for (int base = r; base < nr && before < e1; base += 32) {
         const int idx = base + lane;
         const int2 q = idx < nr ? rr[idx] : make_int2(0, 0);
@@ -3048,14 +3051,20 @@ __device__ __forceinline__ void expand_share(const int2 *rr, int nr, int e0, int
         }
         const int start = before + incl - q.y; // list position of this lane's range
         const int nb = min(32, nr - base);
-        for (int k = 0; k < nb; k++) {
-            const int st = __shfl_sync(FULL, start, k), first = __shfl_sync(FULL, q.x, k),
-                      cn = __shfl_sync(FULL, q.y, k);
-            if (st >= e1) break;
-            const int a = max(st, e0), b = min(st + cn, e1);
-            for (int e = a + lane; e < b; e += 32) dst[e] = first + (e - st);
+        const int end = before + __shfl_sync(FULL, incl, 31);
+        const int lo = max(before, e0), hi = min(end, e1);
+        for (int eb = lo; eb < hi; eb += 32) {
+            const int e = eb + lane;
+            int k = 0; // the last range of the batch starting at or before e
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = k + step;
+                const int sc = __shfl_sync(FULL, start, c & 31);
+                if (c < nb && sc <= e) k = c;
+            }
+            const int first = __shfl_sync(FULL, q.x, k), st = __shfl_sync(FULL, start, k);
+            if (e < hi) dst[e] = first + (e - st);
         }
-        before += __shfl_sync(FULL, incl, 31);
+        before = end;
     }
 }
 
@@ -3248,27 +3257,53 @@ static int lists_match(Tree *t, const int64_t *active, int64_t n_active, cudaStr
     return SFG_OK;
 }
 
-// Resident blocks per SM of a kernel at its launch shape (looked up once).
+// Resident blocks per SM of a kernel at its launch shape (looked up once per
+// kernel and device).
 template <class F>
 static int resident_blocks(F kernel, int threads)
 {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void *, int>, int>> seen;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair((const void *)kernel, dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const auto &e : seen)
+            if (e.first == key) return e.second;
+    }
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) {
         cudaGetLastError();
         b = 1;
     }
+    std::lock_guard<std::mutex> lk(mu);
+    seen.push_back(std::make_pair(key, b));
     return b;
+}
+
+// One persistent launch of a chunked evaluation kernel (quadrupole or
+// monopole variant), its grid filling every SM to the kernel's occupancy.
+template <int MODE, class FQ, class FM>
+static void launch_chunks(FQ kq, FM km, int warps, Tree *t, WalkParams &P, cudaStream_t s)
+{
+    const int threads = warps * 32;
+    if (t->prm.quadrupole) kq<<<num_sms() * resident_blocks(kq, threads), threads, 0, s>>>(P);
+    else km<<<num_sms() * resident_blocks(km, threads), threads, 0, s>>>(P);
 }
 
 template <int MODE>
 static void launch_eval(Tree *t, WalkParams &P, cudaStream_t s)
 {
     if constexpr (MODE == MODE_EVAL || MODE == MODE_VJP) {
-        // forward and adjoint: source chunks, several targets per lane
-        static const int bq = resident_blocks(k_eval_chunks<true, MODE>, CK_WARPS * 32);
-        static const int bm = resident_blocks(k_eval_chunks<false, MODE>, CK_WARPS * 32);
-        if (t->prm.quadrupole) k_eval_chunks<true, MODE><<<num_sms() * bq, CK_WARPS * 32, 0, s>>>(P);
-        else k_eval_chunks<false, MODE><<<num_sms() * bm, CK_WARPS * 32, 0, s>>>(P);
+        // forward and adjoint: source chunks of the tree's depth, two targets per lane
+        const int depth = t->prm.list_depth == 0 ? 2 : t->prm.list_depth;
+        if (depth == 1) launch_chunks<MODE>(ck1::k_eval_chunks<true, MODE>, ck1::k_eval_chunks<false, MODE>,
+                                            ck1::CK_WARPS, t, P, s);
+        else if (depth == 4) launch_chunks<MODE>(ck4::k_eval_chunks<true, MODE>, ck4::k_eval_chunks<false, MODE>,
+                                                 ck4::CK_WARPS, t, P, s);
+        else launch_chunks<MODE>(ck2::k_eval_chunks<true, MODE>, ck2::k_eval_chunks<false, MODE>, ck2::CK_WARPS, t,
+                                 P, s);
     } else {
         const int blocks = num_sms() * eval_minb(MODE);
         if (t->prm.quadrupole) k_eval<true, MODE><<<blocks, EVAL_WARPS * 32, 0, s>>>(P);
@@ -3723,8 +3758,7 @@ __global__ void k_gleaf_prep(const double *gnode, const int32_t *nnchild, int nn
 // order.  With s = x - com (member offset from the leaf's centre of mass):
 // d/dx += m (v + 6 S s - 2 tr(S) s), d/dm += g_M + v.s + 3 s.S s - tr(S) s.s.
 __global__ void k_gleaf_out(const float4 *gl, const float4 *E0, const float4 *pw, const int32_t *pleaf,
-                            const double *gpart, const float4 *gpart32, const int32_t *order, int n, double G,
-                            double *d_pos, double *d_mass)
+                            double *gpart, const float4 *gpart32, int n, double G)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = pleaf[k];
@@ -3755,24 +3789,26 @@ __global__ void k_gleaf_out(const float4 *gl, const float4 *E0, const float4 *pw
             o2 *= G;
             o3 *= G;
         }
-        const int r = order[k];
-        d_pos[3 * (size_t)r] = o0;
-        d_pos[3 * (size_t)r + 1] = o1;
-        d_pos[3 * (size_t)r + 2] = o2;
-        d_mass[r] = o3;
+        // in place, sorted order (coalesced); k_gather_out writes the input order
+        *reinterpret_cast<double2 *>(gpart + 4 * (size_t)k) = make_double2(o0, o1);
+        *reinterpret_cast<double2 *>(gpart + 4 * (size_t)k + 2) = make_double2(o2, o3);
     }
 }
 
-__global__ void k_unpermute(const double *gpart, const int32_t *order, int n, double G, double *d_pos,
-                            double *d_mass)
+// Input-order outputs from the sorted per-particle results: a gather, so that
+// the caller's arrays are written coalesced (scattered 24- and 8-byte writes
+// into them cost partial-sector read-modify-writes).
+__global__ void k_gather_out(const double *gsorted, const int32_t *rank, int n, double scale, double *d_pos,
+                             double *d_mass)
 {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        int i = order[r];
-        const double *g = gpart + 4 * (size_t)r;
-        d_pos[3 * (size_t)i] = G * g[0];
-        d_pos[3 * (size_t)i + 1] = G * g[1];
-        d_pos[3 * (size_t)i + 2] = G * g[2];
-        d_mass[i] = G * g[3];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const size_t k = (size_t)rank[i];
+        const double2 a = *reinterpret_cast<const double2 *>(gsorted + 4 * k);
+        const double2 b = *reinterpret_cast<const double2 *>(gsorted + 4 * k + 2);
+        d_pos[3 * (size_t)i] = scale * a.x;
+        d_pos[3 * (size_t)i + 1] = scale * a.y;
+        d_pos[3 * (size_t)i + 2] = scale * b.x;
+        d_mass[i] = scale * b.y;
     }
 }
 
@@ -3877,11 +3913,12 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
             }
         }
         k_gleaf_prep<<<grid_for(nn, BT), BT, 0, s>>>(gnode, t->nnchild, nn, gl);
-        k_gleaf_out<<<grid_for(n, BT), BT, 0, s>>>(gl, t->E0, t->pw, t->pleaf, gpart, (const float4 *)gpart32,
-                                                   t->order, n, t->prm.G, d_pos, d_mass);
-        t->n_launch += 1;
+        k_gleaf_out<<<grid_for(n, BT), BT, 0, s>>>(gl, t->E0, t->pw, t->pleaf, gpart, (const float4 *)gpart32, n,
+                                                   t->prm.G);
+        k_gather_out<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->rank, n, 1.0, d_pos, d_mass);
+        t->n_launch += 2;
     } else {
-        k_unpermute<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->order, n, t->prm.G, d_pos, d_mass);
+        k_gather_out<<<grid_for(n, BT), BT, 0, s>>>(gpart, t->rank, n, t->prm.G, d_pos, d_mass);
     }
     t->n_launch += 1;
     ph_end(t, PH_VJP, s);

@@ -15,12 +15,12 @@ FORCE_P99 = 2e-4
 PHI_MAX = 1e-6
 
 
-def _run(c, active, theta, leaf_size=16, group_size=32, quad=True, check_lists=True, G=1.0):
+def _run(c, active, theta, leaf_size=16, group_size=32, quad=True, check_lists=True, G=1.0, list_depth=0):
     import torch
     import paper_2010_11254_gb300 as sfg
     pos, mass, soft, sink = to_dev(c, torch)
     t = sfg.Tree(pos, mass, soft, sink, theta=theta, leaf_size=leaf_size, group_size=group_size, quadrupole=quad,
-                 G=G)
+                 G=G, list_depth=list_depth)
     act = torch.from_numpy(np.asarray(active, np.int64)).cuda()
     acc, phi = t.accel(act)
     assert t.status() == sfg.SFG_OK
@@ -76,6 +76,17 @@ def test_leaf_and_group_sizes(leaf_size, group_size):
     c = gen.uniform_cloud(6000, seed=2, n_sink=9)
     act = gen.active_subset(c.n, 0.4, seed=3)
     acc, phi, ao, po, _ = _run(c, act, 0.5, leaf_size=leaf_size, group_size=group_size)
+    _check_fields(acc, phi, ao, po)
+
+
+@pytest.mark.parametrize("list_depth", [1, 2, 4])
+@pytest.mark.parametrize("group_size", [5, 16, 32])
+def test_list_depths(list_depth, group_size):
+    """Every evaluation chunk depth, with groups whose target counts give
+    slices of 1..16 lanes (padding slots and absent targets included)."""
+    c = gen.clumpy_cloud(1 << 14, n_clumps=16, n_sink=12, seed=24)
+    act = gen.active_subset(c.n, 0.3, seed=25)
+    acc, phi, ao, po, _ = _run(c, act, 0.5, group_size=group_size, list_depth=list_depth, check_lists=False)
     _check_fields(acc, phi, ao, po)
 
 

@@ -13,12 +13,12 @@ pytestmark = pytest.mark.gpu
 VJP_TOL = 1e-4
 
 
-def _gpu_vjp(c, rows, ca, cp, theta, leaf_size=16, group_size=32, quad=True, G=1.0):
+def _gpu_vjp(c, rows, ca, cp, theta, leaf_size=16, group_size=32, quad=True, G=1.0, list_depth=0):
     import torch
     import paper_2010_11254_gb300 as sfg
     pos, mass, soft, sink = to_dev(c, torch)
     t = sfg.Tree(pos, mass, soft, sink, theta=theta, leaf_size=leaf_size, group_size=group_size, quadrupole=quad,
-                 G=G)
+                 G=G, list_depth=list_depth)
     r = torch.from_numpy(np.asarray(rows, np.int64)).cuda()
     d_pos, d_mass = t.accel_vjp(r, torch.from_numpy(ca).cuda(), None if cp is None else torch.from_numpy(cp).cuda())
     assert t.status() == sfg.SFG_OK
@@ -48,6 +48,19 @@ def test_vjp_matches_oracle(quad):
     o = oracle_tree(c, 16)
     o.walk(rows, 32, 0.6)
     o_pos, o_mass = o.vjp(rows, ca, cp, quadrupole=quad)
+    _close(g_pos, o_pos)
+    _close(g_mass, o_mass)
+
+
+@pytest.mark.parametrize("list_depth", [1, 2, 4])
+def test_vjp_list_depths(list_depth):
+    c = gen.clumpy_cloud(1 << 14, n_clumps=16, n_sink=12, seed=26)
+    rows = gen.active_subset(c.n, 0.3, seed=27)
+    ca, cp = gen.cotangents(rows.size, seed=28)
+    g_pos, g_mass = _gpu_vjp(c, rows, ca, cp, 0.5, group_size=13, list_depth=list_depth)
+    o = oracle_tree(c, 16)
+    o.walk(rows, 13, 0.5)
+    o_pos, o_mass = o.vjp(rows, ca, cp)
     _close(g_pos, o_pos)
     _close(g_mass, o_mass)
 
