@@ -19,9 +19,10 @@
 // targets with slot (tl + j) mod TL of the block, adds the source-side
 // terms to an accumulator and hands it to lane tl - 1, so that after TL
 // steps lane tl holds the sum over all targets for slot tl of the block and
-// adds it to that source's FP64 gradient.  Pairs inside a softening support
-// (possible on softened ranges only) are flagged and evaluated afterwards
-// with the full pair rule, one per lane per round.
+// adds it to that source's FP32 gradient sum (P2P list entries are dealt to
+// the blocks so that list neighbours land in different slices).  Pairs
+// inside a softening support (possible on softened ranges only) are flagged
+// and evaluated afterwards with the full pair rule, one per lane per round.
 #pragma once
 
 // Source-side adjoint sums are added to FP32 gradient buffers with vector
