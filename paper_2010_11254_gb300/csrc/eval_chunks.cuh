@@ -14,7 +14,7 @@
 // bounds checks; each source read from shared memory serves two pairs.
 //
 // Forward: slice s evaluates the chunk's slots s, s + R, ...; potentials are
-// summed in FP32 over a chunk and in FP64 across chunks.  Adjoint: each
+// summed in FP32 over a chunk and in float-float (two_sum_add) across chunks.  Adjoint: each
 // slice takes blocks of TL consecutive slots; at step j lane tl pairs its
 // targets with slot (tl + j) mod TL of the block, adds the source-side
 // terms to an accumulator and hands it to lane tl - 1, so that after TL
@@ -63,6 +63,18 @@ struct ChunkTargets {
 };
 
 constexpr int CK_NT = 2; // targets per lane
+
+// Adds b to the float-float sum (hi, lo): the error-free two-sum of hi and b
+// (Knuth's TwoSum, six FP32 additions) leaves hi + b = s + e exactly, e goes
+// to lo.  hi + lo carries about 48 bits, as an FP64 accumulator of FP32 chunk
+// sums would, at FP32 cost (FP64 arithmetic runs at 1/64 of the FP32 rate).
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float b)
+{
+    const float s = hi + b;
+    const float v = s - hi;
+    lo += (hi - (s - v)) + (b - v);
+    hi = s;
+}
 
 // The item's share of a list of n entries cut in 32-entry tiles: [b, e).
 __device__ __forceinline__ void item_share(int n, int kk, int K, int &b, int &e)
