@@ -42,23 +42,23 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # FP32 operations per interaction, counted from the evaluation source
-# (eval_chunks.cuh: chunk_fwd_parts for every P2P pair, chunk_fwd_nodes with
-# quadrupole / monopole); FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The deferred
+# (eval_chunks_body.inc: chunk_fwd_parts for every P2P pair, chunk_fwd_nodes
+# with quadrupole / monopole); FFMA = 2, FADD/FMUL/MUFU.RSQ = 1.  The deferred
 # evaluation of the pairs inside a softening support, padding slots and
 # absent targets are extra work and not counted.
 FLOP_P2P = 20
 FLOP_P2M_QUAD = 53
 FLOP_P2M_MONO = 20
-# Adjoint (eval_chunks.cuh: chunk_vjp_parts for every P2P pair,
+# Adjoint (eval_chunks_body.inc: chunk_vjp_parts for every P2P pair,
 # chunk_vjp_nodes with quadrupole), same counting rule; the source-side
 # rotation shuffles and the deferred softened pairs are not counted.
 FLOP_VJP_P2P = 44
 FLOP_VJP_P2M_QUAD = 137
 # DRAM bytes per launch of the evaluation kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu capture), valid only for the evaluation
-# sources (sha256 over walk.cu and eval_chunks.cuh), workload and launch shape
-# they were taken on; otherwise the line reports null.
-EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 2,
+# sources (sha256 over EVAL_SOURCES), workload and launch shape they were
+# taken on; otherwise the line reports null.
+EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 0,
                 "fwd": None, "vjp": None}
 EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh", "eval_chunks_body.inc")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
@@ -530,7 +530,7 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
     kw = dict(theta=wl["theta"], leaf_size=leaf, group_size=group, list_depth=depth, quadrupole=True,
               precision=args.precision, store_lists=bool(args.store_lists))
     lists = bool(args.store_lists) and args.precision == 0
-    kname = "k_eval" if lists else "k_walk"
+    kname = "k_eval_chunks" if lists else "k_walk"
 
     def one_step():
         tree = sfg.Tree(d_pos, d_mass, d_soft, d_sink, **kw)
@@ -652,7 +652,7 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         return {"bound": "alu", "kernel": kernel, "achieved": round(a, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(a / peak, 4),
                 "traffic": EVAL_TRAFFIC[traffic_key] if (same_src and args.workload == EVAL_TRAFFIC["workload"]
-                                                          and (leaf, group, depth or 2) == (
+                                                          and (leaf, group, depth or 0) == (
                                                               EVAL_TRAFFIC["leaf_size"], EVAL_TRAFFIC["group_size"],
                                                               EVAL_TRAFFIC["list_depth"])) else None,
                 "peak_source": peak_text,
@@ -674,7 +674,8 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         "dtype": "f32+f64" if args.precision == 0 else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
                    "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"],
-                   "leaf_size": leaf, "group_size": group, "list_depth": depth or 2, "quadrupole": True,
+                   "leaf_size": leaf, "group_size": group,
+                   "list_depth": {"forward": depth or 2, "adjoint": depth or 1}, "quadrupole": True,
                    "precision": args.precision, "store_lists": bool(args.store_lists),
                    "autotune": None if tuned is None else {"key": tuned["key"], "cached": tuned["cached"],
                                                             "trials": tuned.get("trials")},
@@ -776,8 +777,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--leaf-size", type=int, default=None, help="default: the autotuner's choice")
     ap.add_argument("--group-size", type=int, default=None, help="default: the autotuner's choice")
-    ap.add_argument("--list-depth", type=int, default=None, choices=[1, 2, 4],
-                    help="evaluation chunk depth (sources staged per lane); default: the autotuner's choice")
+    ap.add_argument("--list-depth", type=int, default=None, choices=[0, 1, 2, 4],
+                    help="evaluation chunk depth (sources staged per lane; 0: 2 forward, 1 adjoint); "
+                         "default: the autotuner's choice")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     ap.add_argument("--opening-curve", action="store_true",

@@ -3297,7 +3297,9 @@ static void launch_eval(Tree *t, WalkParams &P, cudaStream_t s)
 {
     if constexpr (MODE == MODE_EVAL || MODE == MODE_VJP) {
         // forward and adjoint: source chunks of the tree's depth, two targets per lane
-        const int depth = t->prm.list_depth == 0 ? 2 : t->prm.list_depth;
+        // (by default 2 for the forward and 1 for the adjoint, the faster of
+        // each on the 2^21 and paper-scale clouds)
+        const int depth = t->prm.list_depth != 0 ? t->prm.list_depth : MODE == MODE_VJP ? 1 : 2;
         if (depth == 1) launch_chunks<MODE>(ck1::k_eval_chunks<true, MODE>, ck1::k_eval_chunks<false, MODE>,
                                             ck1::CK_WARPS, t, P, s);
         else if (depth == 4) launch_chunks<MODE>(ck4::k_eval_chunks<true, MODE>, ck4::k_eval_chunks<false, MODE>,
