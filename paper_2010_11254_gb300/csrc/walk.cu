@@ -2368,22 +2368,35 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, walk_minb(MODE)) k_walk(WalkP
 }
 
 // Work items from the counted list sizes: the sliced iteration count of a
-// group (P2M, softened P2P and Newtonian P2P sources x T'/32, each weighted
-// by its relative cost in quarters: wt = (P2M, softened, Newtonian, walk
-// term)) plus a walk term; groups above the split size are cut into up to
-// KMAX items, while the partial-sum slot pool lasts.
+// group (P2M, softened P2P and Newtonian P2P sources, each weighted by its
+// relative cost in quarters: wt = (P2M, softened, Newtonian, walk term),
+// times the lane steps a source costs: T'/32 for the tile kernel's T' =
+// 2^ceil(log2 T) target lanes, 2/R for the chunk kernels' R slices of
+// ceil(T/2) lanes) plus a walk term; groups above the split size are cut
+// into up to KMAX items, while the partial-sum slot pool lasts.
 constexpr int SPLIT_ITERS = 1024;
 constexpr int SPLIT_PER_WARP = 8; // items per resident warp's share, at least
 constexpr int KMAX = 32;
 constexpr int PSLOTS = 65536;
 
-__device__ inline long long group_iters(const int *cnt, int tc, int g, int4 wt)
+struct ItemCost {
+    int4 wt;    // relative costs (P2M, softened P2P, Newtonian P2P, walk term)
+    int chunks; // 1: the chunk kernels' lane layout, 0: the tile kernel's
+};
+
+__device__ inline long long group_iters(const int *cnt, int tc, int g, ItemCost ic)
 {
+    const int4 wt = ic.wt;
+    const int *c = cnt + NCNT * (size_t)g;
+    const long long src = (long long)wt.x * c[0] + (long long)wt.y * c[2] + (long long)wt.z * c[4];
+    const long long walk = ((long long)c[0] + c[1] + c[3]) * wt.w / 16 + 32;
+    if (ic.chunks) {
+        const int R = 32 / max(1, (tc + 1) / 2);
+        return src / (2 * R) + walk;
+    }
     int tp = 1;
     while (tp < tc) tp <<= 1;
-    const int *c = cnt + NCNT * (size_t)g;
-    long long src = (long long)wt.x * c[0] + (long long)wt.y * c[2] + (long long)wt.z * c[4];
-    return src * tp / 128 + ((long long)c[0] + c[1] + c[3]) * wt.w / 16 + 32;
+    return src * tp / 128 + walk;
 }
 
 // Total estimated cost of all groups (one 64-bit atomic per warp).
@@ -2396,7 +2409,7 @@ __host__ __device__ inline void group_share(int ng, int rank, int world, int &g0
     g1 = (int)((long long)ng * (rank + 1) / world);
 }
 
-__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
+__global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngroups, ItemCost wt,
                              unsigned long long *total, int2 share)
 {
     int g0, g1;
@@ -2413,7 +2426,7 @@ __global__ void k_item_total(const int *cnt, const int2 *gtab, const int *d_ngro
 // SPLIT_PER_WARP slots per resident warp (the slot pool holds PSLOTS) and
 // every item stays small next to a warp's share (longest-first scheduling
 // then balances the rest).
-__global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngroups, int4 wt,
+__global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngroups, ItemCost wt,
                               const unsigned long long *total, long long warps, int *kcnt, int *is_split,
                               int2 share)
 {
@@ -2437,14 +2450,14 @@ __global__ void k_item_counts(const int *cnt, const int2 *gtab, const int *d_ngr
 
 // Longest first: items are bucketed by log2 of their estimated cost and the
 // buckets are issued from the most to the least expensive.
-__device__ inline int cost_bucket(const int *cnt, const int2 *gtab, const int *kcnt, int g, int4 wt)
+__device__ inline int cost_bucket(const int *cnt, const int2 *gtab, const int *kcnt, int g, ItemCost wt)
 {
     long long c = group_iters(cnt, gtab[g].y, g, wt) / kcnt[g];
     int b = 63 - __clzll(c > 1 ? c : 1);
     return 31 - min(b, 31);
 }
 
-__global__ void k_item_hist(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int4 wt,
+__global__ void k_item_hist(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, ItemCost wt,
                             int *hist)
 {
     int ng = *d_ngroups;
@@ -2464,7 +2477,7 @@ __global__ void k_item_scan(int *hist)
     }
 }
 
-__global__ void k_item_fill(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, int4 wt,
+__global__ void k_item_fill(const int *cnt, const int2 *gtab, const int *kcnt, const int *d_ngroups, ItemCost wt,
                             int *cursor, int2 *items)
 {
     int ng = *d_ngroups;
@@ -2890,16 +2903,20 @@ static void count_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
 }
 
 // Relative costs (in quarters) of a P2M, softened P2P and Newtonian P2P
-// source per target lane, and of the walk term: evaluation from stored lists
-// (forward, adjoint; measured per interaction on a clumpy cloud) and the
-// walking evaluation (unit weights).
+// source per target lane, and of the walk term: the chunk kernels' forward
+// and adjoint (from their instruction counts per pair: P2M 2.5 and 2.75
+// times a Newtonian pair, a softened-range pair 1.25 times with its checks
+// and deferred pairs), the tile kernel's stored-list modes (measured per
+// interaction on a clumpy cloud) and the walking evaluation (unit weights).
+constexpr int4 WT_FWD = {10, 5, 4, 1};
+constexpr int4 WT_VJP = {11, 5, 4, 1};
 constexpr int4 WT_EVAL = {7, 8, 4, 1};
-constexpr int4 WT_VJP = {20, 6, 4, 1};
 constexpr int4 WT_WALK = {4, 4, 4, 4};
 
 // Cut the heavy groups into work items, from the list sizes.
-static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int4 wt)
+static void items_from_counts(Tree *t, Work &w, WalkParams &P, cudaStream_t s, int4 weights, bool chunks = false)
 {
+    const ItemCost wt = {weights, chunks ? 1 : 0};
     const int n = (int)t->n, BT = 256;
     const int *d_ng = P.d_ngroups;
     cudaMemsetAsync(t->d_counters + 2, 0, 3 * sizeof(unsigned long long), s);
@@ -3336,7 +3353,7 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
         if (rc) return rc;
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
-        items_from_counts(t, w, P, s, WT_EVAL);
+        items_from_counts(t, w, P, s, WT_FWD, true);
         rc = expand_lists(t, w, P, s);
         if (rc) return rc;
     } else {
@@ -3881,7 +3898,7 @@ int accel_vjp(Tree *t, const int64_t *active, int64_t n_active, const double *co
                 rc = remember_active(t, active, n_active, s);
                 if (rc) return rc;
             }
-            items_from_counts(t, w, P, s, WT_VJP);
+            items_from_counts(t, w, P, s, WT_VJP, true);
             rc = expand_lists(t, w, P, s);
             if (rc) return rc;
         } else {
