@@ -891,14 +891,33 @@ __device__ inline void node_centre(const Frame &fr, const uint32_t lo[3], int le
 // the normal FP32 exponent range keeps the top 23 of its 52 fraction bits;
 // the 29 bits below decide the rounding (above half: up; exactly half: to
 // even); a carry out of the fraction moves into the exponent, up to infinity
-// past the largest float.  Zeros, FP32-subnormal magnitudes, infinities and
-// NaN take the hardware conversion.
+// past the largest float.  The rest (zeros, FP32-subnormal magnitudes,
+// values past the FP32 range, infinities, NaN) goes to f32_rn_rare, out of
+// line so that no FP64 conversion is issued on the common path.
+__device__ __noinline__ unsigned f32_rn_rare(unsigned long long b)
+{
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int E = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long frac = b & ((1ull << 52) - 1);
+    if (E == 0x7ff) return sign | 0x7f800000u | (frac ? 0x400000u : 0u); // infinity; NaN made quiet
+    const int e = E - 1023;
+    if (e > 127) return sign | 0x7f800000u; // past the largest float: infinity
+    if (E == 0) return sign;                // zero and FP64 subnormals round to zero
+    // |x| < 2^-126: the FP32 subnormal q 2^-149 with q = RNE(mant 2^(e + 97)), a
+    // right shift by s = -(e + 97) >= 30 of the 53-bit significand
+    const unsigned long long mant = frac | (1ull << 52);
+    const int sh = -(e + 97);
+    if (sh > 54) return sign; // below half the smallest subnormal
+    const unsigned long long q = mant >> sh, rem = mant & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    return sign | (unsigned)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+}
+
 __device__ __forceinline__ float f32_rn(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
     const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
-    if (e < -126 || e > 127) return (float)x;
+    if (e < -126 || e > 127) return __uint_as_float(f32_rn_rare(b));
     unsigned f = ((unsigned)(e + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned r = lo & 0x1fffffffu;
     f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
