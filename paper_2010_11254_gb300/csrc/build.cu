@@ -532,12 +532,16 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
     uint32_t v[OS_ITEMS];
     int dg[OS_ITEMS], loc[OS_ITEMS];
     const int base = tile * OS_TILE + w * 32 * OS_ITEMS;
+    // all of the thread's loads in flight before the first digit is ranked
 #pragma unroll
     for (int r = 0; r < OS_ITEMS; r++) {
-        int i = base + r * 32 + lane;
-        bool valid = i < n;
-        k[r] = valid ? kin[i] : 0;
-        v[r] = valid ? vin[i] : 0;
+        const int i = base + r * 32 + lane;
+        k[r] = i < n ? kin[i] : 0;
+        v[r] = i < n ? vin[i] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < OS_ITEMS; r++) {
+        const bool valid = base + r * 32 + lane < n;
         int d = valid ? rs_digit(k[r], v[r], shift, cl) : 256;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int before = __popc(peers & lt);
@@ -608,21 +612,47 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
 }
 
 // --------------------------------------------------------------- gather ----
+constexpr int PK_UNROLL = 4;
 __global__ void k_pack(const double *pos, const double *mass, const double *soft, const uint8_t *sink, int n,
                        const uint32_t *val, int32_t *order, int32_t *rank, double *pos_s, double *mass_s,
                        double *soft_s, uint8_t *sink_s, const uint16_t *cloud_of, int32_t *pcloud)
 {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        int i = (int)val[r];
-        if (pcloud) pcloud[r] = cloud_of[i];
-        order[r] = i;
-        rank[i] = r;
-        pos_s[3 * (size_t)r] = pos[3 * (size_t)i];
-        pos_s[3 * (size_t)r + 1] = pos[3 * (size_t)i + 1];
-        pos_s[3 * (size_t)r + 2] = pos[3 * (size_t)i + 2];
-        mass_s[r] = mass[i];
-        soft_s[r] = soft[i];
-        sink_s[r] = sink ? (uint8_t)(sink[i] != 0) : (uint8_t)0;
+    // PK_UNROLL ranks per thread and round, so that their gathers are in
+    // flight together
+    const int stride = gridDim.x * blockDim.x;
+    for (int r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < n; r0 += PK_UNROLL * stride) {
+        int idx[PK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < PK_UNROLL; u++) {
+            const int r = r0 + u * stride;
+            idx[u] = r < n ? (int)val[r] : -1;
+        }
+        double x[PK_UNROLL][3], m[PK_UNROLL], h[PK_UNROLL];
+        uint8_t sk[PK_UNROLL];
+        uint16_t cl[PK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < PK_UNROLL; u++) {
+            const int i = idx[u] < 0 ? 0 : idx[u];
+            if (idx[u] >= 0) {
+                for (int a = 0; a < 3; a++) x[u][a] = pos[3 * (size_t)i + a];
+                m[u] = mass[i];
+                h[u] = soft[i];
+                sk[u] = sink ? (uint8_t)(sink[i] != 0) : (uint8_t)0;
+                cl[u] = pcloud ? cloud_of[i] : (uint16_t)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PK_UNROLL; u++) {
+            const int r = r0 + u * stride, i = idx[u];
+            if (i < 0) continue;
+            if (pcloud) pcloud[r] = cl[u];
+            order[r] = i;
+            rank[i] = r;
+            for (int a = 0; a < 3; a++) pos_s[3 * (size_t)r + a] = x[u][a];
+            mass_s[r] = m[u];
+            soft_s[r] = h[u];
+            sink_s[r] = sk[u];
+        }
     }
 }
 
