@@ -464,6 +464,7 @@ constexpr int OS_ITEMS = 8;                        // keys per thread of a one-s
 constexpr int OS_TILE = RS_WARPS * 32 * OS_ITEMS;  // 2048 keys: few registers, 4 blocks per SM
 constexpr unsigned long long RS_AGG = 1ull << 32;  // look-back word: flag in the high half, count below
 constexpr unsigned long long RS_INC = 2ull << 32;
+constexpr int LB_W = 4; // look-back words read per round
 
 __global__ void __launch_bounds__(256)
     k_rs_count_all(const uint64_t *key, int n, const uint16_t *cloud_of, int cloud_passes, unsigned *gcount)
@@ -572,20 +573,36 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
             atomicExch(mine, RS_INC | run);
         } else {
             atomicExch(mine, RS_AGG | run);
+            // Look-back over LB_W predecessors per round, their words read
+            // together: the tiles of the first wave all start at once, and a
+            // tile there finds an inclusive prefix only about tile / 2 tiles
+            // back, so a one-word-per-round walk would chain that many L2
+            // round trips.  Published words are consumed in order up to the
+            // first inclusive one (the end) or the first unpublished one (read
+            // again next round).
             int j = tile - 1;
             for (long long spin = 0; j >= 0;) {
-                const unsigned long long x = *(volatile unsigned long long *)(look + (size_t)j * 256 + d);
-                const unsigned long long f = x & ~0xffffffffull;
-                if (f == 0ull) {
-                    if (++spin > (1ll << 24)) { // a tile that never published: give up
-                        atomicOr(status, ST_ETIMEOUT);
-                        break;
-                    }
-                    continue;
+                unsigned long long x[LB_W];
+#pragma unroll
+                for (int q = 0; q < LB_W; q++)
+                    x[q] = j - q >= 0 ? *(volatile unsigned long long *)(look + (size_t)(j - q) * 256 + d) : +RS_INC;
+                int used = 0;
+                bool end = false;
+#pragma unroll
+                for (int q = 0; q < LB_W; q++) {
+                    if (end || used < q) continue;
+                    const unsigned long long f = x[q] & ~0xffffffffull;
+                    if (f == 0ull) continue; // unpublished: stop consuming here
+                    excl += (unsigned)x[q];
+                    used = q + 1;
+                    end = f == RS_INC;
                 }
-                excl += (unsigned)x;
-                if (f == RS_INC) break;
-                j--;
+                if (end) break;
+                if (used == 0 && ++spin > (1ll << 24)) { // a tile that never published: give up
+                    atomicOr(status, ST_ETIMEOUT);
+                    break;
+                }
+                j -= used;
             }
             atomicExch(mine, RS_INC | (excl + run));
         }
