@@ -185,32 +185,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(wl: dict, c, act, ca, cp, sample: int = 4096, seed: int = 0) -> dict:
+def cpu_baseline(wl: dict, c, act, ca, cp, sample: int | None = None, seed: int = 0, target_s: float = 12.0) -> dict:
     """The oracle as it stands (FP64, OpenMP) on a bounded sample: the full
-    tree build, plus walk + field + adjoint for `sample` random active rows,
-    extrapolated per active row to the whole active set."""
+    tree build, plus walk + field + adjoint for a random sample of active
+    rows, extrapolated per active row to the whole active set.  Without a
+    fixed `sample`, a 256-row pass sizes the sample so that its rows take
+    about `target_s` seconds."""
     import oracle
     rng = np.random.default_rng(seed)
-    pick = np.sort(rng.choice(act.size, min(sample, act.size), replace=False))
-    rows = act[pick]
     t0 = time.perf_counter()
     tr = oracle.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=16)
     t1 = time.perf_counter()
-    tr.walk(act, 32, wl["theta"], need=rows)
-    tr.accel_group(rows)
+
+    def rows_pass(k):
+        pick = np.sort(rng.choice(act.size, min(k, act.size), replace=False))
+        rows = act[pick]
+        ta = time.perf_counter()
+        tr.walk(act, 32, wl["theta"], need=rows)
+        tr.accel_group(rows)
+        tb = time.perf_counter()
+        tr.vjp(rows[:1], ca[pick[:1]], cp[pick[:1]])
+        tc = time.perf_counter()
+        tr.vjp(rows, ca[pick], cp[pick])
+        td = time.perf_counter()
+        per_row = ((tb - ta) + max(0.0, (td - tc) - (tc - tb))) / rows.size
+        return rows.size, per_row, tc - tb, td - ta
+
+    if sample is None:
+        _, est, _, _ = rows_pass(256)
+        sample = int(min(act.size, max(1024, target_s / max(est, 1e-9))))
     t2 = time.perf_counter()
-    tr.vjp(rows[:1], ca[pick[:1]], cp[pick[:1]])
+    n_rows, per_row, t_fixed_vjp, _ = rows_pass(sample)
     t3 = time.perf_counter()
-    tr.vjp(rows, ca[pick], cp[pick])
-    t4 = time.perf_counter()
     t_build = t1 - t0
-    per_row = ((t2 - t1) + max(0.0, (t4 - t3) - (t3 - t2))) / rows.size
-    t_fixed_vjp = t3 - t2
     t_step = t_build + t_fixed_vjp + per_row * act.size
     return {"value": act.size / t_step, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"oracle tree build over all {c.n} particles + group walk, field and adjoint for "
-                      f"{rows.size} of {act.size} active rows; per-row cost extrapolated to all rows",
-            "cpu_seconds_measured": round(t4 - t0, 3), "est_step_s": round(t_step, 4)}
+                      f"{n_rows} of {act.size} active rows; per-row cost extrapolated to all rows",
+            "cpu_seconds_measured": round(t_build + (t3 - t2), 3), "est_step_s": round(t_step, 4)}
 
 
 def force_error(c, act, acc, phi, sample: int = 1000, seed: int = 0) -> dict:
