@@ -185,12 +185,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(wl: dict, c, act, ca, cp, sample: int | None = None, seed: int = 0, target_s: float = 12.0) -> dict:
+def cpu_baseline(wl: dict, c, act, ca, cp, sample: int | None = None, seed: int = 0, target_s: float = 20.0) -> dict:
     """The oracle as it stands (FP64, OpenMP) on a bounded sample: the full
     tree build, plus walk + field + adjoint for a random sample of active
     rows, extrapolated per active row to the whole active set.  Without a
-    fixed `sample`, a 256-row pass sizes the sample so that its rows take
-    about `target_s` seconds."""
+    fixed `sample`, the sample grows from 1024 rows until its rows take at
+    least half of `target_s` seconds (or every active row is in); the last
+    pass is the one reported."""
     import oracle
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
@@ -211,11 +212,18 @@ def cpu_baseline(wl: dict, c, act, ca, cp, sample: int | None = None, seed: int 
         per_row = ((tb - ta) + max(0.0, (td - tc) - (tc - tb))) / rows.size
         return rows.size, per_row, tc - tb, td - ta
 
-    if sample is None:
-        _, est, _, _ = rows_pass(256)
-        sample = int(min(act.size, max(1024, target_s / max(est, 1e-9))))
     t2 = time.perf_counter()
-    n_rows, per_row, t_fixed_vjp, _ = rows_pass(sample)
+    if sample is None:
+        # grow the sample until its rows take about target_s (or all rows are in)
+        k = 1024
+        while True:
+            t2 = time.perf_counter()
+            n_rows, per_row, t_fixed_vjp, took = rows_pass(k)
+            if took >= 0.5 * target_s or n_rows >= act.size:
+                break
+            k = int(min(act.size, k * min(16.0, target_s / max(took, 1e-3))))
+    else:
+        n_rows, per_row, t_fixed_vjp, _ = rows_pass(sample)
     t3 = time.perf_counter()
     t_build = t1 - t0
     t_step = t_build + t_fixed_vjp + per_row * act.size
