@@ -58,8 +58,9 @@ FLOP_VJP_P2M_QUAD = 137
 # dram__bytes_write.sum, one ncu capture), valid only for the evaluation
 # sources (sha256 over EVAL_SOURCES), workload and launch shape they were
 # taken on; otherwise the line reports null.
-EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 0,
-                "fwd": None, "vjp": None}
+EVAL_TRAFFIC = {"sha256": "a497f045aff6511cd5d0cb39b1e0be7a3c8a7f3b8ab232a82043dcdc47258ee5",
+                "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 0,
+                "fwd": 14024652800, "vjp": 28415006464}
 EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh", "eval_chunks_body.inc")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
@@ -462,7 +463,7 @@ def run_ensemble(args, rank, world, dist, dev):
     e2e_ms, e2e_val = aggregate(statistics.mean(e2e), len(clouds), world, dist, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_ensemble_sample(clouds, 150_000, seed=11, leaf_size=kw["leaf_size"],
+        cpu = oracle_ensemble_sample(clouds, 2_000_000, seed=11, leaf_size=kw["leaf_size"],
                                      group_size=kw["group_size"])
     line = {
         "metric": "clouds per second (batched build + field + adjoint of an ensemble)", "value": value,
@@ -484,7 +485,8 @@ def run_ensemble(args, rank, world, dist, dev):
                                     "vjp_walk_p99": float(np.percentile(vjp_lat, 99)),
                                     "vjp_walk_max": float(vjp_lat.max())},
         "fixed_tree_graph_replay_ms": round(replay_ms, 4), "graph_vs_eager_max_rel_diff": gdiff,
-        "roofline": {"bound": "alu", "kernel": "k_walk<QUAD, MODE_VJP> (adjoint, all clouds in one launch)",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_eval_chunks<QUAD, MODE_VJP> (adjoint from stored lists, all clouds in one launch)",
                      "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                      "frac": round(ach / peak, 4), "traffic": None, "peak_source": peak_text},
         "interactions": {"p2p": int(st["n_p2p"]), "p2m": int(st["n_p2m"]),
