@@ -58,9 +58,9 @@ FLOP_VJP_P2M_QUAD = 137
 # dram__bytes_write.sum, one ncu capture), valid only for the evaluation
 # sources (sha256 over EVAL_SOURCES), workload and launch shape they were
 # taken on; otherwise the line reports null.
-EVAL_TRAFFIC = {"sha256": "a497f045aff6511cd5d0cb39b1e0be7a3c8a7f3b8ab232a82043dcdc47258ee5",
+EVAL_TRAFFIC = {"sha256": "d792ac683e94e9afec0f10c265824ad4b5f291f824b6cd9ed16e3010b52ec5d9",
                 "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 0,
-                "fwd": 14024652800, "vjp": 28415006464}
+                "fwd": 14172778752, "vjp": 28365686528}
 EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh", "eval_chunks_body.inc")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).

@@ -2903,12 +2903,14 @@ static void count_lists(Tree *t, Work &w, WalkParams &P, cudaStream_t s)
 }
 
 // Relative costs (in quarters) of a P2M, softened P2P and Newtonian P2P
-// source per target lane, and of the walk term: the chunk kernels' forward
-// and adjoint (from their instruction counts per pair: P2M 2.5 and 2.75
-// times a Newtonian pair, a softened-range pair 1.25 times with its checks
-// and deferred pairs), the tile kernel's stored-list modes (measured per
-// interaction on a clumpy cloud) and the walking evaluation (unit weights).
-constexpr int4 WT_FWD = {10, 5, 4, 1};
+// source per target lane, and of the walk term: the chunk kernel's adjoint
+// (from its instruction counts per pair: P2M 2.75 times a Newtonian pair, a
+// softened-range pair 1.25 times with its checks and deferred pairs), the
+// stored-list forward and tile modes (measured per interaction on a clumpy
+// cloud) and the walking evaluation (unit weights).  The forward keeps the
+// tile layout's split: its items also cut the list expansion, which the
+// finer chunk-layout split made slower (0.94 -> 1.24 ms on the paper-scale
+// cloud) for no gain in the forward evaluation itself.
 constexpr int4 WT_VJP = {11, 5, 4, 1};
 constexpr int4 WT_EVAL = {7, 8, 4, 1};
 constexpr int4 WT_WALK = {4, 4, 4, 4};
@@ -3353,7 +3355,7 @@ int accel(Tree *t, const int64_t *active, int64_t n_active, double *acc, double 
         if (rc) return rc;
         rc = remember_active(t, active, n_active, s);
         if (rc) return rc;
-        items_from_counts(t, w, P, s, WT_FWD, true);
+        items_from_counts(t, w, P, s, WT_EVAL);
         rc = expand_lists(t, w, P, s);
         if (rc) return rc;
     } else {
