@@ -55,12 +55,11 @@ FLOP_P2M_MONO = 20
 FLOP_VJP_P2P = 44
 FLOP_VJP_P2M_QUAD = 137
 # DRAM bytes per launch of the evaluation kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum, one ncu capture), valid only for the evaluation
-# sources (sha256 over EVAL_SOURCES), workload and launch shape they were
-# taken on; otherwise the line reports null.
-EVAL_TRAFFIC = {"sha256": "d792ac683e94e9afec0f10c265824ad4b5f291f824b6cd9ed16e3010b52ec5d9",
-                "workload": "paper-20M", "leaf_size": 32, "group_size": 16, "list_depth": 0,
-                "fwd": 14172778752, "vjp": 28365686528}
+# dram__bytes_write.sum, one ncu capture per list depth), valid only for the
+# evaluation sources (sha256 over EVAL_SOURCES), workload and launch shape they
+# were taken on; otherwise the line reports null.
+EVAL_TRAFFIC = {"sha256": None, "workload": "paper-20M", "leaf_size": 32, "group_size": 16,
+                "by_depth": {}}
 EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh", "eval_chunks_body.inc")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
@@ -673,10 +672,9 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         a = flops / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": kernel, "achieved": round(a, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(a / peak, 4),
-                "traffic": EVAL_TRAFFIC[traffic_key] if (same_src and args.workload == EVAL_TRAFFIC["workload"]
-                                                          and (leaf, group, depth or 0) == (
-                                                              EVAL_TRAFFIC["leaf_size"], EVAL_TRAFFIC["group_size"],
-                                                              EVAL_TRAFFIC["list_depth"])) else None,
+                "traffic": EVAL_TRAFFIC["by_depth"].get(depth or 1, {}).get(traffic_key)
+                if (same_src and args.workload == EVAL_TRAFFIC["workload"]
+                    and (leaf, group) == (EVAL_TRAFFIC["leaf_size"], EVAL_TRAFFIC["group_size"])) else None,
                 "peak_source": peak_text,
                 "flops_per_launch": int(flops), "launch_ms": round(ms, 4), "flop_model": model}
 
@@ -697,7 +695,7 @@ def run_point(args, wl, c, act, ca, cp, frac, rank, world, local, dist, dev):
         "config": {"workload": args.workload, "n_particles": int(c.n), "n_sinks": int(c.n_sink),
                    "n_active": int(act.size), "active_frac": frac, "theta": wl["theta"],
                    "leaf_size": leaf, "group_size": group,
-                   "list_depth": {"forward": depth or 2, "adjoint": depth or 1}, "quadrupole": True,
+                   "list_depth": depth or 1, "quadrupole": True,
                    "precision": args.precision, "store_lists": bool(args.store_lists),
                    "autotune": None if tuned is None else {"key": tuned["key"], "cached": tuned["cached"],
                                                             "trials": tuned.get("trials")},
@@ -799,9 +797,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--leaf-size", type=int, default=None, help="default: the autotuner's choice")
     ap.add_argument("--group-size", type=int, default=None, help="default: the autotuner's choice")
-    ap.add_argument("--list-depth", type=int, default=None, choices=[0, 1, 2, 4],
-                    help="evaluation chunk depth (sources staged per lane; 0: 2 forward, 1 adjoint); "
-                         "default: the autotuner's choice")
+    ap.add_argument("--list-depth", type=int, default=None, choices=[1, 2, 4],
+                    help="evaluation chunk depth (sources staged per lane); default: the autotuner's choice")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="0: FP32 pair arithmetic with FP64 frame/moments/potential sums; 1: all FP64")
     ap.add_argument("--opening-curve", action="store_true",

@@ -63,8 +63,7 @@ typedef struct sfg_params {
     int leaf_size;   /* N_leaf: a node with <= N_leaf particles (or at the 21st level) is a leaf; 1..256 */
     int group_size;  /* G_group: <= G_group active targets share one walk; 1..32 */
     int list_depth;  /* depth of the evaluation's shared-memory list buffer: the interaction-list
-                        sources each active lane stages per chunk (1, 2 or 4; 0 = 2 for the
-                        forward evaluation and 1 for the adjoint) */
+                        sources each active lane stages per chunk (1, 2 or 4; 0 = 1) */
     int quadrupole;  /* 1: monopole + quadrupole node fields; 0: monopole only (Sec. 2.2) */
     int precision;   /* 0: FP32 pair/multipole arithmetic on node-centred offsets, FP64
                         frame/moments/potential sums; 1: all-FP64 evaluation */

@@ -2,13 +2,12 @@
 
 The tree's leaf size (N_leaf) and group size (targets sharing one walk) trade
 walk length against list length, and the list-buffer depth (the sources
-each active lane stages per chunk of the evaluation: 1, 2 or 4, or 0 for 2
-in the forward and 1 in the adjoint) trades the per-chunk costs against
-shared memory per warp; the best choice depends on the particle
-distribution, the active fraction and the GPU.  ``tune`` builds the tree
-with each candidate on the caller's own data, times one forward + adjoint
-(CUDA events, after one warm-up), and returns the fastest: first over
-(leaf size, group size) at depth 0, then over the other depths at the best
+each active lane stages per chunk of the evaluation: 1, 2 or 4) trades the
+per-chunk costs against shared memory per warp; the best choice depends on
+the particle distribution, the active fraction and the GPU.  ``tune`` builds
+the tree with each candidate on the caller's own data, times one forward +
+adjoint (CUDA events, after one warm-up), and returns the fastest: first over
+(leaf size, group size) at depth 1, then over the other depths at the best
 pair.  Results are cached in a JSON file keyed by GPU name and a coarse
 workload class, so a repeated workload pays the search once.
 """
@@ -21,8 +20,8 @@ import os
 import torch
 
 DEFAULT_CANDIDATES = ((8, 16), (8, 32), (16, 16), (16, 32), (32, 16), (32, 32))
-DEPTHS = (0, 1, 2, 4)
-KEY_VERSION = "v3"  # cache entries carry the list depth (0: per mode)
+DEPTHS = (1, 2, 4)
+KEY_VERSION = "v4"  # cache entries carry the list depth
 
 
 def _cache_path() -> str:
@@ -80,7 +79,7 @@ def tune(pos, mass, soft, is_sink=None, *, offsets=None, active=None, cot_a=None
         trials.append({"leaf_size": leaf, "group_size": group, "list_depth": depth, "ms": best})
         return trials[-1]
 
-    first = 0 if 0 in depths else depths[0]
+    first = 1 if 1 in depths else depths[0]
     for leaf, group in candidates:
         trial(leaf, group, first)
     win = min(trials, key=lambda r: r["ms"])

@@ -3316,9 +3316,8 @@ static void launch_eval(Tree *t, WalkParams &P, cudaStream_t s)
 {
     if constexpr (MODE == MODE_EVAL || MODE == MODE_VJP) {
         // forward and adjoint: source chunks of the tree's depth, two targets per lane
-        // (by default 2 for the forward and 1 for the adjoint, the faster of
-        // each on the 2^21 and paper-scale clouds)
-        const int depth = t->prm.list_depth != 0 ? t->prm.list_depth : MODE == MODE_VJP ? 1 : 2;
+        // (by default 1, the faster depth of both on the paper-scale cloud)
+        const int depth = t->prm.list_depth != 0 ? t->prm.list_depth : 1;
         if (depth == 1) launch_chunks<MODE>(ck1::k_eval_chunks<true, MODE>, ck1::k_eval_chunks<false, MODE>,
                                             ck1::CK_WARPS, t, P, s);
         else if (depth == 4) launch_chunks<MODE>(ck4::k_eval_chunks<true, MODE>, ck4::k_eval_chunks<false, MODE>,
