@@ -4,9 +4,10 @@
 // ring_take, cp_async16, global_ns, WalkParams).
 //
 // One warp per work item.  The group's T targets are dealt two per lane:
-// TL = ceil(T / 2) target lanes form a slice, R = floor(32 / TL) slices,
-// A = R TL active lanes, and lane (tl, s) holds targets tl and tl + TL.
-// Sources arrive in chunks of C = 2 A: every active lane stages two (P2M
+// TL = ceil(T / 2) target lanes form a slice (8 for 13 or 14 targets),
+// R = floor(32 / TL) slices, A = R TL active lanes, and lane (tl, s) holds
+// targets tl and tl + TL.  Sources arrive in chunks of C = A CK_M (CK_M,
+// the list depth, 1, 2 or 4): every active lane stages CK_M of them (P2M
 // node ids, or sorted particle ranks of the group's expanded P2P list),
 // converted to the group-centred FP32 frame (exact integer half-cell centre
 // differences plus the stored FP32 offsets).  Slots past the end of a list
@@ -14,15 +15,16 @@
 // bounds checks; each source read from shared memory serves two pairs.
 //
 // Forward: slice s evaluates the chunk's slots s, s + R, ...; potentials are
-// summed in FP32 over a chunk and in float-float (two_sum_add) across chunks.  Adjoint: each
-// slice takes blocks of TL consecutive slots; at step j lane tl pairs its
-// targets with slot (tl + j) mod TL of the block, adds the source-side
-// terms to an accumulator and hands it to lane tl - 1, so that after TL
-// steps lane tl holds the sum over all targets for slot tl of the block and
-// adds it to that source's FP32 gradient sum (P2P list entries are dealt to
-// the blocks so that list neighbours land in different slices).  Pairs
-// inside a softening support (possible on softened ranges only) are flagged
-// and evaluated afterwards with the full pair rule, one per lane per round.
+// summed in FP32 over a chunk and in float-float (two_sum_add) across
+// chunks.  Adjoint: each slice takes blocks of TL consecutive slots; at step
+// j lane tl pairs its targets with slot (tl + j) mod TL of the block, adds
+// the source-side terms to an accumulator and hands it to lane tl - 1, so
+// that after TL steps lane tl holds the sum over all targets for slot tl of
+// the block and adds it to that source's FP32 gradient sum (P2P list entries
+// are dealt to the blocks so that list neighbours land in different
+// slices).  Pairs inside a softening support (possible on softened ranges
+// only) are flagged and evaluated afterwards with the full pair rule, one
+// per lane per round.
 #pragma once
 
 // Source-side adjoint sums are added to FP32 gradient buffers with vector
