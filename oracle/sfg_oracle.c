@@ -670,6 +670,17 @@ void sfgo_nodes_f64(const sfgo_tree *t, double *out)
 }
 
 /* ---------------- group form: integer, conservative opening rule --------- */
+/* The group level of a cloud holding U targets: the largest L with
+ * G 8^L <= U (0 below 8 G), the depth at which a uniform cloud's nodes hold
+ * about G targets.  Nodes above it are always opened and their children are
+ * not packed together, so that no group spans sparse octants of the top
+ * levels (such groups had boxes covering much of the cloud). */
+static int group_level(int64_t U, int gsize)
+{
+    int L = 0;
+    for (int64_t v = (int64_t)gsize * 8; v <= U && L < 21; v *= 8) L++;
+    return L;
+}
 
 /* ceil(4^(21-l) / theta^2), capped at 2^62: "open if L/r > theta" with L and
  * r in cell units (L = 2^(21-l) cells). */
@@ -804,25 +815,36 @@ int64_t sfgo_walk(sfgo_tree *t, const int64_t *active, int64_t n_active, int gsi
         runs[nr].node = (nd);                                              \
         nr++;                                                              \
     } while (0)
+    const int glevel = group_level(U, gsize);
     for (int64_t i = 0; i < t->nn; i++) {
         const onode *nd = &t->nodes[i];
         int64_t c = pre[nd->first + nd->count] - pre[nd->first];
         if (c == 0) continue;
-        if (i == 0 && c <= gsize) EMIT(pre[nd->first], c, i);
+        /* a node is opened (its children considered) when it holds more than
+         * G targets, or when it lies above the group level and has children */
+        const int open = nd->nchild > 0 && (c > gsize || nd->level < glevel);
+        if (i == 0 && !open && c <= gsize) EMIT(pre[nd->first], c, i);
         if (c > gsize && nd->nchild == 0 && i == 0)
             for (int64_t s = 0; s < c; s += gsize) EMIT(pre[nd->first] + s, (c - s) < gsize ? (c - s) : gsize, i);
-        if (c <= gsize || nd->nchild == 0) continue;
+        if (!open) continue;
+        /* siblings are packed together only below the group level */
+        const int pack = nd->level >= glevel;
         int64_t run_first = -1, run_count = 0;
         for (int k = 0; k < nd->nchild; k++) {
             const onode *ch = &t->nodes[nd->child_first + k];
             int64_t tf = pre[ch->first];
             int64_t cc = pre[ch->first + ch->count] - tf;
             if (cc == 0) continue;
-            if (cc > gsize) {
+            const int ch_open = ch->nchild > 0 && (cc > gsize || ch->level < glevel);
+            if (cc > gsize || ch_open) {
                 if (run_count) EMIT(run_first, run_count, i);
                 run_count = 0;
                 if (ch->nchild == 0)
                     for (int64_t s = 0; s < cc; s += gsize) EMIT(tf + s, (cc - s) < gsize ? (cc - s) : gsize, i);
+                continue;
+            }
+            if (!pack) {
+                EMIT(tf, cc, i);
                 continue;
             }
             if (run_count + cc > gsize) {

@@ -2498,6 +2498,18 @@ __global__ void k_item_cap(const int *soff, const int *d_ngroups, int *kcnt)
 }
 
 // ---------------------------------------------------- group formation ----
+// The group level of a cloud holding U targets: the largest L with
+// G 8^L <= U (0 below 8 G), the depth at which a uniform cloud's nodes hold
+// about G targets.  Nodes above it are always opened and their children are
+// not packed together, so that no group spans sparse octants of the top
+// levels: such groups had boxes covering much of the cloud, and their
+// single-warp walks outlasted the rest of the walk launch.
+__device__ __forceinline__ int group_level(int U, int G)
+{
+    int L = 0;
+    for (long long v = 8ll * G; v <= U && L < 21; v *= 8) L++;
+    return L;
+}
 __global__ void k_mark(const int64_t *idx, int64_t n_active, int n, const int32_t *rank, int *flag, int *status)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_active;
@@ -2524,8 +2536,8 @@ __device__ inline void put_group(int *gflag, int *gcnt, int tf, int tc)
 }
 
 __global__ void k_group_marks(const int32_t *nfirst, const int32_t *ncount, const int32_t *nchild_first,
-                              const int32_t *nnchild, int nn, int nroots, const int *pre, int G, int *gflag,
-                              int *gcnt)
+                              const int32_t *nnchild, const int32_t *nlevel, const int32_t *ncloud, int nn,
+                              int nroots, const int *pre, int G, int *gflag, int *gcnt)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
         int f = nfirst[i];
@@ -2534,10 +2546,16 @@ __global__ void k_group_marks(const int32_t *nfirst, const int32_t *ncount, cons
         if (c == 0) continue;
         bool leaf = nnchild[i] == 0;
         const bool root = i < nroots;
-        if (root && c <= G) put_group(gflag, gcnt, tf, c);
+        // the cloud's root is node ncloud[i]; its target count sets the group level
+        const int rt = ncloud[i];
+        const int gl = group_level(pre[nfirst[rt] + ncount[rt]] - pre[nfirst[rt]], G);
+        // opened (children considered): more than G targets, or above the group level with children
+        const bool open = !leaf && (c > G || nlevel[i] < gl);
+        if (root && !open && c <= G) put_group(gflag, gcnt, tf, c);
         if (root && c > G && leaf)
             for (int s = 0; s < c; s += G) put_group(gflag, gcnt, tf + s, min(G, c - s));
-        if (c <= G || leaf) continue;
+        if (!open) continue;
+        const bool pack = nlevel[i] >= gl; // siblings are packed together only below it
         int run_first = -1, run_count = 0;
         int cf = nchild_first[i], nc = nnchild[i];
         for (int k = 0; k < nc; k++) {
@@ -2545,11 +2563,16 @@ __global__ void k_group_marks(const int32_t *nfirst, const int32_t *ncount, cons
             int ctf = pre[nfirst[ch]];
             int cc = pre[nfirst[ch] + ncount[ch]] - ctf;
             if (cc == 0) continue;
-            if (cc > G) {
+            const bool ch_open = nnchild[ch] > 0 && (cc > G || nlevel[ch] < gl);
+            if (cc > G || ch_open) {
                 if (run_count) put_group(gflag, gcnt, run_first, run_count);
                 run_count = 0;
                 if (nnchild[ch] == 0)
                     for (int s = 0; s < cc; s += G) put_group(gflag, gcnt, ctf + s, min(G, cc - s));
+                continue;
+            }
+            if (!pack) {
+                put_group(gflag, gcnt, ctf, cc);
                 continue;
             }
             if (run_count + cc > G) {
@@ -2735,8 +2758,9 @@ static int form_groups(Tree *t, const int64_t *active, int64_t n_active, Work &w
     k_mark<<<grid_for(n_active, BT), BT, 0, s>>>(active, n_active, n, t->rank, w.flag, t->d_status);
     w.sc.exclusive(w.flag, w.pre, t->d_n, n, t->d_status, s);
     k_compact<<<grid_for(n, BT), BT, 0, s>>>(w.flag, w.pre, n, w.tgt);
-    k_group_marks<<<grid_for(t->nn, BT), BT, 0, s>>>(t->nfirst, t->ncount, t->nchild_first, t->nnchild, t->nn,
-                                                     t->nclouds, w.pre, t->prm.group_size, w.gflag, w.gcnt);
+    k_group_marks<<<grid_for(t->nn, BT), BT, 0, s>>>(t->nfirst, t->ncount, t->nchild_first, t->nnchild, t->nlevel,
+                                                     t->ncloud, t->nn, t->nclouds, w.pre, t->prm.group_size,
+                                                     w.gflag, w.gcnt);
     w.sc.exclusive(w.gflag, w.goff, w.pre + n, n, t->d_status, s);
     k_group_table<<<grid_for(n, BT), BT, 0, s>>>(w.gflag, w.gcnt, w.goff, w.pre + n, w.gtab);
     *d_ngroups = nullptr;

@@ -103,6 +103,50 @@ def test_moments_against_flat_sums(small):
         np.testing.assert_array_equal(mf[i, 14:17], x[sl].max(0))
 
 
+def group_level(U, G):
+    """Largest L with G 8^L <= U (0 below 8 G): the depth at which a uniform
+    cloud's nodes hold about G targets."""
+    L, v = 0, 8 * G
+    while v <= U and L < 21:
+        L, v = L + 1, v * 8
+    return L
+
+
+def test_group_level_values():
+    assert [group_level(U, 16) for U in (1, 127, 128, 1023, 1024, 209741, 2000102)] == [0, 0, 1, 1, 2, 4, 5]
+
+
+def test_groups_stay_inside_one_cell_of_the_group_level(oracle_lib):
+    """A clumpy cloud with a sparse background: every group's targets lie in
+    one node of the group level, or in one leaf above it (a group never packs
+    sparse octants of the top levels together)."""
+    c = gen.clumpy_cloud(60000, n_clumps=16, n_sink=8, seed=12)
+    t = oracle_lib.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=16)
+    act = gen.active_subset(c.n, 0.1, seed=2)
+    G = 16
+    ng = t.walk(act, G, 0.5)
+    g = t.groups()
+    tg = t.group_targets()
+    nd = t.nodes_int()
+    key = t.keys()[0]
+    gl = group_level(len(tg), G)
+    assert gl >= 2
+    cell = key >> np.uint64(3 * (21 - gl))
+    # the leaf holding each sorted rank
+    leaf_of = np.full(c.n, -1, np.int64)
+    for i in np.nonzero(nd[:, 5] == 0)[0]:
+        leaf_of[nd[i, 1]:nd[i, 1] + nd[i, 2]] = i
+    shallow = 0
+    for k in range(ng):
+        tf, tc = g[k, 1], g[k, 2]
+        r = tg[tf:tf + tc]
+        if np.all(cell[r] == cell[r[0]]):
+            continue
+        assert np.all(leaf_of[r] == leaf_of[r[0]]) and nd[leaf_of[r[0]], 0] < gl
+        shallow += 1
+    assert shallow < ng
+
+
 def test_groups_partition_targets(oracle_lib):
     c = gen.uniform_cloud(5000, seed=9, n_sink=8)
     t = oracle_lib.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=16)
@@ -120,14 +164,15 @@ def test_groups_partition_targets(oracle_lib):
     isact[rank[act]] = True
     assert np.all(np.diff(g[:, 1]) > 0)  # Morton order of first targets
     np.testing.assert_array_equal(np.cumsum(g[:, 2])[:-1], g[1:, 1])
+    gl = group_level(len(tg), G)
     for k in range(ng):
         node, tf, tc = g[k, :3]
         assert 1 <= tc <= G
         inside = tg[tf:tf + tc]
         # the run lies inside the node that packed it, and that node holds > G
-        # targets unless it is the root
+        # targets unless it is the root or lies above the group level
         assert np.all((inside >= nd[node, 1]) & (inside < nd[node, 1] + nd[node, 2]))
-        if node != 0:
+        if node != 0 and nd[node, 0] >= gl:
             assert isact[nd[node, 1]:nd[node, 1] + nd[node, 2]].sum() > G
     # groups are no smaller than the packing rule allows: two consecutive runs
     # packed under the same node never fit together into one group unless a
