@@ -509,6 +509,21 @@ __global__ void k_rs_start(const unsigned *gcount, int npass, unsigned *gstart)
     }
 }
 
+// The lanes holding the same 8-bit digit d as this one (valid lanes only; the
+// invalid lanes form their own set), from one ballot per digit bit: cheaper
+// here than one __match_any_sync (build on 2e7 particles 6.42 -> 6.33 ms).
+__device__ __forceinline__ unsigned digit_peers(int d, bool valid)
+{
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    unsigned peers = valid ? vm : ~vm;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1);
+        peers &= ((d >> b) & 1) ? bb : ~bb;
+    }
+    return peers;
+}
+
 __global__ void __launch_bounds__(RS_WARPS * 32, 4)
     k_rs_onesweep(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n, int shift,
                   const uint16_t *cl, const unsigned *gstart, unsigned long long *look, unsigned *tile_ctr,
@@ -544,7 +559,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 4)
     for (int r = 0; r < OS_ITEMS; r++) {
         const bool valid = base + r * 32 + lane < n;
         int d = valid ? rs_digit(k[r], v[r], shift, cl) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned peers = digit_peers(d, valid);
         int before = __popc(peers & lt);
         int c0 = valid ? wcnt[w][d] : 0;
         __syncwarp();
