@@ -168,11 +168,14 @@ struct Tgt {
 
 // Exact FP32 -> FP64 conversion of a normal or zero float (every result of
 // the flush-to-zero FP32 arithmetic here), on the integer pipes; infinities
-// and NaN take the hardware conversion.
+// and NaN take the hardware conversion, out of line so that no FP64
+// conversion is issued on the common path.
+__device__ __noinline__ double f64_of_special(float x) { return (double)x; }
+
 __device__ __forceinline__ double f64_of(float x)
 {
     const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu;
-    if (e == 255u) return (double)x;
+    if (e == 255u) return f64_of_special(x);
     const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
     if (e == 0u) return __longlong_as_double((long long)sign);
     return __longlong_as_double(
