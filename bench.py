@@ -58,10 +58,10 @@ FLOP_VJP_P2M_QUAD = 137
 # dram__bytes_write.sum, one ncu capture per list depth), valid only for the
 # evaluation sources (sha256 over EVAL_SOURCES), workload and launch shape they
 # were taken on; otherwise the line reports null.
-EVAL_TRAFFIC = {"sha256": "7a9facdbdc912d207e0c3ed347e6a6632b4c78a6e03c6a15475f0e6513416823",
+EVAL_TRAFFIC = {"sha256": "47d1dda0bfff05e8e772f39b0ba1687f9ddafc886f81e3134f3c5449c9fe7b7b",
                 "workload": "paper-20M", "leaf_size": 32, "group_size": 16,
-                "by_depth": {1: {"fwd": 13960663040, "vjp": 27508692736},
-                             2: {"fwd": 13804148480, "vjp": 28104479744}}}
+                "by_depth": {1: {"fwd": 14087021312, "vjp": 27807148032},
+                             2: {"fwd": 13966775296, "vjp": 28388249344}}}
 EVAL_SOURCES = ("walk.cu", "eval_chunks.cuh", "eval_chunks_body.inc")
 # Algorithmic HBM bytes per particle of sfg_build (frame 40, keys 36, 8 sort
 # passes x 32, gather 94, moments + walk records 150).
