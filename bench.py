@@ -187,32 +187,50 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# The oracle's tree and group shape for the CPU baselines: the shape the
+# autotuner picks for the clumpy workloads on the GPU.
+ORACLE_LEAF, ORACLE_GROUP = 32, 16
+
+
 def cpu_baseline(wl: dict, c, act, ca, cp, sample: int | None = None, seed: int = 0, target_s: float = 20.0) -> dict:
     """The oracle as it stands (FP64, OpenMP) on a bounded sample: the full
-    tree build, plus walk + field + adjoint for a random sample of active
-    rows, extrapolated per active row to the whole active set.  Without a
-    fixed `sample`, the sample grows from 1024 rows until its rows take at
-    least half of `target_s` seconds (or every active row is in); the last
-    pass is the one reported."""
+    tree build, then the group walks the sampled active rows need and their
+    field and adjoint.  The step time is extrapolated per walked group (to
+    every group) and per evaluated row (to every active row): a sparse sample
+    walks about one group per row, so charging the walk per row would count
+    each group's walk once per member.  Without a fixed `sample`, the sample
+    grows from 1024 rows until its rows take at least half of `target_s`
+    seconds (or every active row is in); the last pass is the one reported."""
     import oracle
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
-    tr = oracle.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=16)
+    tr = oracle.Tree(c.pos, c.mass, c.soft, c.is_sink, leaf_size=ORACLE_LEAF)
     t1 = time.perf_counter()
 
+    def timed(f):
+        ta = time.perf_counter()
+        r = f()
+        return r, time.perf_counter() - ta
+
     def rows_pass(k):
+        # every stage once for one row (its fixed cost) and once for the
+        # sample; the differences give the cost per walked group and per row
+        t_start = time.perf_counter()
         pick = np.sort(rng.choice(act.size, min(k, act.size), replace=False))
         rows = act[pick]
-        ta = time.perf_counter()
-        tr.walk(act, 32, wl["theta"], need=rows)
-        tr.accel_group(rows)
-        tb = time.perf_counter()
-        tr.vjp(rows[:1], ca[pick[:1]], cp[pick[:1]])
-        tc = time.perf_counter()
-        tr.vjp(rows, ca[pick], cp[pick])
-        td = time.perf_counter()
-        per_row = ((tb - ta) + max(0.0, (td - tc) - (tc - tb))) / rows.size
-        return rows.size, per_row, tc - tb, td - ta
+        _, w1 = timed(lambda: tr.walk(act, ORACLE_GROUP, wl["theta"], need=rows[:1]))
+        walked1 = int(tr.groups()[:, 3].sum())
+        _, a1 = timed(lambda: tr.accel_group(rows[:1]))
+        _, v1 = timed(lambda: tr.vjp(rows[:1], ca[pick[:1]], cp[pick[:1]]))
+        ng, w = timed(lambda: tr.walk(act, ORACLE_GROUP, wl["theta"], need=rows))
+        walked = int(tr.groups()[:, 3].sum())
+        _, a = timed(lambda: tr.accel_group(rows))
+        _, v = timed(lambda: tr.vjp(rows, ca[pick], cp[pick]))
+        dr = max(rows.size - 1, 1)
+        per_group = max(0.0, w - w1) / max(walked - walked1, 1)
+        per_row = (max(0.0, a - a1) + max(0.0, v - v1)) / dr
+        est = (w1 + per_group * (ng - walked1)) + (a1 + v1) + per_row * (act.size - 1)
+        return rows.size, walked, ng, est, time.perf_counter() - t_start
 
     t2 = time.perf_counter()
     if sample is None:
@@ -220,19 +238,21 @@ def cpu_baseline(wl: dict, c, act, ca, cp, sample: int | None = None, seed: int 
         k = 1024
         while True:
             t2 = time.perf_counter()
-            n_rows, per_row, t_fixed_vjp, took = rows_pass(k)
+            n_rows, walked, ng, est, took = rows_pass(k)
             if took >= 0.5 * target_s or n_rows >= act.size:
                 break
             k = int(min(act.size, k * min(16.0, target_s / max(took, 1e-3))))
     else:
-        n_rows, per_row, t_fixed_vjp, _ = rows_pass(sample)
+        n_rows, walked, ng, est, _ = rows_pass(sample)
     t3 = time.perf_counter()
     t_build = t1 - t0
-    t_step = t_build + t_fixed_vjp + per_row * act.size
+    t_step = t_build + est
     return {"value": act.size / t_step, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"oracle tree build over all {c.n} particles + group walk, field and adjoint for "
-                      f"{n_rows} of {act.size} active rows; per-row cost extrapolated to all rows",
-            "cpu_seconds_measured": round(t_build + (t3 - t2), 3), "est_step_s": round(t_step, 4)}
+            "sample": f"oracle tree build over all {c.n} particles (leaf {ORACLE_LEAF}), then {walked} of {ng} "
+                      f"group walks (groups of <= {ORACLE_GROUP}) and the field and adjoint of {n_rows} of "
+                      f"{act.size} active rows; walk cost extrapolated per group, evaluation per row",
+            "cpu_seconds_measured": round(t_build + (t3 - t2), 3), "est_step_s": round(t_step, 4),
+            "rows": int(n_rows)}
 
 
 def force_error(c, act, acc, phi, sample: int = 1000, seed: int = 0) -> dict:
@@ -264,15 +284,20 @@ def aggregate(local_ms: float, units_per_rank: int, world: int, dist=None, devic
 def run_reference(args, wl, rank, world):
     """--impl reference: the CPU oracle on this workload (rank 0 only).  One
     step is a bounded sample of the workload: the oracle tree over every
-    particle, then walk + field + adjoint of a random sample of the active
-    rows; ms_per_step is that step's wall time, and the value is the
-    evals/s of a whole step extrapolated from it per active row."""
+    particle, then the group walks, field and adjoint of a random sample of
+    the active rows (sized in the first warm-up step to about 4-8 s of row
+    work); ms_per_step is that step's wall time, and the value is the evals/s
+    of a whole step extrapolated from it (walks per group, evaluation per
+    row)."""
     if rank != 0:
         return
     c, act, ca, cp, frac = make_inputs(wl, 0, args.active_frac)
-    sample = 1024
-    for k in range(args.warmup):
-        cpu_baseline(wl, c, act, ca, cp, sample=64, seed=1 + k)
+    # the first warm-up step sizes the row sample (about 8 s of rows per step),
+    # the others run it
+    sample = None
+    for k in range(max(args.warmup, 1)):
+        r = cpu_baseline(wl, c, act, ca, cp, sample=sample, seed=1 + k, target_s=8.0)
+        sample = r["rows"]
     vals, wall = [], []
     r = None
     for k in range(args.steps):
@@ -286,6 +311,7 @@ def run_reference(args, wl, rank, world):
             "ms_per_step": 1e3 * statistics.mean(wall), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n_particles": int(c.n), "n_active": int(act.size),
+                       "leaf_size": ORACLE_LEAF, "group_size": ORACLE_GROUP,
                        "active_frac": frac, "theta": wl["theta"]},
             "cpu_baseline": {"kind": "oracle", "cores": r["cores"],
                              "sample": r["sample"] + "; ms_per_step is the wall time of one such sampled step",
